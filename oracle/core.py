@@ -15,7 +15,8 @@ reflector and the recursive block QR (Alg. 1) and hQR itself (Alg. 2) are writte
 Readings of places where the paper is silent or ambiguous (each is listed in the design doc):
 
 * Householder reflector (Alg. 1, n = 1): LAPACK dlarfg convention,
-  beta = -sign(alpha) * ||x|| with sign(alpha) = +1 for alpha >= 0 (including -0.0),
+  beta = -sign(alpha) * ||x|| where sign takes the sign bit of alpha (so -0.0 counts as
+  negative, as in LAPACK),
   gamma = (beta - alpha) / beta, y = [1; x_2 / (alpha - beta)], rho = beta; gamma = 0,
   y = e_1, rho = alpha when x_2 = 0.
 * The update of Alg. 1 uses Q_1^T = I - Y_1 T_1^T Y_1^T (the transpose is what Sec. 3
@@ -257,7 +258,7 @@ def householder(x):
     if xnorm == 0.0:
         return y, 0.0, alpha
     h = math.hypot(alpha, xnorm)
-    beta = -h if alpha >= 0.0 else h
+    beta = -math.copysign(h, alpha)
     gamma = (beta - alpha) / beta
     y[1:] = x[1:] / (alpha - beta)
     return y, gamma, beta
