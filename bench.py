@@ -1,0 +1,317 @@
+"""Benchmark of the hQR hot path on GB300: HODLR-QR factorizations per second (FP64).
+
+Workload (one step = one full factorization, Alg. 2 with every step on the device):
+  n = 8192, nmin = 256 (5 levels), off-diagonal rank 10 with Gaussian factors N(0,1)/sqrt(n),
+  leaves N(0,1) + 4 I, columns scaled by 10^(-14 j/(n-1)) (condition number ~1e14), tol = 1e-12,
+  synthetic and seeded.  ||A||_2 is estimated on the device inside every step.
+
+Timed arms (one JSON line on rank 0):
+  value      device throughput: A restored from a device snapshot and factored by one CUDA-graph
+             launch per step, CUDA events on the library's stream around each step, L2 flushed
+             (256 MiB write) between steps outside the timed events.
+  e2e        the same through the public C ABI with host buffers: pinned host -> device upload of
+             the matrix, factorization, and a device -> host read of the whole factorization.
+  roofline   the dominant kernel kind from an event-instrumented run of the same factorization.
+  cpu_baseline  the CPU oracle timed on the host cores on one factorization of the same workload.
+
+`--impl reference` times the CPU oracle itself (the paper publishes no code and no timings).
+Under torchrun every rank factors its own matrix (replicas only: one factorization does not
+shard), with no collective on the data path; rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "HODLR-QR factorizations/s (FP64, tol 1e-12)"
+UNIT = "factorizations/s"
+WORKLOAD = "hodlr_qr_n8192_nmin256_k10_colscaled1e-14_tol1e-12"
+N, NMIN, K, DECADES, TOL = 8192, 256, 10, 14.0, 1e-12
+RANK_CAP = 128
+# FP64 ALU peak from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
+# (the DFMA rate per SM was measured on this GPU)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_input(seed):
+    import workloads as W
+    return W.random_hodlr(N, NMIN, K, seed=seed, col_scale_decades=DECADES, name=WORKLOAD)
+
+
+def cpu_threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        t = [i.get("num_threads", 0) for i in info if i.get("user_api") == "blas"]
+        if t:
+            return int(max(t))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def time_oracle(inp, reps=1):
+    """Wall time of the CPU oracle on full factorizations of `inp` (seconds per factorization)."""
+    import oracle.core as O
+    ts = []
+    for _ in range(reps):
+        A = O.from_input(inp)
+        t0 = time.perf_counter()
+        O.hqr(A, TOL)
+        ts.append(time.perf_counter() - t0)
+    return min(ts)
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    inp = make_input(0)
+    for _ in range(args.warmup):
+        time_oracle(inp)
+    t = 0.0
+    for _ in range(args.steps):
+        t += time_oracle(inp)
+    value = args.steps / t
+    cores = cpu_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": N, "nmin": NMIN, "rank": K, "tol": TOL},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "one full factorization of the workload per step (numpy FP64 oracle)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1809_10585_gb300 import binding as B
+    from paper_1809_10585_gb300 import build as BUILD
+    BUILD.build()
+
+    inp = make_input(rank)
+    ctx = B.Context(local)
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream.cuda_stream)
+    M = B.Matrix(ctx, inp, rank_cap=RANK_CAP)
+    M.snapshot()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    # warm-up (the first call records the CUDA graph)
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 1)):
+            M.qr_graph(TOL, 0.0)
+    ctx.sync()
+    st, anorm = M.status()
+    if st != 0:
+        raise RuntimeError(f"factorization status {st}")
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    clocks = ClockSampler(local)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            M.qr_graph(TOL, 0.0)
+            evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    barrier()
+    ms_steps = [a.elapsed_time(b) for a, b in evs]
+    ms_total = float(sum(ms_steps))
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    st, anorm = M.status()
+    if st != 0:
+        raise RuntimeError(f"factorization status {st}")
+    ms_per_step = ms_total / args.steps
+    value = ws * args.steps / (ms_total / 1e3)
+
+    # ---------------------------------------------------------------- end to end (host buffers)
+    def pinned_like(a):
+        t = torch.empty(a.shape[::-1], dtype=torch.float64, pin_memory=True)   # column-major storage
+        t.numpy()[...] = np.asarray(a).T
+        return t
+    keep = []
+
+    def pin_list(lst):
+        out = []
+        for a in lst:
+            t = pinned_like(a)
+            keep.append(t)
+            out.append(t.numpy().T)      # Fortran-ordered view on pinned memory
+        return out
+    import workloads as W
+    pinp = W.HodlrInput(inp.n, inp.leaf_sizes, pin_list(inp.leaves), pin_list(inp.U12), pin_list(inp.V12),
+                        pin_list(inp.U21), pin_list(inp.V21), name=inp.name)
+    h2d = sum(a.nbytes for lst in (inp.leaves, inp.U12, inp.V12, inp.U21, inp.V21) for a in lst)
+    out_bytes = M.storage_bytes()
+    host_out = torch.empty(out_bytes, dtype=torch.uint8, pin_memory=True).numpy()
+    e2e_steps = max(1, min(args.steps, 10))
+    with torch.cuda.stream(stream):
+        M.upload(pinp)
+        M.qr(TOL, 0.0)
+        M.download(host_out)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for _ in range(e2e_steps):
+            M.upload(pinp)
+            M.qr(TOL, 0.0)
+            M.download(host_out)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": ws * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(out_bytes), "steps": e2e_steps}
+
+    # ---------------------------------------------------------------- roofline of the top kernel
+    prof = M.qr_profile(TOL, 0.0)
+    flops_total = M.flops()["total"]
+    top = max((k for k in prof if prof[k]["flops"] > 0), key=lambda k: prof[k]["ms"])
+    p = prof[top]
+    achieved = p["flops"] / (p["ms"] / 1e3) / 1e12 if p["ms"] > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "launches": p["launches"], "ms_per_launch": p["ms"] / max(1, p["launches"]),
+                "flops_per_launch": p["flops"] / max(1, p["launches"]),
+                "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (per-SM DFMA rate measured)",
+                "kind_ms": {k: round(v["ms"], 4) for k, v in prof.items()},
+                "kind_share": {k: round(v["ms"] / max(1e-9, sum(x["ms"] for x in prof.values())), 4)
+                               for k, v in prof.items()}}
+    gpu_launches = sum(v["launches"] for v in prof.values()) * args.steps
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N, "nmin": NMIN, "rank": K, "col_scale_decades": DECADES,
+                       "tol": TOL, "rank_cap": RANK_CAP, "l2": "flushed (256 MiB write) between timed steps",
+                       "parallelism": f"replicas x{ws}", "anorm": anorm},
+            "effective_gflops": flops_total / (ms_per_step / 1e3) / 1e9,
+            "algorithmic_gflop_per_step": flops_total / 1e9,
+            "wall_s_timed": t_wall, "clocks": clk, "e2e": e2e, "roofline": roofline,
+            "gpu_launches": gpu_launches}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        t = time_oracle(inp)
+        line["cpu_baseline"] = {"value": 1.0 / t, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                                "sample": "one full factorization of the same n=8192 workload"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,182 @@
+/*
+ * hodlr_qr.h — C ABI of a GB300 (sm_103a) FP64 implementation of hQR, the recursive
+ * Householder QR decomposition of HODLR matrices of Kressner & Susnjara, "Fast QR
+ * decomposition of HODLR matrices" (arXiv:1809.10585).
+ *
+ * A = Q R with Q = I - Y T Y^T in compact WY form (Sec. 1, Eq. (9)); Y (unit lower
+ * triangular), T and R (upper triangular) are HODLR matrices of the same partition as A, and
+ * every block update runs in HODLR arithmetic with truncation (Alg. 2).
+ *
+ * Conventions for every entry point below:
+ *  - All floating point data is IEEE double, column-major.
+ *  - "host" pointers point to CPU memory, "dev" pointers to memory of the context's device.
+ *    The caller owns every array it passes; the library owns the opaque handles.
+ *  - Work is queued on the context's stream and is asynchronous unless stated otherwise;
+ *    hodlr_sync() waits for it.  Calls on one context must not overlap from several threads.
+ *  - Every function returns HODLR_OK (0) or one of the error codes; on an error nothing that
+ *    the call would have written is guaranteed, and the handles stay valid.
+ *  - HODLR partition (Sec. 2.1, Eq. (2)): n = n_1 + ... + n_{2^l}.  Cluster-tree nodes are
+ *    numbered in heap order (root 0, children of v are 2v+1 and 2v+2); the internal nodes are
+ *    0 .. 2^l - 2.  For an internal node v with children c1 (size m1) and c2 (size m2), the
+ *    upper block is A12 = U12 V12^T (U12: m1 x r, V12: m2 x r) and the lower block is
+ *    A21 = U21 V21^T (U21: m2 x r, V21: m1 x r)  (Eq. (3) with A_L = U, A_R = V^T).
+ */
+#ifndef HODLR_QR_H
+#define HODLR_QR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HODLR_OK 0
+#define HODLR_EINVAL 1     /* malformed argument (sizes, partition, rank > block size ...)  */
+#define HODLR_ENOMEM 2     /* device or host allocation failed                               */
+#define HODLR_ERANK 3      /* a truncated rank exceeded the rank capacity: result truncated  */
+#define HODLR_ESINGULAR 4  /* zero diagonal entry of R met in a triangular solve             */
+#define HODLR_ETIMEOUT 5   /* a device-side wait gave up                                     */
+#define HODLR_ECUDA 6      /* a CUDA runtime call failed                                     */
+#define HODLR_ESTATE 7     /* call not valid in the object's state (e.g. solve before qr)    */
+
+typedef struct hodlr_ctx hodlr_ctx;   /* device, stream, workspace                          */
+typedef struct hodlr_mat hodlr_mat;   /* device-resident HODLR matrix and, after hodlr_qr,
+                                         its factors: Y and R in place of A, plus T           */
+
+const char* hodlr_strerror(int code);
+
+/* Context on CUDA device `device`; creates its own non-blocking stream. */
+int hodlr_ctx_create(int device, hodlr_ctx** out);
+void hodlr_ctx_destroy(hodlr_ctx* ctx);
+/* Use `stream` (a cudaStream_t, or NULL for the context's own stream) for later work. */
+int hodlr_ctx_set_stream(hodlr_ctx* ctx, void* stream);
+/* Block until all queued work on the context's stream is done. */
+int hodlr_sync(hodlr_ctx* ctx);
+
+/*
+ * hodlr_build — allocate a device-resident HODLR matrix and upload it (Sec. 2.1, Eq. (3)).
+ *   n, nleaf        : order, number of leaves (a power of two, >= 1).
+ *   leaf_sizes      : host, nleaf entries n_j > 0 summing to n.
+ *   leaves          : host, nleaf pointers; leaves[j] is n_j x n_j, leading dimension n_j.
+ *   U12, V12, U21, V21 : host, nleaf-1 pointers each (NULL allowed where the rank is 0),
+ *                     layouts as in the header comment, leading dimension = row count.
+ *   r12, r21        : host, nleaf-1 ranks, 0 <= r <= min(m1, m2) and r <= rank_cap.
+ *   rank_cap        : storage capacity per off-diagonal block (ranks of Y, T and R produced
+ *                     by hodlr_qr must fit; 8 <= rank_cap <= 256).
+ * Errors: HODLR_EINVAL on bad sizes, HODLR_ENOMEM.  The copies complete before return.
+ */
+int hodlr_build(hodlr_ctx* ctx, int n, int nleaf, const int* leaf_sizes,
+                const double* const* leaves,
+                const double* const* U12, const double* const* V12, const int* r12,
+                const double* const* U21, const double* const* V21, const int* r21,
+                int rank_cap, hodlr_mat** out);
+void hodlr_free(hodlr_mat* A);
+
+/* Re-upload new values into an existing matrix of the same partition (no allocation;
+ * the arguments have the meaning of hodlr_build).  Asynchronous w.r.t. the host only if the
+ * host arrays are pinned. */
+int hodlr_upload(hodlr_ctx* ctx, hodlr_mat* A, const double* const* leaves,
+                 const double* const* U12, const double* const* V12, const int* r12,
+                 const double* const* U21, const double* const* V21, const int* r21);
+
+/* Keep a device copy of the current A (snapshot) / copy it back (restore), so that A can be
+ * factored again after hodlr_qr overwrote it.  restore is a device-to-device copy. */
+int hodlr_snapshot(hodlr_ctx* ctx, hodlr_mat* A);
+int hodlr_restore(hodlr_ctx* ctx, hodlr_mat* A);
+
+/*
+ * hodlr_qr — hQR (Alg. 2 applied with A~ = A and void B, C): A = (I - Y T Y^T) R.
+ *   tol   : truncation tolerance eps.  Truncations that carry A's scale (S~, A^12 and the
+ *           HODLR update of A^22) use eps * anorm, T~12 uses eps (Alg. 2).
+ *   anorm : ||A||_2 to scale thresholds; <= 0 means estimate it on the device by
+ *           30 power iterations on A^T A from the normalized all-ones vector.
+ * A is overwritten: its storage then holds Y (strictly lower leaves and lower blocks) and R
+ * (upper leaves and upper blocks); T is stored alongside.  Asynchronous; the device-side
+ * status (e.g. HODLR_ERANK) is returned by hodlr_status.
+ */
+int hodlr_qr(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm);
+
+/* Record hodlr_restore + hodlr_qr(tol, anorm) into a CUDA graph held by A (first call), and
+ * launch that graph (every call).  Same results as restore followed by hodlr_qr. */
+int hodlr_qr_graph(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm);
+
+/*
+ * hodlr_qr_profile — hodlr_restore followed by hodlr_qr(tol, anorm), run eagerly with a CUDA
+ * event pair around every kernel launch (needs a prior hodlr_snapshot).  For each kernel kind
+ * k in 0..7 = {batched GEMM, split-K reduction, cluster Householder QR, cluster Jacobi SVD,
+ * rank selection, data movement (concat/copy/gather/scatter), vector norm, other} it returns
+ * the summed event time ms[k] (milliseconds), the launch count launches[k] and the
+ * algorithmic FP64 flops flops[k] those launches performed (standard counts per primitive:
+ * 2mnk per product, 2hk^2 - 2k^3/3 per QR plus hk^2 - k^3/3 when T is built, the R-SVD count
+ * 4p^2q + 8pq^2 + 9q^3 per Jacobi core).  Synchronous; results equal those of hodlr_qr.
+ */
+int hodlr_qr_profile(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm, double* ms,
+                     int* launches, double* flops);
+
+/* Synchronize and return the status word of the last factorization (HODLR_OK, HODLR_ERANK,
+ * HODLR_ETIMEOUT) in *status, and the ||A||_2 used in *anorm_used (either may be NULL). */
+int hodlr_status(hodlr_ctx* ctx, hodlr_mat* A, int* status, double* anorm_used);
+
+/* Copy the current ranks to host arrays of nleaf-1 entries (any may be NULL):
+ * r12/r21 of the A/Y/R storage and rT of T's upper blocks.  Synchronous. */
+int hodlr_ranks(hodlr_ctx* ctx, const hodlr_mat* A, int* r12, int* r21, int* rT);
+
+/* Algorithmic FP64 flop counts of the last hodlr_qr, per step of the hot path, into
+ * out[0..7] = {norm estimate, left-orthogonalization, leaf QR, S~, S, update, T12, total}
+ * (standard counts per primitive computed from the sizes each kernel met).  Synchronous. */
+int hodlr_flops(hodlr_ctx* ctx, const hodlr_mat* A, double* out);
+
+/*
+ * Dense n x n copy of a part of the stored matrix into out_dev (leading dimension ld >= n):
+ * which = 0: A as stored (full), 1: Y (unit lower part), 2: R (upper part), 3: T.
+ */
+int hodlr_to_dense(hodlr_ctx* ctx, const hodlr_mat* A, int which, double* out_dev, int ld);
+
+/* Y_dev = op(M) X_dev for M = part `which` (as in hodlr_to_dense), op = transpose if trans;
+ * X and Y are n x nrhs (Table 1, matrix-vector multiplication, with nrhs vectors at once). */
+int hodlr_matvec(hodlr_ctx* ctx, const hodlr_mat* A, int which, int trans, int nrhs,
+                 const double* X_dev, int ldx, double* Y_dev, int ldy);
+
+/* B_dev <- Q B or Q^T B with Q = I - Y T Y^T (Sec. 1), B is n x nrhs.  Needs hodlr_qr. */
+int hodlr_apply_q(hodlr_ctx* ctx, const hodlr_mat* A, int nrhs, double* B_dev, int ldb);
+int hodlr_apply_qt(hodlr_ctx* ctx, const hodlr_mat* A, int nrhs, double* B_dev, int ldb);
+
+/* B_dev <- R^{-1} Q^T B: Q^T b followed by HODLR back-substitution with R
+ * (x2 = R22^{-1} b2, x1 = R11^{-1} (b1 - R12 x2)).  Needs hodlr_qr.  A zero diagonal entry
+ * of R makes the result non-finite; hodlr_solve then returns HODLR_ESINGULAR (synchronous). */
+int hodlr_solve(hodlr_ctx* ctx, const hodlr_mat* A, int nrhs, double* B_dev, int ldb);
+
+/* ||A||_2 estimate as used by hodlr_qr (power iteration, `iters` steps).  Synchronous. */
+int hodlr_norm2_estimate(hodlr_ctx* ctx, const hodlr_mat* A, int iters, double* out);
+
+/* Size in bytes of the compact device storage of A (factors, T, ranks) and a synchronous
+ * copy of it into host memory (for moving a factorization off the device). */
+size_t hodlr_storage_bytes(const hodlr_mat* A);
+int hodlr_download(hodlr_ctx* ctx, const hodlr_mat* A, void* host, size_t bytes);
+
+/*
+ * Primitives of the hot path, exposed for testing kernel by kernel.
+ *
+ * hodlr_dense_qr — Householder QR in compact WY form of one dense h x w device matrix
+ * (Alg. 1; h >= 1, 1 <= w <= 1024): on return A holds R in its upper triangle and the
+ * Householder vectors (unit diagonal implied) below it, T_dev (w x w, leading dimension ldt)
+ * the upper-triangular T with Q = I - Y T Y^T.  LAPACK dlarfg sign convention.
+ */
+int hodlr_dense_qr(hodlr_ctx* ctx, int h, int w, double* A_dev, int lda, double* T_dev, int ldt);
+
+/*
+ * hodlr_truncate — recompression T_thr of the low-rank product L Rt^T (Sec. 2.1.1):
+ * L_dev (nL x K, ld nL), Rt_dev (nR x K, ld nR); keeps the singular triplets with
+ * sigma > thr.  Writes Lout_dev (nL x k, ld nL, orthonormal columns) and Rout_dev
+ * (nR x k, ld nR) with k <= min(K, kmax), and k to *k_out (host).  Synchronous.
+ * K <= 256.  Returns HODLR_ERANK if more than kmax singular values exceed thr.
+ */
+int hodlr_truncate(hodlr_ctx* ctx, int nL, int nR, int K, const double* L_dev,
+                   const double* Rt_dev, double thr, int kmax, double* Lout_dev,
+                   double* Rout_dev, int* k_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HODLR_QR_H */

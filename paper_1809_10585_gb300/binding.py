@@ -1,0 +1,245 @@
+"""ctypes binding of the hQR C ABI (include/hodlr_qr.h).
+
+Argument marshalling only: every step of the factorization, apply and solve runs in the CUDA
+library.  Device buffers are passed as raw pointers (e.g. ``torch.Tensor.data_ptr()``), host
+buffers as numpy arrays.  Loading fails loudly when the library has not been built — there is
+no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+HODLR_OK, HODLR_EINVAL, HODLR_ENOMEM, HODLR_ERANK, HODLR_ESINGULAR, HODLR_ETIMEOUT, HODLR_ECUDA, HODLR_ESTATE = range(8)
+
+_lib = None
+
+
+class HodlrError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {lib().hodlr_strerror(code).decode()} ({code})")
+
+
+_PD = C.POINTER(C.c_double)
+_PPD = C.POINTER(_PD)
+_PI = C.POINTER(C.c_int)
+_VP = C.c_void_p
+
+_SIGS = {
+    "hodlr_strerror": (C.c_char_p, [C.c_int]),
+    "hodlr_ctx_create": (C.c_int, [C.c_int, C.POINTER(_VP)]),
+    "hodlr_ctx_destroy": (None, [_VP]),
+    "hodlr_ctx_set_stream": (C.c_int, [_VP, _VP]),
+    "hodlr_sync": (C.c_int, [_VP]),
+    "hodlr_build": (C.c_int, [_VP, C.c_int, C.c_int, _PI, _PPD, _PPD, _PPD, _PI, _PPD, _PPD, _PI, C.c_int, C.POINTER(_VP)]),
+    "hodlr_free": (None, [_VP]),
+    "hodlr_upload": (C.c_int, [_VP, _VP, _PPD, _PPD, _PPD, _PI, _PPD, _PPD, _PI]),
+    "hodlr_snapshot": (C.c_int, [_VP, _VP]),
+    "hodlr_restore": (C.c_int, [_VP, _VP]),
+    "hodlr_qr": (C.c_int, [_VP, _VP, C.c_double, C.c_double]),
+    "hodlr_qr_graph": (C.c_int, [_VP, _VP, C.c_double, C.c_double]),
+    "hodlr_qr_profile": (C.c_int, [_VP, _VP, C.c_double, C.c_double, _PD, _PI, _PD]),
+    "hodlr_status": (C.c_int, [_VP, _VP, _PI, _PD]),
+    "hodlr_ranks": (C.c_int, [_VP, _VP, _PI, _PI, _PI]),
+    "hodlr_flops": (C.c_int, [_VP, _VP, _PD]),
+    "hodlr_to_dense": (C.c_int, [_VP, _VP, C.c_int, _VP, C.c_int]),
+    "hodlr_matvec": (C.c_int, [_VP, _VP, C.c_int, C.c_int, C.c_int, _VP, C.c_int, _VP, C.c_int]),
+    "hodlr_apply_q": (C.c_int, [_VP, _VP, C.c_int, _VP, C.c_int]),
+    "hodlr_apply_qt": (C.c_int, [_VP, _VP, C.c_int, _VP, C.c_int]),
+    "hodlr_solve": (C.c_int, [_VP, _VP, C.c_int, _VP, C.c_int]),
+    "hodlr_norm2_estimate": (C.c_int, [_VP, _VP, C.c_int, _PD]),
+    "hodlr_storage_bytes": (C.c_size_t, [_VP]),
+    "hodlr_download": (C.c_int, [_VP, _VP, _VP, C.c_size_t]),
+    "hodlr_dense_qr": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.c_int, _VP, C.c_int]),
+    "hodlr_truncate": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, _VP, _VP, C.c_double, C.c_int, _VP, _VP, _PI]),
+}
+
+SYMBOLS = tuple(_SIGS)
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libhodlrqr.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing: run paper_1809_10585_gb300.build.build()")
+        L = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(rc, what=""):
+    if rc != HODLR_OK:
+        raise HodlrError(rc, what)
+    return rc
+
+
+def _ptr_array(arrs):
+    """Array of double* for a list of C-contiguous-in-Fortran-order numpy arrays (None -> NULL)."""
+    out = (_PD * len(arrs))()
+    keep = []
+    for i, a in enumerate(arrs):
+        if a is None or a.size == 0:
+            out[i] = _PD()
+            continue
+        a = np.asfortranarray(a, dtype=np.float64)
+        keep.append(a)
+        out[i] = a.ctypes.data_as(_PD)
+    return out, keep
+
+
+class Context:
+    def __init__(self, device: int = 0):
+        self.h = _VP()
+        check(lib().hodlr_ctx_create(device, C.byref(self.h)), "hodlr_ctx_create")
+
+    def set_stream(self, stream_handle: int | None):
+        check(lib().hodlr_ctx_set_stream(self.h, _VP(stream_handle or 0)), "hodlr_ctx_set_stream")
+
+    def sync(self):
+        check(lib().hodlr_sync(self.h), "hodlr_sync")
+
+    def close(self):
+        if self.h:
+            lib().hodlr_ctx_destroy(self.h)
+            self.h = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _marshal(inp):
+    nleaf = len(inp.leaf_sizes)
+    nn = nleaf - 1
+    sizes = (C.c_int * nleaf)(*inp.leaf_sizes)
+    leaves, k1 = _ptr_array(list(inp.leaves))
+    U12, k2 = _ptr_array(list(inp.U12) if nn else [None])
+    V12, k3 = _ptr_array(list(inp.V12) if nn else [None])
+    U21, k4 = _ptr_array(list(inp.U21) if nn else [None])
+    V21, k5 = _ptr_array(list(inp.V21) if nn else [None])
+    r12 = (C.c_int * max(1, nn))(*[int(np.shape(u)[1]) for u in inp.U12] if nn else [0])
+    r21 = (C.c_int * max(1, nn))(*[int(np.shape(u)[1]) for u in inp.U21] if nn else [0])
+    return sizes, leaves, U12, V12, r12, U21, V21, r21, (k1, k2, k3, k4, k5)
+
+
+class Matrix:
+    """A device-resident HODLR matrix built from a host description with the fields
+    n, leaf_sizes, leaves, U12, V12, U21, V21 (see workloads.HodlrInput)."""
+
+    def __init__(self, ctx: Context, inp, rank_cap: int = 128):
+        self.ctx = ctx
+        self.n = int(inp.n)
+        self.nleaf = len(inp.leaf_sizes)
+        self.h = _VP()
+        sizes, leaves, U12, V12, r12, U21, V21, r21, keep = _marshal(inp)
+        check(lib().hodlr_build(ctx.h, self.n, self.nleaf, sizes, leaves, U12, V12, r12, U21, V21, r21,
+                                rank_cap, C.byref(self.h)), "hodlr_build")
+        self.rank_cap = rank_cap
+
+    def upload(self, inp):
+        sizes, leaves, U12, V12, r12, U21, V21, r21, keep = _marshal(inp)
+        check(lib().hodlr_upload(self.ctx.h, self.h, leaves, U12, V12, r12, U21, V21, r21), "hodlr_upload")
+
+    def snapshot(self):
+        check(lib().hodlr_snapshot(self.ctx.h, self.h), "hodlr_snapshot")
+
+    def restore(self):
+        check(lib().hodlr_restore(self.ctx.h, self.h), "hodlr_restore")
+
+    def qr(self, tol: float, anorm: float = 0.0):
+        check(lib().hodlr_qr(self.ctx.h, self.h, tol, anorm), "hodlr_qr")
+
+    def qr_graph(self, tol: float, anorm: float = 0.0):
+        check(lib().hodlr_qr_graph(self.ctx.h, self.h, tol, anorm), "hodlr_qr_graph")
+
+    KINDS = ("gemm", "gemm_reduce", "cluster_qr", "cluster_jacobi", "select", "data_movement", "norm", "other")
+
+    def qr_profile(self, tol: float, anorm: float = 0.0):
+        ms, ln, fl = (C.c_double * 8)(), (C.c_int * 8)(), (C.c_double * 8)()
+        check(lib().hodlr_qr_profile(self.ctx.h, self.h, tol, anorm, ms, ln, fl), "hodlr_qr_profile")
+        return {k: {"ms": ms[i], "launches": ln[i], "flops": fl[i]} for i, k in enumerate(self.KINDS)}
+
+    def status(self):
+        st = C.c_int()
+        an = C.c_double()
+        check(lib().hodlr_status(self.ctx.h, self.h, C.byref(st), C.byref(an)), "hodlr_status")
+        return st.value, an.value
+
+    def ranks(self):
+        nn = max(1, self.nleaf - 1)
+        a, b, c = (C.c_int * nn)(), (C.c_int * nn)(), (C.c_int * nn)()
+        check(lib().hodlr_ranks(self.ctx.h, self.h, a, b, c), "hodlr_ranks")
+        k = self.nleaf - 1
+        return np.array(a[:k]), np.array(b[:k]), np.array(c[:k])
+
+    def flops(self):
+        out = (C.c_double * 8)()
+        check(lib().hodlr_flops(self.ctx.h, self.h, out), "hodlr_flops")
+        keys = ["a2_norm", "a3_left_orth", "a4_leaf_qr", "a5_S", "a6_TS", "a7_update", "a8_T12", "total"]
+        return dict(zip(keys, list(out)))
+
+    def to_dense(self, which: int, out_ptr: int, ld: int):
+        check(lib().hodlr_to_dense(self.ctx.h, self.h, which, _VP(out_ptr), ld), "hodlr_to_dense")
+
+    def matvec(self, which, trans, nrhs, X_ptr, ldx, Y_ptr, ldy):
+        check(lib().hodlr_matvec(self.ctx.h, self.h, which, int(trans), nrhs, _VP(X_ptr), ldx, _VP(Y_ptr), ldy),
+              "hodlr_matvec")
+
+    def apply_q(self, nrhs, B_ptr, ldb):
+        check(lib().hodlr_apply_q(self.ctx.h, self.h, nrhs, _VP(B_ptr), ldb), "hodlr_apply_q")
+
+    def apply_qt(self, nrhs, B_ptr, ldb):
+        check(lib().hodlr_apply_qt(self.ctx.h, self.h, nrhs, _VP(B_ptr), ldb), "hodlr_apply_qt")
+
+    def solve(self, nrhs, B_ptr, ldb):
+        return lib().hodlr_solve(self.ctx.h, self.h, nrhs, _VP(B_ptr), ldb)
+
+    def norm2_estimate(self, iters=30):
+        out = C.c_double()
+        check(lib().hodlr_norm2_estimate(self.ctx.h, self.h, iters, C.byref(out)), "hodlr_norm2_estimate")
+        return out.value
+
+    def storage_bytes(self):
+        return int(lib().hodlr_storage_bytes(self.h))
+
+    def download(self, host: np.ndarray):
+        check(lib().hodlr_download(self.ctx.h, self.h, _VP(host.ctypes.data), host.nbytes), "hodlr_download")
+
+    def free(self):
+        if self.h:
+            lib().hodlr_free(self.h)
+            self.h = _VP()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def dense_qr(ctx: Context, h, w, A_ptr, lda, T_ptr, ldt):
+    check(lib().hodlr_dense_qr(ctx.h, h, w, _VP(A_ptr), lda, _VP(T_ptr), ldt), "hodlr_dense_qr")
+
+
+def truncate(ctx: Context, nL, nR, K, L_ptr, Rt_ptr, thr, kmax, Lout_ptr, Rout_ptr):
+    k = C.c_int()
+    rc = lib().hodlr_truncate(ctx.h, nL, nR, K, _VP(L_ptr), _VP(Rt_ptr), thr, kmax, _VP(Lout_ptr),
+                              _VP(Rout_ptr), C.byref(k))
+    return rc, k.value

@@ -1,0 +1,377 @@
+// Cluster-cooperative FP64 factorizations of the hQR hot path:
+//
+//  * qr_cluster_kernel — Householder QR in compact WY form (Alg. 1 semantics: one
+//    reflector per column, LAPACK dlarfg sign convention) of one dense h x w matrix per
+//    thread-block cluster.  Columns are dealt cyclically to the CTAs of the cluster; for
+//    column j its owner builds the reflector, one cluster barrier publishes it, and every CTA
+//    applies it to its own later columns (one warp per column, warp-shuffle reductions).  The
+//    T factor is then built from G = Y^T Y: 16 x 16 diagonal blocks by the column recurrence
+//    of the compact WY form, and larger blocks by T12 = -T1 G12 T2 (Sec. 3, Eq. (10)).
+//    Used for the compressed leaf columns (Alg. 2, lowest level), the left-orthogonalization
+//    (Sec. 2.1) and the two QRs inside T_eps (Sec. 2.1.1).
+//
+//  * jacobi_cluster_kernel — one-sided (Hestenes) Jacobi on the columns of the K x K core of
+//    T_eps, round-robin pair ordering, pairs spread over all warps of the cluster, one
+//    cluster barrier per round.
+//
+// On GB300 a single SM retires about 2 FP64 FMA per clock, so a K^3 factorization on one SM
+// takes milliseconds for K ~ 100; a cluster of up to 16 CTAs (one per SM) multiplies the FP64
+// rate at the cost of one hardware cluster barrier per step.  Data stay in global memory
+// (L2-resident at these sizes) and are read with ld.global.cg so that values published by
+// other CTAs of the cluster after a barrier are never served stale from L1.
+#include <cooperative_groups.h>
+
+#include <cstdio>
+
+#include "common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace hq {
+
+constexpr int QT = 256;            // threads per CTA
+constexpr int QW = QT / 32;        // warps per CTA
+constexpr int TNB = 16;            // diagonal block size of the T build
+
+__device__ inline double warp_sum2(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ double block_sum(double v, double* red) {
+  v = warp_sum2(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = (threadIdx.x < QW) ? red[threadIdx.x] : 0.0;
+  if (w == 0) t = warp_sum2(t);
+  if (threadIdx.x == 0) red[QW] = t;
+  __syncthreads();
+  return red[QW];
+}
+
+__global__ void __launch_bounds__(QT) qr_cluster_kernel(const QRDesc* __restrict__ descs,
+                                                        const int* __restrict__ di, double* flops) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int crank = (int)cl.block_rank();
+  const QRDesc& d = descs[blockIdx.y];
+  const int h = dimv(d.h, d.href, di), w = dimv(d.w, d.wref, di);
+  const int kmax = min(h, w);
+  double* A = d.A;
+  const size_t lda = d.lda;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ double red[QW + 1];
+  __shared__ double bc[2];
+
+  if (crank == 0 && threadIdx.x == 0 && flops && kmax > 0) {
+    if (d.step >= 0) {
+      double f;
+      if (d.fmode == 0) {   // dense QR with its T factor
+        f = 2.0 * h * (double)w * w - 2.0 * (double)w * w * w / 3.0 + (double)h * w * w - (double)w * w * w / 3.0;
+      } else {              // economy QR with Q formed
+        double q = kmax;
+        f = 4.0 * h * (double)w * q - 4.0 * q * q * q / 3.0;
+      }
+      atomicAdd(&flops[d.step], f);
+    }
+    // work of this launch: Householder QR (reflectors applied to all w columns) and T
+    const double q = kmax;
+    double g = 2.0 * h * (double)w * q - q * q * (double)w - q * q * q / 3.0 + (double)w * q * q / 3.0;
+    if (g < 0) g = 0;
+    if (d.T) g += (double)h * q * q - q * q * q / 3.0;
+    atomicAdd(&flops[kKindSlot + 2], g);
+  }
+
+  for (int j = 0; j < kmax; ++j) {
+    if ((j % C) == crank) {
+      double s = 0.0;
+      for (int i = j + 1 + threadIdx.x; i < h; i += QT) {
+        double v = __ldcg(&A[i + j * lda]);
+        s = fma(v, v, s);
+      }
+      s = block_sum(s, red);
+      if (threadIdx.x == 0) {
+        double alpha = __ldcg(&A[j + j * lda]);
+        double tau = 0.0, scal = 0.0;
+        if (s > 0.0) {
+          double hn = hypot(alpha, sqrt(s));
+          double beta = -copysign(hn, alpha);
+          tau = (beta - alpha) / beta;
+          scal = 1.0 / (alpha - beta);
+          A[j + j * lda] = beta;
+        }
+        d.tau[j] = tau;
+        bc[0] = scal;
+      }
+      __syncthreads();
+      const double scal = bc[0];
+      if (scal != 0.0)
+        for (int i = j + 1 + threadIdx.x; i < h; i += QT) A[i + j * lda] = __ldcg(&A[i + j * lda]) * scal;
+    }
+    cl.sync();
+    const double tau = __ldcg(&d.tau[j]);
+    if (tau != 0.0) {
+      // own columns c > j with c % C == crank, one warp per column
+      int first = j + 1;
+      int c0 = first + ((crank - first % C) + C) % C;
+      const double* y = A + j * lda;
+      for (int c = c0 + warp * C; c < w; c += QW * C) {
+        double* a = A + c * lda;
+        double t = 0.0;
+        for (int i = j + 1 + lane; i < h; i += 32) t = fma(__ldcg(&y[i]), __ldcg(&a[i]), t);
+        t = warp_sum2(t);
+        t += __ldcg(&a[j]);
+        t *= tau;
+        if (lane == 0) a[j] = __ldcg(&a[j]) - t;
+        for (int i = j + 1 + lane; i < h; i += 32) a[i] = fma(-t, __ldcg(&y[i]), __ldcg(&a[i]));
+      }
+    }
+    __syncthreads();
+  }
+  if (d.T == nullptr || kmax == 0) return;
+
+  // ---- T from G = Y^T Y (strictly upper part), Y unit lower trapezoidal
+  double* G = d.G;
+  const size_t ldg = d.ldg;
+  double* T = d.T;
+  const size_t ldt = d.ldt;
+  cl.sync();   // all columns final
+  {
+    const int gw = crank * QW + warp, nw = C * QW;
+    const long npairs = (long)kmax * (kmax - 1) / 2;
+    for (long p = gw; p < npairs; p += nw) {
+      // decode p -> (i, jj) with i < jj, jj-major
+      int jj = (int)((1.0 + sqrt(1.0 + 8.0 * (double)p)) * 0.5);
+      while ((long)jj * (jj - 1) / 2 > p) --jj;
+      while ((long)(jj + 1) * jj / 2 <= p) ++jj;
+      int i = (int)(p - (long)jj * (jj - 1) / 2);
+      const double* yi = A + i * lda;
+      const double* yj = A + jj * lda;
+      double t = 0.0;
+      for (int r = jj + 1 + lane; r < h; r += 32) t = fma(__ldcg(&yi[r]), __ldcg(&yj[r]), t);
+      t = warp_sum2(t);
+      if (lane == 0) G[i + jj * ldg] = t + __ldcg(&yi[jj]);
+    }
+    // zero T's strictly lower part, then diagonal blocks by the column recurrence
+    for (long e = (long)crank * QT + threadIdx.x; e < (long)kmax * kmax; e += (long)C * QT) {
+      int i = (int)(e % kmax), jj = (int)(e / kmax);
+      if (i > jj) T[i + jj * ldt] = 0.0;
+    }
+  }
+  cl.sync();
+  {
+    const int gw = crank * QW + warp, nw = C * QW;
+    const int nblk = (kmax + TNB - 1) / TNB;
+    for (int b = gw; b < nblk; b += nw) {
+      const int b0 = b * TNB, b1 = min(kmax, b0 + TNB);
+      for (int jj = b0; jj < b1; ++jj) {
+        const double tj = __ldcg(&d.tau[jj]);
+        // lane l computes T[b0 + l, jj] for b0 + l < jj
+        int i = b0 + lane;
+        double v = 0.0;
+        if (i < jj && lane < TNB) {
+          double s = 0.0;
+          for (int l = i; l < jj; ++l) s = fma(T[i + l * ldt], __ldcg(&G[l + jj * ldg]), s);
+          v = -tj * s;
+        }
+        __syncwarp();
+        if (i < jj && lane < TNB) T[i + jj * ldt] = v;
+        if (lane == 0) T[jj + jj * ldt] = tj;
+        __syncwarp();
+      }
+    }
+  }
+  // ---- merges: T12 = -T1 G12 T2 for adjacent blocks of size s
+  for (int s = TNB; s < kmax; s *= 2) {
+    cl.sync();
+    const long tid = (long)crank * QT + threadIdx.x, nt = (long)C * QT;
+    const int npair = (kmax + 2 * s - 1) / (2 * s);
+    // X = T1 G12 stored transposed in G's strictly lower part: G[b + jj, a + i]
+    for (long e = tid; e < (long)npair * s * s; e += nt) {
+      int q = (int)(e / ((long)s * s));
+      int rem = (int)(e % ((long)s * s));
+      int i = rem % s, jj = rem / s;
+      int a = 2 * q * s, b = a + s;
+      if (b + jj >= kmax) continue;
+      double acc = 0.0;
+      for (int l = i; l < s; ++l) acc = fma(__ldcg(&T[(a + i) + (size_t)(a + l) * ldt]), __ldcg(&G[(a + l) + (size_t)(b + jj) * ldg]), acc);
+      G[(b + jj) + (size_t)(a + i) * ldg] = acc;
+    }
+    cl.sync();
+    for (long e = tid; e < (long)npair * s * s; e += nt) {
+      int q = (int)(e / ((long)s * s));
+      int rem = (int)(e % ((long)s * s));
+      int i = rem % s, jj = rem / s;
+      int a = 2 * q * s, b = a + s;
+      if (b + jj >= kmax) continue;
+      double acc = 0.0;
+      for (int l = 0; l <= jj; ++l) acc = fma(__ldcg(&G[(b + l) + (size_t)(a + i) * ldg]), __ldcg(&T[(b + l) + (size_t)(b + jj) * ldt]), acc);
+      T[(a + i) + (size_t)(b + jj) * ldt] = -acc;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __restrict__ descs,
+                                                            const int* __restrict__ di, double* flops);
+
+// Largest cluster size both cluster kernels can be launched with (16 needs the non-portable
+// attribute and enough SMs per GPC), probed once per process; attributes are set here, never
+// during stream capture.
+int qr_max_cluster() {
+  static int cached = -1;
+  if (cached > 0) return cached;
+  int v = 8;
+  bool ok = cudaFuncSetAttribute(qr_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+            cudaFuncSetAttribute(jacobi_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+  if (ok) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16, 1, 1);
+    cfg.blockDim = dim3(QT, 1, 1);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 16;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, qr_cluster_kernel, &cfg) == cudaSuccess && nclusters > 0) {
+      int nj = 0;
+      if (cudaOccupancyMaxActiveClusters(&nj, jacobi_cluster_kernel, &cfg) == cudaSuccess && nj > 0) v = 16;
+    }
+  }
+  cudaGetLastError();
+  cached = v;
+  return v;
+}
+
+cudaError_t launch_qr(const QRDesc* h, int n, QRDesc* d, const int* devints, double* flops,
+                      int cluster, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cluster, n, 1);
+  cfg.blockDim = dim3(QT, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, qr_cluster_kernel, (const QRDesc*)d, devints, flops);
+}
+
+// --------------------------------------------------------------------------------- Jacobi
+__device__ inline void rr_pair(int r, int i, int P, int& a, int& b) {
+  // round-robin (circle) schedule on P (even) players, round r in [0, P-1)
+  if (i == 0) {
+    a = P - 1;
+    b = r;
+  } else {
+    a = (r + i) % (P - 1);
+    b = (r - i + (P - 1)) % (P - 1);
+  }
+}
+
+__global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __restrict__ descs,
+                                                            const int* __restrict__ di, double* flops) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int crank = (int)cl.block_rank();
+  const JacobiDesc& d = descs[blockIdx.y];
+  const int q1 = dimv(d.q1, d.q1ref, di), q2 = dimv(d.q2, d.q2ref, di);
+  if (crank == 0 && threadIdx.x == 0 && flops && q1 > 0 && q2 > 0) {
+    // algorithmic count of an SVD of the q1 x q2 core (R-SVD, Golub & Van Loan)
+    double p = max(q1, q2), q = min(q1, q2);
+    atomicAdd(&flops[kKindSlot + 3], 4.0 * p * p * q + 8.0 * p * q * q + 9.0 * q * q * q);
+  }
+  double* M = d.M;
+  const size_t ldm = d.ldm;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = crank * QW + warp, nw = C * QW;
+  // relative orthogonality threshold for a pair
+  const double tol = fmin(1e-13, fmax(1e-15, 4.4e-16 * (double)q1));
+
+  if (crank == 0)
+    for (int i = threadIdx.x; i < kMaxSweeps; i += QT) d.rot[i] = 0;
+  for (int j = gw; j < q2; j += nw) {
+    double s = 0.0;
+    for (int i = lane; i < q1; i += 32) {
+      double v = M[i + j * ldm];
+      s = fma(v, v, s);
+    }
+    s = warp_sum2(s);
+    if (lane == 0) d.nrm[j] = s;
+  }
+  cl.sync();
+  if (q2 < 2 || q1 == 0) return;
+  const int P = q2 + (q2 & 1);
+  for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+    int local = 0;
+    for (int r = 0; r < P - 1; ++r) {
+      for (int pi = gw; pi < P / 2; pi += nw) {
+        int a, b;
+        rr_pair(r, pi, P, a, b);
+        if (a >= q2 || b >= q2) continue;
+        double* ca = M + a * ldm;
+        double* cb = M + b * ldm;
+        const double al = __ldcg(&d.nrm[a]), be = __ldcg(&d.nrm[b]);
+        if (al == 0.0 || be == 0.0) continue;
+        double g = 0.0;
+        for (int i = lane; i < q1; i += 32) g = fma(__ldcg(&ca[i]), __ldcg(&cb[i]), g);
+        g = warp_sum2(g);
+        if (!(fabs(g) > tol * sqrt(al) * sqrt(be))) continue;
+        const double zeta = (be - al) / (2.0 * g);
+        double t;
+        if (fabs(zeta) > 1e100) t = 0.5 / zeta;
+        else t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+        double na = 0.0, nb = 0.0;
+        for (int i = lane; i < q1; i += 32) {
+          double x = __ldcg(&ca[i]), y = __ldcg(&cb[i]);
+          double xn = c * x - sn * y;
+          double yn = sn * x + c * y;
+          ca[i] = xn;
+          cb[i] = yn;
+          na = fma(xn, xn, na);
+          nb = fma(yn, yn, nb);
+        }
+        na = warp_sum2(na);
+        nb = warp_sum2(nb);
+        if (lane == 0) {
+          d.nrm[a] = na;
+          d.nrm[b] = nb;
+        }
+        ++local;
+      }
+      cl.sync();
+    }
+    if (lane == 0 && local) atomicAdd(&d.rot[sweep], local);
+    cl.sync();
+    if (*(volatile int*)&d.rot[sweep] == 0) break;
+  }
+}
+
+cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, const int* devints, double* flops,
+                          int cluster, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cluster, n, 1);
+  cfg.blockDim = dim3(QT, 1, 1);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel, (const JacobiDesc*)d, devints, flops);
+}
+
+}  // namespace hq

@@ -1,0 +1,1399 @@
+// Host side of the hQR library: the device-resident HODLR container, the recursion
+// scheduler of Alg. 2, apply/solve, and the C ABI declared in include/hodlr_qr.h.
+//
+// Scheduling model.  The recursion of Alg. 2 depends only on the cluster tree, never on the
+// ranks, so a factorization is planned once per matrix: the planner walks the recursion and
+// emits a flat list of kernel launches whose descriptors (pointers, capacities and
+// references to ranks kept in device memory) are uploaded once.  Running a factorization
+// replays that list on one stream, and hodlr_qr_graph captures it as a single CUDA graph.
+// Ranks produced by T_eps stay on the device; kernels read them and size nothing on the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/hodlr_qr.h"
+#include "common.cuh"
+
+using namespace hq;
+
+namespace hq {
+cudaError_t launch_gemm_reduce(const GemmDesc* d, const int* rd, int nred, int nblocks,
+                               const int* devints, cudaStream_t s);
+}
+
+// ------------------------------------------------------------------------------- objects
+struct hodlr_ctx {
+  int dev = 0;
+  cudaStream_t own = nullptr;
+  cudaStream_t s = nullptr;
+  int cluster = 8;
+};
+
+enum RecType { R_GEMM, R_REDUCE, R_CONCAT, R_GATHER, R_SCATTER, R_QR, R_JACOBI, R_SELECT, R_COPY,
+               R_FILL, R_IDENT, R_NORM, R_MEMSET_INT, R_TRSM };
+
+struct Rec {
+  int type;
+  int n;          // descriptors
+  size_t off;     // byte offset of the descriptors in the blob
+  int extra0, extra1;
+  double* p0;
+  int* ip;
+  double v;
+  size_t cnt;
+  int i0, i1, i2, i3;
+};
+
+struct Plan {
+  std::vector<Rec> recs;
+  std::vector<char> blob;
+  char* dblob = nullptr;
+  size_t dblob_bytes = 0;
+  // host copies of descriptors needed for launch-time grid sizing live inside blob
+};
+
+struct View {
+  // HODLR storage view: leaves and per-node factor pointers (device), rank refs
+  double* D;
+  int ldl;
+  const std::vector<double*>* U12;
+  const std::vector<double*>* V12;
+  const std::vector<double*>* U21;
+  const std::vector<double*>* V21;
+  int r12_base, r21_base;  // -1 = block absent
+};
+
+struct hodlr_mat {
+  int n = 0, nleaf = 0, levels = 0, kc = 0, ldl = 0, nn = 0;
+  std::vector<int> leaf_sizes, lo, hi;  // per heap node
+  // device storage
+  double* store = nullptr;
+  size_t store_doubles = 0, a_doubles = 0;
+  double* D = nullptr;
+  double* TD = nullptr;
+  std::vector<double*> U12, V12, U21, V21, TU, TV;
+  int* devints = nullptr;
+  int n_devints = 0;
+  double* dscal = nullptr;   // [0] anorm, [1..8] flops
+  int* dstatus = nullptr;
+  double* snapshot = nullptr;
+  int* snap_ints = nullptr;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  // plan of the factorization
+  Plan plan;
+  bool planned = false;
+  double plan_tol = -1, plan_anorm = -2;
+  cudaGraphExec_t gexec = nullptr;
+  double g_tol = -1, g_anorm = -2;
+  bool factored = false;
+};
+
+// ----------------------------------------------------------------------------- planner
+struct Planner {
+  hodlr_mat* M;
+  Plan* P;
+  size_t top = 0, high = 0;      // arena bump pointer
+  char* base;                    // arena base (nullptr in the measuring pass)
+  int int_top;                   // devints bump pointer
+  int int_high;
+  int cluster;
+  double tol;
+
+  template <class T>
+  T* alloc(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    size_t off = top;
+    top += bytes;
+    high = std::max(high, top);
+    return reinterpret_cast<T*>(base + off);
+  }
+  size_t mark() const { return top; }
+  void release(size_t m) { top = m; }
+  int ints(int n) {
+    int r = int_top;
+    int_top += n;
+    int_high = std::max(int_high, int_top);
+    return r;
+  }
+
+  template <class D>
+  size_t put(const std::vector<D>& v) {
+    size_t off = (P->blob.size() + 15) & ~size_t(15);
+    P->blob.resize(off + v.size() * sizeof(D));
+    memcpy(P->blob.data() + off, v.data(), v.size() * sizeof(D));
+    return off;
+  }
+  void rec(int type, int n, size_t off) {
+    Rec r = {};
+    r.type = type;
+    r.n = n;
+    r.off = off;
+    P->recs.push_back(r);
+  }
+
+  // ---------------------------------------------------------------- GEMM batches
+  // Add a batch of GEMMs that may run concurrently (no output overlaps).
+  void gemm(std::vector<GemmDesc> ds) {
+    std::vector<GemmDesc> out;
+    int work = 0;
+    std::vector<int> red;
+    int redblocks = 0;
+    for (auto d : ds) {
+      if (d.m <= 0 || d.n <= 0) continue;
+      d.tiles_m = (d.m + 31) / 32;
+      d.tiles_n = (d.n + 31) / 32;
+      int tiles = d.tiles_m * d.tiles_n;
+      d.ksplit = 1;
+      d.part = nullptr;
+      if (d.k > 768 && tiles < 96) {
+        d.ksplit = std::min(64, std::max(2, d.k / 256));
+        while (d.ksplit > 1 && tiles * d.ksplit > 2048) d.ksplit /= 2;
+      }
+      if (d.ksplit > 1) d.part = alloc<double>((size_t)d.ksplit * d.m * d.n);
+      d.work0 = work;
+      work += tiles * d.ksplit;
+      out.push_back(d);
+    }
+    if (out.empty()) return;
+    size_t off = put(out);
+    rec(R_GEMM, (int)out.size(), off);
+    for (size_t i = 0; i < out.size(); ++i) {
+      if (out[i].ksplit > 1) {
+        red.push_back((int)i);
+        red.push_back(redblocks);
+        redblocks += (out[i].m * out[i].n + 255) / 256;
+      }
+    }
+    if (!red.empty()) {
+      size_t roff = put(red);
+      Rec r = {};
+      r.type = R_REDUCE;
+      r.n = (int)red.size() / 2;
+      r.off = roff;
+      r.extra0 = redblocks;
+      r.extra1 = (int)off;   // offset of the GEMM descriptors
+      P->recs.push_back(r);
+    }
+  }
+
+  static GemmDesc gd(const double* A, int lda, int ta, int mska, const double* B, int ldb, int tb,
+                     int mskb, double* C, int ldc, int m, int mref, int n, int nref, int k, int kref,
+                     double alpha, double beta, int step, int fmode) {
+    GemmDesc d = {};
+    d.A = A; d.lda = lda; d.ta = ta; d.mska = mska;
+    d.B = B; d.ldb = ldb; d.tb = tb; d.mskb = mskb;
+    d.C = C; d.ldc = ldc;
+    d.m = m; d.mref = mref; d.n = n; d.nref = nref; d.k = k; d.kref = kref;
+    d.alpha = alpha; d.beta = beta; d.alpha_ref = nullptr;
+    d.step = step; d.fmode = fmode;
+    return d;
+  }
+
+  // ------------------------------------------------------------------- tree helpers
+  bool is_leaf(int v) const { return v >= M->nleaf - 1; }
+  int m1(int v) const { return M->hi[2 * v + 1] - M->lo[2 * v + 1]; }
+  int m2(int v) const { return M->hi[2 * v + 2] - M->lo[2 * v + 2]; }
+  int size(int v) const { return M->hi[v] - M->lo[v]; }
+  int r12(int v) const { return v; }
+  int r21(int v) const { return M->nn + v; }
+  int rT(int v) const { return 2 * M->nn + v; }
+  void subtree_nodes(int s, std::vector<int>& internal, std::vector<int>& leaves, std::vector<int>& depth) const {
+    std::vector<std::pair<int, int>> st = {{s, 0}};
+    while (!st.empty()) {
+      auto [v, d] = st.back();
+      st.pop_back();
+      if (is_leaf(v)) {
+        leaves.push_back(v);
+      } else {
+        internal.push_back(v);
+        depth.push_back(d);
+        st.push_back({2 * v + 2, d + 1});
+        st.push_back({2 * v + 1, d + 1});
+      }
+    }
+  }
+  // ancestors u (closest first) whose left subtree contains v: their lower blocks' right
+  // factors supply the B_R / C rows of v's compressed column
+  std::vector<int> rowsrc(int v) const {
+    std::vector<int> out;
+    int x = v;
+    while (x > 0) {
+      int p = (x - 1) / 2;
+      if (x == 2 * p + 1) out.push_back(p);
+      x = p;
+    }
+    return out;
+  }
+
+  View aview() const {
+    return View{M->D, M->ldl, &M->U12, &M->V12, &M->U21, &M->V21, 0, M->nn};
+  }
+  View tview() const {
+    return View{M->TD, M->ldl, &M->TU, &M->TV, nullptr, nullptr, 2 * M->nn, -1};
+  }
+
+  // ------------------------------------------------------------- HODLR x block (Table 1)
+  // Y = alpha * op(part(H_s)) X + beta * Y (beta acts on the leaf products; block parts add).
+  // part: 0 full, 1 unit lower, 2 upper.
+  void matvec(const View& H, int s, int part, int trans, const double* X, int ldx, double* Y, int ldy,
+              int pcap, int pref, double alpha, double beta, int step) {
+    const int los = M->lo[s];
+    std::vector<int> internal, leaves, depth;
+    subtree_nodes(s, internal, leaves, depth);
+    const int kc = M->kc;
+    int mask = part == 0 ? kMaskNone : (part == 1 ? kMaskUnitLower : kMaskUpper);
+    int fm = part == 0 ? 0 : 1;
+    std::vector<GemmDesc> lv;
+    for (int v : leaves) {
+      int j = v - (M->nleaf - 1);
+      int w = size(v), off = M->lo[v] - los;
+      lv.push_back(gd(H.D + (size_t)j * H.ldl * H.ldl, H.ldl, trans, mask, X + off, ldx, 0, kMaskNone,
+                      Y + off, ldy, w, -1, pcap, pref, w, -1, alpha, beta, step, fm));
+    }
+    gemm(lv);
+    if (internal.empty()) return;
+    size_t mk = mark();
+    std::vector<GemmDesc> zd;
+    struct Up { GemmDesc d; int depth; };
+    std::vector<Up> ups;
+    for (size_t q = 0; q < internal.size(); ++q) {
+      int u = internal[q];
+      int c1lo = M->lo[2 * u + 1] - los, c2lo = M->lo[2 * u + 2] - los;
+      int a = m1(u), b = m2(u);
+      bool up = (part == 0 || part == 2) && H.r12_base >= 0;
+      bool lo = (part == 0 || part == 1) && H.r21_base >= 0;
+      if (up) {
+        double* Z = alloc<double>((size_t)kc * pcap);
+        int rref = H.r12_base + u;
+        if (!trans) {
+          zd.push_back(gd((*H.V12)[u], b, 1, 0, X + c2lo, ldx, 0, 0, Z, kc, kc, rref, pcap, pref, b, -1, 1.0, 0.0, step, 0));
+          ups.push_back({gd((*H.U12)[u], a, 0, 0, Z, kc, 0, 0, Y + c1lo, ldy, a, -1, pcap, pref, kc, rref, alpha, 1.0, step, 0), depth[q]});
+        } else {
+          zd.push_back(gd((*H.U12)[u], a, 1, 0, X + c1lo, ldx, 0, 0, Z, kc, kc, rref, pcap, pref, a, -1, 1.0, 0.0, step, 0));
+          ups.push_back({gd((*H.V12)[u], b, 0, 0, Z, kc, 0, 0, Y + c2lo, ldy, b, -1, pcap, pref, kc, rref, alpha, 1.0, step, 0), depth[q]});
+        }
+      }
+      if (lo) {
+        double* Z = alloc<double>((size_t)kc * pcap);
+        int rref = H.r21_base + u;
+        if (!trans) {
+          zd.push_back(gd((*H.V21)[u], a, 1, 0, X + c1lo, ldx, 0, 0, Z, kc, kc, rref, pcap, pref, a, -1, 1.0, 0.0, step, 0));
+          ups.push_back({gd((*H.U21)[u], b, 0, 0, Z, kc, 0, 0, Y + c2lo, ldy, b, -1, pcap, pref, kc, rref, alpha, 1.0, step, 0), depth[q]});
+        } else {
+          zd.push_back(gd((*H.U21)[u], b, 1, 0, X + c2lo, ldx, 0, 0, Z, kc, kc, rref, pcap, pref, b, -1, 1.0, 0.0, step, 0));
+          ups.push_back({gd((*H.V21)[u], a, 0, 0, Z, kc, 0, 0, Y + c1lo, ldy, a, -1, pcap, pref, kc, rref, alpha, 1.0, step, 0), depth[q]});
+        }
+      }
+    }
+    gemm(zd);
+    int maxd = 0;
+    for (auto& u : ups) maxd = std::max(maxd, u.depth);
+    for (int dd = 0; dd <= maxd; ++dd) {
+      std::vector<GemmDesc> g;
+      for (auto& u : ups)
+        if (u.depth == dd) g.push_back(u.d);
+      gemm(g);
+    }
+    release(mk);
+  }
+
+  // ---------------------------------------------------------------- T_eps (Sec. 2.1.1)
+  struct Trunc {
+    int nL, nR;
+    std::vector<ConcatSeg> L, R;
+    double thr;
+    const double* thr_ref;
+    double* Uout; int ldu;
+    double* Vout; int ldv;
+    int kout_ref;
+    int step;
+  };
+  static ConcatSeg seg(const double* src, int lds, int cols, int colsref, double alpha) {
+    ConcatSeg g;
+    g.src = src; g.lds = lds; g.cols = cols; g.colsref = colsref; g.alpha = alpha;
+    return g;
+  }
+
+  void truncate(std::vector<Trunc>& ps) {
+    if (ps.empty()) return;
+    size_t mk = mark();
+    const int kc = M->kc;
+    int np = (int)ps.size();
+    std::vector<ConcatDesc> cds;
+    std::vector<QRDesc> qds;
+    std::vector<GemmDesc> gM, gP1, gZ, gP2, gP3, gF;
+    std::vector<JacobiDesc> jds;
+    std::vector<SelectDesc> sds;
+    std::vector<CopyDesc> cps;
+    for (auto& p : ps) {
+      int Kcap = 0;
+      for (auto& g : p.L) Kcap += g.cols;
+      int KcapR = 0;
+      for (auto& g : p.R) KcapR += g.cols;
+      Kcap = std::max(Kcap, KcapR);
+      if (Kcap == 0) Kcap = 1;
+      int q1c = std::min(p.nL, Kcap), q2c = std::min(p.nR, Kcap);
+      double* Lb = alloc<double>((size_t)p.nL * Kcap);
+      double* Rb = alloc<double>((size_t)p.nR * Kcap);
+      double* tauL = alloc<double>(Kcap);
+      double* tauR = alloc<double>(Kcap);
+      double* TL = alloc<double>((size_t)q1c * q1c);
+      double* TR = alloc<double>((size_t)q2c * q2c);
+      double* GL = alloc<double>((size_t)q1c * q1c);
+      double* GR = alloc<double>((size_t)q2c * q2c);
+      double* Mb = alloc<double>((size_t)q1c * q2c);
+      double* nrm = alloc<double>(q2c);
+      int* rot = alloc<int>(kMaxSweeps);
+      double* Uk = alloc<double>((size_t)q1c * kc);
+      double* P1 = alloc<double>((size_t)Kcap * kc);
+      double* Zb = alloc<double>((size_t)q2c * kc);
+      double* P2 = alloc<double>((size_t)q1c * kc);
+      double* P3 = alloc<double>((size_t)q1c * kc);
+      double* P2r = alloc<double>((size_t)q2c * kc);
+      double* P3r = alloc<double>((size_t)q2c * kc);
+      int iL = ints(2), iR = ints(2);   // (K, q) for each side
+      int kref = p.kout_ref;
+      ConcatDesc c = {};
+      c.dst = Lb; c.ldd = p.nL; c.rows = p.nL; c.cap = Kcap; c.nseg = (int)p.L.size();
+      for (int i = 0; i < c.nseg; ++i) c.seg[i] = p.L[i];
+      c.kout_ref = iL;
+      cds.push_back(c);
+      c = {};
+      c.dst = Rb; c.ldd = p.nR; c.rows = p.nR; c.cap = Kcap; c.nseg = (int)p.R.size();
+      for (int i = 0; i < c.nseg; ++i) c.seg[i] = p.R[i];
+      c.kout_ref = iR;
+      cds.push_back(c);
+      QRDesc q = {};
+      q.A = Lb; q.lda = p.nL; q.h = p.nL; q.w = Kcap; q.href = -1; q.wref = iL;
+      q.tau = tauL; q.T = TL; q.ldt = q1c; q.G = GL; q.ldg = q1c; q.step = kStepNone; q.fmode = 1;
+      qds.push_back(q);
+      q.A = Rb; q.lda = p.nR; q.h = p.nR; q.wref = iR; q.tau = tauR; q.T = TR; q.ldt = q2c; q.G = GR; q.ldg = q2c;
+      qds.push_back(q);
+      // M = R1 R2^T  (q1 x q2)
+      gM.push_back(gd(Lb, p.nL, 0, kMaskUpper, Rb, p.nR, 1, kMaskUpper, Mb, q1c, q1c, iL + 1, q2c, iR + 1,
+                      Kcap, iL, 1.0, 0.0, kStepNone, -1));
+      JacobiDesc jd = {};
+      jd.M = Mb; jd.ldm = q1c; jd.q1 = q1c; jd.q2 = q2c; jd.q1ref = iL + 1; jd.q2ref = iR + 1;
+      jd.nrm = nrm; jd.rot = rot;
+      jds.push_back(jd);
+      SelectDesc sd = {};
+      sd.W = Mb; sd.ldw = q1c; sd.nrm = nrm; sd.q1 = q1c; sd.q2 = q2c; sd.q1ref = iL + 1; sd.q2ref = iR + 1;
+      sd.thr = p.thr; sd.thr_ref = p.thr_ref; sd.U = Uk; sd.ldu = q1c; sd.kcap = kc; sd.kref = kref;
+      sd.status = M->dstatus; sd.nL = p.nL; sd.nR = p.nR; sd.Kref = iL; sd.step = p.step;
+      sds.push_back(sd);
+      // Z = R2 (R1^T Uk)
+      gP1.push_back(gd(Lb, p.nL, 1, kMaskUpper, Uk, q1c, 0, 0, P1, Kcap, Kcap, iL, kc, kref, q1c, iL + 1, 1.0, 0.0, kStepNone, -1));
+      gZ.push_back(gd(Rb, p.nR, 0, kMaskUpper, P1, Kcap, 0, 0, Zb, q2c, q2c, iR + 1, kc, kref, Kcap, iR, 1.0, 0.0, kStepNone, -1));
+      // outputs: Q1 [Uk; 0] and Q2 [Z; 0] with Q = I - Y T Y^T
+      CopyDesc cp = {};
+      cp.src = Uk; cp.lds = q1c; cp.dst = p.Uout; cp.ldd = p.ldu; cp.rows = p.nL; cp.rows_src = q1c;
+      cp.rows_src_ref = iL + 1; cp.cols = kc; cp.colsref = kref; cp.alpha = 1.0;
+      cps.push_back(cp);
+      cp.src = Zb; cp.lds = q2c; cp.dst = p.Vout; cp.ldd = p.ldv; cp.rows = p.nR; cp.rows_src = q2c;
+      cp.rows_src_ref = iR + 1;
+      cps.push_back(cp);
+      gP2.push_back(gd(Lb, p.nL, 1, kMaskUnitLower, Uk, q1c, 0, 0, P2, q1c, q1c, iL + 1, kc, kref, q1c, iL + 1, 1.0, 0.0, kStepNone, -1));
+      gP2.push_back(gd(Rb, p.nR, 1, kMaskUnitLower, Zb, q2c, 0, 0, P2r, q2c, q2c, iR + 1, kc, kref, q2c, iR + 1, 1.0, 0.0, kStepNone, -1));
+      gP3.push_back(gd(TL, q1c, 0, kMaskUpper, P2, q1c, 0, 0, P3, q1c, q1c, iL + 1, kc, kref, q1c, iL + 1, 1.0, 0.0, kStepNone, -1));
+      gP3.push_back(gd(TR, q2c, 0, kMaskUpper, P2r, q2c, 0, 0, P3r, q2c, q2c, iR + 1, kc, kref, q2c, iR + 1, 1.0, 0.0, kStepNone, -1));
+      gF.push_back(gd(Lb, p.nL, 0, kMaskUnitLower, P3, q1c, 0, 0, p.Uout, p.ldu, p.nL, -1, kc, kref, q1c, iL + 1, -1.0, 1.0, kStepNone, -1));
+      gF.push_back(gd(Rb, p.nR, 0, kMaskUnitLower, P3r, q2c, 0, 0, p.Vout, p.ldv, p.nR, -1, kc, kref, q2c, iR + 1, -1.0, 1.0, kStepNone, -1));
+    }
+    rec(R_CONCAT, (int)cds.size(), put(cds));
+    rec(R_QR, (int)qds.size(), put(qds));
+    gemm(gM);
+    rec(R_JACOBI, (int)jds.size(), put(jds));
+    rec(R_SELECT, (int)sds.size(), put(sds));
+    gemm(gP1);
+    gemm(gZ);
+    rec(R_COPY, (int)cps.size(), put(cps));
+    gemm(gP2);
+    gemm(gP3);
+    gemm(gF);
+    (void)np;
+    release(mk);
+  }
+
+  // --------------------------------------------------------- left-orthogonal form (Sec. 2.1)
+  void left_orth(int p) {
+    size_t mk = mark();
+    const int kc = M->kc;
+    int a = m1(p), b = m2(p);          // U21: b x r, V21: a x r
+    int rr = r21(p);
+    double* S = alloc<double>((size_t)b * kc);
+    double* Vt = alloc<double>((size_t)a * kc);
+    int kq = std::min(b, kc);
+    double* tau = alloc<double>(kc);
+    double* T = alloc<double>((size_t)kq * kq);
+    double* G = alloc<double>((size_t)kq * kq);
+    double* P2 = alloc<double>((size_t)kc * kc);
+    double* P3 = alloc<double>((size_t)kc * kc);
+    std::vector<CopyDesc> cps(2);
+    cps[0] = {}; cps[0].src = M->U21[p]; cps[0].lds = b; cps[0].dst = S; cps[0].ldd = b; cps[0].rows = b;
+    cps[0].rows_src = b; cps[0].rows_src_ref = -1; cps[0].cols = kc; cps[0].colsref = rr; cps[0].alpha = 1.0;
+    cps[1] = {}; cps[1].src = M->V21[p]; cps[1].lds = a; cps[1].dst = Vt; cps[1].ldd = a; cps[1].rows = a;
+    cps[1].rows_src = a; cps[1].rows_src_ref = -1; cps[1].cols = kc; cps[1].colsref = rr; cps[1].alpha = 1.0;
+    rec(R_COPY, 2, put(cps));
+    QRDesc q = {};
+    q.A = S; q.lda = b; q.h = b; q.w = kc; q.href = -1; q.wref = rr; q.tau = tau; q.T = T; q.ldt = kq;
+    q.G = G; q.ldg = kq; q.step = kStepLeftOrth; q.fmode = 1;
+    rec(R_QR, 1, put(std::vector<QRDesc>{q}));
+    // U21 <- Q = (I - Y T Y^T) [I; 0]
+    Rec ri = {};
+    ri.type = R_IDENT; ri.p0 = M->U21[p]; ri.i0 = b; ri.i1 = b; ri.i2 = kc;
+    P->recs.push_back(ri);
+    gemm({gd(S, b, 1, kMaskUnitLower, M->U21[p], b, 0, 0, P2, kc, kc, rr, kc, rr, kc, rr, 1.0, 0.0, kStepNone, -1)});
+    gemm({gd(T, kq, 0, kMaskUpper, P2, kc, 0, 0, P3, kc, kq, rr, kc, rr, kq, rr, 1.0, 0.0, kStepNone, -1)});
+    gemm({gd(S, b, 0, kMaskUnitLower, P3, kc, 0, 0, M->U21[p], b, b, -1, kc, rr, kq, rr, -1.0, 1.0, kStepNone, -1),
+          // V21 <- V21 R^T  (B_R <- R B_R)
+          gd(Vt, a, 0, 0, S, b, 1, kMaskUpper, M->V21[p], a, a, -1, kc, rr, kc, rr, 1.0, 0.0, kStepLeftOrth, 0)});
+    release(mk);
+  }
+
+  // ------------------------------------------------------ lowest level of Alg. 2 at a leaf
+  void leaf(int v) {
+    size_t mk = mark();
+    const int kc = M->kc;
+    int j = v - (M->nleaf - 1);
+    int w = size(v);
+    std::vector<int> rs = rowsrc(v);
+    int hcap = w + (int)rs.size() * kc;
+    double* Pn = alloc<double>((size_t)hcap * w);
+    double* tau = alloc<double>(w);
+    double* G = alloc<double>((size_t)w * w);
+    int href = ints(1);
+    PanelDesc pd = {};
+    pd.D = M->D + (size_t)j * M->ldl * M->ldl; pd.ldD = M->ldl; pd.w = w; pd.P = Pn; pd.ldP = hcap;
+    pd.nsrc = (int)rs.size();
+    for (size_t i = 0; i < rs.size(); ++i) {
+      int u = rs[i];
+      int off = M->lo[v] - M->lo[2 * u + 1];
+      pd.src[i] = M->V21[u] + off;
+      pd.lds[i] = m1(u);
+      pd.rref[i] = r21(u);
+      pd.rcap[i] = kc;
+    }
+    pd.href = href;
+    rec(R_GATHER, 1, put(std::vector<PanelDesc>{pd}));
+    QRDesc q = {};
+    q.A = Pn; q.lda = hcap; q.h = hcap; q.w = w; q.href = href; q.wref = -1; q.tau = tau;
+    q.T = M->TD + (size_t)j * M->ldl * M->ldl; q.ldt = M->ldl; q.G = G; q.ldg = w;
+    q.step = kStepLeafQR; q.fmode = 0;
+    rec(R_QR, 1, put(std::vector<QRDesc>{q}));
+    rec(R_SCATTER, 1, put(std::vector<PanelDesc>{pd}));
+    release(mk);
+  }
+
+  // ----------------------------------------------------------------- Alg. 2 recursion
+  void node(int v) {
+    if (v != 0 && v == 2 * ((v - 1) / 2) + 1) left_orth((v - 1) / 2);   // B of v is A21 of its parent
+    if (is_leaf(v)) {
+      leaf(v);
+      return;
+    }
+    const int kc = M->kc;
+    const int c1 = 2 * v + 1, c2 = 2 * v + 2;
+    const int a = m1(v), b = m2(v);
+    node(c1);
+    View A = aview(), T = tview();
+    std::vector<int> rs = rowsrc(v);
+    const double* anorm = M->dscal;
+    size_t mk = mark();
+    // S~ = T_{eps ||A||}( Y11^T A12 + Y21^T A22 + Y_BR1^T B_R2 + Y_C1^T C2 )
+    double* X1 = alloc<double>((size_t)a * kc);
+    double* X2 = alloc<double>((size_t)b * kc);
+    matvec(A, c1, 1, 1, M->U12[v], a, X1, a, kc, r12(v), 1.0, 0.0, kStepS);
+    matvec(A, c2, 0, 1, M->U21[v], b, X2, b, kc, r21(v), 1.0, 0.0, kStepS);
+    double* SL = alloc<double>((size_t)a * kc);
+    double* SR = alloc<double>((size_t)b * kc);
+    int kS = ints(1);
+    {
+      Trunc t;
+      t.nL = a; t.nR = b;
+      t.L = {seg(X1, a, kc, r12(v), 1.0), seg(M->V21[v], a, kc, r21(v), 1.0)};
+      t.R = {seg(M->V12[v], b, kc, r12(v), 1.0), seg(X2, b, kc, r21(v), 1.0)};
+      for (int u : rs) {
+        int off = M->lo[v] - M->lo[2 * u + 1];
+        t.L.push_back(seg(M->V21[u] + off, m1(u), kc, r21(u), 1.0));
+        t.R.push_back(seg(M->V21[u] + off + a, m1(u), kc, r21(u), 1.0));
+      }
+      t.thr = tol; t.thr_ref = anorm; t.Uout = SL; t.ldu = a; t.Vout = SR; t.ldv = b; t.kout_ref = kS;
+      t.step = kStepS;
+      std::vector<Trunc> ts = {t};
+      truncate(ts);
+    }
+    // S = T1^T S~
+    double* SL2 = alloc<double>((size_t)a * kc);
+    matvec(T, c1, 2, 1, SL, a, SL2, a, kc, kS, 1.0, 0.0, kStepTS);
+    // A^12 = T_{eps ||A||}(A12 - Y11 S)
+    double* X3 = alloc<double>((size_t)a * kc);
+    matvec(A, c1, 1, 0, SL2, a, X3, a, kc, kS, 1.0, 0.0, kStepUpdate);
+    {
+      Trunc t;
+      t.nL = a; t.nR = b;
+      t.L = {seg(M->U12[v], a, kc, r12(v), 1.0), seg(X3, a, kc, kS, -1.0)};
+      t.R = {seg(M->V12[v], b, kc, r12(v), 1.0), seg(SR, b, kc, kS, 1.0)};
+      t.thr = tol; t.thr_ref = anorm; t.Uout = M->U12[v]; t.ldu = a; t.Vout = M->V12[v]; t.ldv = b;
+      t.kout_ref = r12(v); t.step = kStepUpdate;
+      std::vector<Trunc> ts = {t};
+      truncate(ts);
+    }
+    // A^22 = A~22 -_H (B_L21 (Y~_B S_L)) S_R^T
+    double* Pm = alloc<double>((size_t)kc * kc);
+    double* Uu = alloc<double>((size_t)b * kc);
+    gemm({gd(M->V21[v], a, 1, 0, SL2, a, 0, 0, Pm, kc, kc, r21(v), kc, kS, a, -1, 1.0, 0.0, kStepUpdate, 0)});
+    gemm({gd(M->U21[v], b, 0, 0, Pm, kc, 0, 0, Uu, b, b, -1, kc, kS, kc, r21(v), 1.0, 0.0, kStepUpdate, 0)});
+    lr_update(c2, Uu, b, SR, b, kS);
+    // B^_R2 = B_R2 - Y_BR1 S,  C^2 = C2 - Y_C1 S   (rows stored transposed in ancestors' V21)
+    if (!rs.empty()) {
+      std::vector<GemmDesc> g1, g2;
+      for (int u : rs) {
+        int off = M->lo[v] - M->lo[2 * u + 1];
+        double* Pu = alloc<double>((size_t)kc * kc);
+        g1.push_back(gd(SL2, a, 1, 0, M->V21[u] + off, m1(u), 0, 0, Pu, kc, kc, kS, kc, r21(u), a, -1, 1.0, 0.0, kStepUpdate, 0));
+        g2.push_back(gd(SR, b, 0, 0, Pu, kc, 0, 0, M->V21[u] + off + a, m1(u), b, -1, kc, r21(u), kc, kS, -1.0, 1.0, kStepUpdate, 0));
+      }
+      gemm(g1);
+      gemm(g2);
+    }
+    release(mk);
+    node(c2);
+    mk = mark();
+    // T~12 = T_eps( Y21^T Y22 + Y_BR1^T Y_BR2 + Y_C1^T Y_C2 ),  T12 = -T1 T~12 T2
+    double* X4 = alloc<double>((size_t)b * kc);
+    matvec(A, c2, 1, 1, M->U21[v], b, X4, b, kc, r21(v), 1.0, 0.0, kStepT12);
+    double* TLb = alloc<double>((size_t)a * kc);
+    double* TRb = alloc<double>((size_t)b * kc);
+    {
+      Trunc t;
+      t.nL = a; t.nR = b;
+      t.L = {seg(M->V21[v], a, kc, r21(v), 1.0)};
+      t.R = {seg(X4, b, kc, r21(v), 1.0)};
+      for (int u : rs) {
+        int off = M->lo[v] - M->lo[2 * u + 1];
+        t.L.push_back(seg(M->V21[u] + off, m1(u), kc, r21(u), 1.0));
+        t.R.push_back(seg(M->V21[u] + off + a, m1(u), kc, r21(u), 1.0));
+      }
+      t.thr = tol; t.thr_ref = nullptr; t.Uout = TLb; t.ldu = a; t.Vout = TRb; t.ldv = b; t.kout_ref = rT(v);
+      t.step = kStepT12;
+      std::vector<Trunc> ts = {t};
+      truncate(ts);
+    }
+    matvec(T, c1, 2, 0, TLb, a, M->TU[v], a, kc, rT(v), -1.0, 0.0, kStepT12);
+    matvec(T, c2, 2, 1, TRb, b, M->TV[v], b, kc, rT(v), 1.0, 0.0, kStepT12);
+    release(mk);
+  }
+
+  // HODLR low-rank update  H_s <- H_s -_H U V^T  (Table 1)
+  void lr_update(int s, const double* U, int ldu, const double* V, int ldv, int kref) {
+    const int kc = M->kc;
+    std::vector<int> internal, leaves, depth;
+    subtree_nodes(s, internal, leaves, depth);
+    const int los = M->lo[s];
+    std::vector<GemmDesc> g;
+    for (int v : leaves) {
+      int j = v - (M->nleaf - 1);
+      int w = size(v), off = M->lo[v] - los;
+      g.push_back(gd(U + off, ldu, 0, 0, V + off, ldv, 1, 0, M->D + (size_t)j * M->ldl * M->ldl, M->ldl,
+                     w, -1, w, -1, kc, kref, -1.0, 1.0, kStepUpdate, 0));
+    }
+    gemm(g);
+    std::vector<Trunc> ts;
+    for (int u : internal) {
+      int a = m1(u), b = m2(u);
+      int c1lo = M->lo[2 * u + 1] - los, c2lo = M->lo[2 * u + 2] - los;
+      Trunc t;
+      t.nL = a; t.nR = b;
+      t.L = {seg(M->U12[u], a, kc, r12(u), 1.0), seg(U + c1lo, ldu, kc, kref, -1.0)};
+      t.R = {seg(M->V12[u], b, kc, r12(u), 1.0), seg(V + c2lo, ldv, kc, kref, 1.0)};
+      t.thr = tol; t.thr_ref = M->dscal; t.Uout = M->U12[u]; t.ldu = a; t.Vout = M->V12[u]; t.ldv = b;
+      t.kout_ref = r12(u); t.step = kStepUpdate;
+      ts.push_back(t);
+      Trunc t2;
+      t2.nL = b; t2.nR = a;
+      t2.L = {seg(M->U21[u], b, kc, r21(u), 1.0), seg(U + c2lo, ldu, kc, kref, -1.0)};
+      t2.R = {seg(M->V21[u], a, kc, r21(u), 1.0), seg(V + c1lo, ldv, kc, kref, 1.0)};
+      t2.thr = tol; t2.thr_ref = M->dscal; t2.Uout = M->U21[u]; t2.ldu = b; t2.Vout = M->V21[u]; t2.ldv = a;
+      t2.kout_ref = r21(u); t2.step = kStepUpdate;
+      ts.push_back(t2);
+    }
+    truncate(ts);
+  }
+
+  // ||A||_2 by power iteration on A^T A (device), result into dscal[0]
+  void norm_estimate(int iters) {
+    size_t mk = mark();
+    const int n = M->n;
+    double* x = alloc<double>(n);
+    double* y = alloc<double>(n);
+    double* z = alloc<double>(n);
+    double* tmp = alloc<double>(1);
+    Rec f = {};
+    f.type = R_FILL; f.p0 = x; f.cnt = n; f.v = 1.0 / std::sqrt((double)n);
+    P->recs.push_back(f);
+    View A = aview();
+    for (int it = 0; it < iters; ++it) {
+      matvec(A, 0, 0, 0, x, n, y, n, 1, -1, 1.0, 0.0, kStepNorm);
+      matvec(A, 0, 0, 1, y, n, z, n, 1, -1, 1.0, 0.0, kStepNorm);
+      Rec r = {};
+      r.type = R_NORM; r.p0 = z; r.i0 = n; r.i1 = 0; r.ip = reinterpret_cast<int*>(tmp);
+      P->recs.push_back(r);
+      std::swap(x, z);
+    }
+    matvec(A, 0, 0, 0, x, n, y, n, 1, -1, 1.0, 0.0, kStepNorm);
+    Rec r = {};
+    r.type = R_NORM; r.p0 = y; r.i0 = n; r.i1 = 1; r.ip = reinterpret_cast<int*>(M->dscal);
+    P->recs.push_back(r);
+    release(mk);
+  }
+};
+
+// ------------------------------------------------------------------------------ executor
+// kernel kind of a record (profiling): 0 GEMM, 1 reduce, 2 QR, 3 Jacobi, 4 select,
+// 5 data movement, 6 norm, 7 other, -1 not a kernel
+static int rec_kind(int t) {
+  switch (t) {
+    case R_GEMM: return 0;
+    case R_REDUCE: return 1;
+    case R_QR: return 2;
+    case R_JACOBI: return 3;
+    case R_SELECT: return 4;
+    case R_CONCAT: case R_GATHER: case R_SCATTER: case R_COPY: case R_IDENT: case R_FILL: return 5;
+    case R_NORM: return 6;
+    case R_TRSM: return 7;
+    default: return -1;
+  }
+}
+
+struct Profiler {
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kind;
+};
+
+static int run_plan(hodlr_ctx* ctx, hodlr_mat* M, Plan& P, Profiler* prof = nullptr) {
+  cudaStream_t s = ctx->s;
+  char* db = P.dblob;
+  double* flops = M->dscal + 1;
+  for (const Rec& r : P.recs) {
+    int kd = rec_kind(r.type);
+    if (prof && kd >= 0) {
+      cudaEvent_t e0;
+      cudaEventCreate(&e0);
+      cudaEventRecord(e0, s);
+      prof->ev.push_back(e0);
+      prof->kind.push_back(kd);
+    }
+    const char* hb = P.blob.data() + r.off;
+    char* dp = db + r.off;
+    cudaError_t e = cudaSuccess;
+    switch (r.type) {
+      case R_GEMM:
+        e = launch_gemm((GemmDesc*)hb, r.n, (GemmDesc*)dp, M->devints, flops, s);
+        break;
+      case R_REDUCE:
+        e = launch_gemm_reduce((const GemmDesc*)(db + r.extra1), (const int*)dp, r.n, r.extra0, M->devints, s);
+        break;
+      case R_CONCAT: e = launch_concat((const ConcatDesc*)hb, r.n, (ConcatDesc*)dp, M->devints, s); break;
+      case R_GATHER: e = launch_panel_gather((const PanelDesc*)hb, r.n, (PanelDesc*)dp, M->devints, s); break;
+      case R_SCATTER: e = launch_panel_scatter((const PanelDesc*)hb, r.n, (PanelDesc*)dp, M->devints, s); break;
+      case R_QR: e = launch_qr((const QRDesc*)hb, r.n, (QRDesc*)dp, M->devints, flops, ctx->cluster, s); break;
+      case R_JACOBI: e = launch_jacobi((const JacobiDesc*)hb, r.n, (JacobiDesc*)dp, M->devints, flops, ctx->cluster, s); break;
+      case R_SELECT: e = launch_select((const SelectDesc*)hb, r.n, (SelectDesc*)dp, M->devints, flops, s); break;
+      case R_COPY: e = launch_copy((const CopyDesc*)hb, r.n, (CopyDesc*)dp, M->devints, s); break;
+      case R_FILL: e = launch_fill(r.p0, r.cnt, r.v, s); break;
+      case R_IDENT: e = launch_set_diag_identity(r.p0, r.i0, r.i1, r.i2, s); break;
+      case R_NORM: e = launch_norm_scale(r.p0, r.i0, reinterpret_cast<double*>(r.ip), r.i1, s); break;
+      case R_MEMSET_INT: e = cudaMemsetAsync(r.ip, 0, r.cnt, s); break;
+      case R_TRSM: e = launch_trsm_leaf(r.p0, r.i0, r.i1, reinterpret_cast<double*>(r.ip), r.i2, r.i3, s); break;
+      default: e = cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, __FILE__, __LINE__);
+    if (prof && kd >= 0) {
+      cudaEvent_t e1;
+      cudaEventCreate(&e1);
+      cudaEventRecord(e1, s);
+      prof->ev.push_back(e1);
+    }
+  }
+  return HODLR_OK;
+}
+
+static int upload_plan(Plan& P) {
+  if (P.dblob) cudaFree(P.dblob);
+  P.dblob = nullptr;
+  P.dblob_bytes = std::max<size_t>(P.blob.size(), 16);
+  HQ_CUDA_OK(cudaMalloc(&P.dblob, P.dblob_bytes));
+  if (!P.blob.empty()) HQ_CUDA_OK(cudaMemcpy(P.dblob, P.blob.data(), P.blob.size(), cudaMemcpyHostToDevice));
+  return HODLR_OK;
+}
+
+// Build the factorization plan: measure the arena, allocate it, plan again for real.
+template <class F>
+static int build_plan(hodlr_mat* M, Plan& P, int cluster, double tol, F&& body) {
+  for (int pass = 0; pass < 2; ++pass) {
+    P.recs.clear();
+    P.blob.clear();
+    Planner pl;
+    pl.M = M; pl.P = &P; pl.base = pass == 0 ? nullptr : M->arena;
+    pl.int_top = 3 * M->nn; pl.int_high = pl.int_top;
+    pl.cluster = cluster; pl.tol = tol;
+    body(pl);
+    if (pl.int_high > M->n_devints) return HODLR_ENOMEM;
+    if (pass == 0) {
+      size_t need = pl.high + 4096;
+      if (need > M->arena_bytes) {
+        if (M->arena) cudaFree(M->arena);
+        M->arena = nullptr;
+        M->arena_bytes = 0;
+        if (cudaMalloc(&M->arena, need) != cudaSuccess) {
+          cudaGetLastError();
+          return HODLR_ENOMEM;
+        }
+        M->arena_bytes = need;
+      }
+    }
+  }
+  return upload_plan(P);
+}
+
+static void free_plan(Plan& P) {
+  if (P.dblob) cudaFree(P.dblob);
+  P.dblob = nullptr;
+  P.recs.clear();
+  P.blob.clear();
+}
+
+// =============================================================================== C ABI
+extern "C" {
+
+const char* hodlr_strerror(int code) {
+  switch (code) {
+    case HODLR_OK: return "ok";
+    case HODLR_EINVAL: return "invalid argument";
+    case HODLR_ENOMEM: return "out of memory";
+    case HODLR_ERANK: return "rank capacity exceeded (result truncated)";
+    case HODLR_ESINGULAR: return "singular triangular factor";
+    case HODLR_ETIMEOUT: return "device wait timed out";
+    case HODLR_ECUDA: return "CUDA error";
+    case HODLR_ESTATE: return "invalid state";
+    default: return "unknown error";
+  }
+}
+
+int hodlr_ctx_create(int device, hodlr_ctx** out) {
+  if (!out) return HODLR_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return HODLR_EINVAL;
+  }
+  HQ_CUDA_OK(cudaSetDevice(device));
+  hodlr_ctx* c = new (std::nothrow) hodlr_ctx();
+  if (!c) return HODLR_ENOMEM;
+  c->dev = device;
+  if (cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return HODLR_ECUDA;
+  }
+  c->s = c->own;
+  int cl = qr_max_cluster();
+  const char* env = getenv("HODLR_CLUSTER");
+  if (env) cl = std::max(1, std::min(16, atoi(env)));
+  c->cluster = cl;
+  *out = c;
+  return HODLR_OK;
+}
+
+void hodlr_ctx_destroy(hodlr_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->dev);
+  if (ctx->own) {
+    cudaStreamSynchronize(ctx->own);
+    cudaStreamDestroy(ctx->own);
+  }
+  delete ctx;
+}
+
+int hodlr_ctx_set_stream(hodlr_ctx* ctx, void* stream) {
+  if (!ctx) return HODLR_EINVAL;
+  ctx->s = stream ? (cudaStream_t)stream : ctx->own;
+  return HODLR_OK;
+}
+
+int hodlr_sync(hodlr_ctx* ctx) {
+  if (!ctx) return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaStreamSynchronize(ctx->s));
+  return HODLR_OK;
+}
+
+static int upload_values(hodlr_ctx* ctx, hodlr_mat* M, const double* const* leaves,
+                         const double* const* U12, const double* const* V12, const int* r12,
+                         const double* const* U21, const double* const* V21, const int* r21) {
+  for (int v = 0; v < M->nn; ++v) {
+    int a = M->hi[2 * v + 1] - M->lo[2 * v + 1], b = M->hi[2 * v + 2] - M->lo[2 * v + 2];
+    if (r12[v] < 0 || r21[v] < 0 || r12[v] > M->kc || r21[v] > M->kc || r12[v] > std::min(a, b) ||
+        r21[v] > std::min(a, b))
+      return HODLR_EINVAL;
+    if ((r12[v] && (!U12 || !V12 || !U12[v] || !V12[v])) || (r21[v] && (!U21 || !V21 || !U21[v] || !V21[v])))
+      return HODLR_EINVAL;
+  }
+  for (int j = 0; j < M->nleaf; ++j)
+    if (!leaves || !leaves[j]) return HODLR_EINVAL;
+  cudaStream_t s = ctx->s;
+  for (int j = 0; j < M->nleaf; ++j) {
+    int w = M->leaf_sizes[j];
+    HQ_CUDA_OK(cudaMemcpy2DAsync(M->D + (size_t)j * M->ldl * M->ldl, sizeof(double) * M->ldl, leaves[j],
+                                 sizeof(double) * w, sizeof(double) * w, w, cudaMemcpyHostToDevice, s));
+  }
+  for (int v = 0; v < M->nn; ++v) {
+    int a = M->hi[2 * v + 1] - M->lo[2 * v + 1], b = M->hi[2 * v + 2] - M->lo[2 * v + 2];
+    if (r12[v]) {
+      HQ_CUDA_OK(cudaMemcpyAsync(M->U12[v], U12[v], sizeof(double) * a * r12[v], cudaMemcpyHostToDevice, s));
+      HQ_CUDA_OK(cudaMemcpyAsync(M->V12[v], V12[v], sizeof(double) * b * r12[v], cudaMemcpyHostToDevice, s));
+    }
+    if (r21[v]) {
+      HQ_CUDA_OK(cudaMemcpyAsync(M->U21[v], U21[v], sizeof(double) * b * r21[v], cudaMemcpyHostToDevice, s));
+      HQ_CUDA_OK(cudaMemcpyAsync(M->V21[v], V21[v], sizeof(double) * a * r21[v], cudaMemcpyHostToDevice, s));
+    }
+  }
+  std::vector<int> ranks(3 * M->nn, 0);
+  for (int v = 0; v < M->nn; ++v) {
+    ranks[v] = r12[v];
+    ranks[M->nn + v] = r21[v];
+  }
+  if (M->nn) {
+    HQ_CUDA_OK(cudaMemcpyAsync(M->devints, ranks.data(), sizeof(int) * 3 * M->nn, cudaMemcpyHostToDevice, s));
+  }
+  HQ_CUDA_OK(cudaStreamSynchronize(s));
+  M->factored = false;
+  return HODLR_OK;
+}
+
+void hodlr_free(hodlr_mat* M) {
+  if (!M) return;
+  if (M->gexec) cudaGraphExecDestroy(M->gexec);
+  free_plan(M->plan);
+  cudaFree(M->store);
+  cudaFree(M->devints);
+  cudaFree(M->dscal);
+  cudaFree(M->dstatus);
+  if (M->snapshot) cudaFree(M->snapshot);
+  if (M->snap_ints) cudaFree(M->snap_ints);
+  if (M->arena) cudaFree(M->arena);
+  delete M;
+}
+
+int hodlr_build(hodlr_ctx* ctx, int n, int nleaf, const int* leaf_sizes, const double* const* leaves,
+                const double* const* U12, const double* const* V12, const int* r12,
+                const double* const* U21, const double* const* V21, const int* r21, int rank_cap,
+                hodlr_mat** out) {
+  if (!ctx || !out || !leaf_sizes || n <= 0 || nleaf <= 0 || (nleaf & (nleaf - 1)) || rank_cap < 1 ||
+      rank_cap > 256)
+    return HODLR_EINVAL;
+  if (nleaf > 1 && (!r12 || !r21)) return HODLR_EINVAL;
+  long sum = 0;
+  int maxw = 0;
+  for (int j = 0; j < nleaf; ++j) {
+    if (leaf_sizes[j] <= 0 || leaf_sizes[j] > 4096) return HODLR_EINVAL;
+    sum += leaf_sizes[j];
+    maxw = std::max(maxw, leaf_sizes[j]);
+  }
+  if (sum != n) return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  hodlr_mat* M = new (std::nothrow) hodlr_mat();
+  if (!M) return HODLR_ENOMEM;
+  M->n = n; M->nleaf = nleaf; M->kc = rank_cap; M->ldl = maxw; M->nn = nleaf - 1;
+  int lev = 0;
+  while ((1 << lev) < nleaf) ++lev;
+  M->levels = lev;
+  M->leaf_sizes.assign(leaf_sizes, leaf_sizes + nleaf);
+  int nnodes = 2 * nleaf - 1;
+  M->lo.assign(nnodes, 0);
+  M->hi.assign(nnodes, 0);
+  int off = 0;
+  for (int j = 0; j < nleaf; ++j) {
+    M->lo[nleaf - 1 + j] = off;
+    off += leaf_sizes[j];
+    M->hi[nleaf - 1 + j] = off;
+  }
+  for (int v = nleaf - 2; v >= 0; --v) {
+    M->lo[v] = M->lo[2 * v + 1];
+    M->hi[v] = M->hi[2 * v + 2];
+  }
+  // storage: [A leaves][A factors][T leaves][T factors]
+  size_t leafd = (size_t)nleaf * maxw * maxw;
+  size_t afac = 0, tfac = 0;
+  for (int v = 0; v < M->nn; ++v) {
+    size_t a = M->hi[2 * v + 1] - M->lo[2 * v + 1], b = M->hi[2 * v + 2] - M->lo[2 * v + 2];
+    afac += 2 * (a + b) * rank_cap;
+    tfac += (a + b) * rank_cap;
+  }
+  M->a_doubles = leafd + afac;
+  M->store_doubles = 2 * leafd + afac + tfac;
+  if (cudaMalloc(&M->store, M->store_doubles * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    delete M;
+    return HODLR_ENOMEM;
+  }
+  cudaMemsetAsync(M->store, 0, M->store_doubles * sizeof(double), ctx->s);
+  double* p = M->store;
+  M->D = p;
+  p += leafd;
+  M->U12.resize(M->nn); M->V12.resize(M->nn); M->U21.resize(M->nn); M->V21.resize(M->nn);
+  M->TU.resize(M->nn); M->TV.resize(M->nn);
+  for (int v = 0; v < M->nn; ++v) {
+    size_t a = M->hi[2 * v + 1] - M->lo[2 * v + 1], b = M->hi[2 * v + 2] - M->lo[2 * v + 2];
+    M->U12[v] = p; p += a * rank_cap;
+    M->V12[v] = p; p += b * rank_cap;
+    M->U21[v] = p; p += b * rank_cap;
+    M->V21[v] = p; p += a * rank_cap;
+  }
+  M->TD = p;
+  p += leafd;
+  for (int v = 0; v < M->nn; ++v) {
+    size_t a = M->hi[2 * v + 1] - M->lo[2 * v + 1], b = M->hi[2 * v + 2] - M->lo[2 * v + 2];
+    M->TU[v] = p; p += a * rank_cap;
+    M->TV[v] = p; p += b * rank_cap;
+  }
+  M->n_devints = 3 * M->nn + 64 * nleaf + 4096;
+  if (cudaMalloc(&M->devints, sizeof(int) * M->n_devints) != cudaSuccess ||
+      cudaMalloc(&M->dscal, sizeof(double) * 32) != cudaSuccess ||
+      cudaMalloc(&M->dstatus, sizeof(int) * 4) != cudaSuccess) {
+    cudaGetLastError();
+    hodlr_free(M);
+    return HODLR_ENOMEM;
+  }
+  cudaMemsetAsync(M->devints, 0, sizeof(int) * M->n_devints, ctx->s);
+  cudaMemsetAsync(M->dscal, 0, sizeof(double) * 32, ctx->s);
+  cudaMemsetAsync(M->dstatus, 0, sizeof(int) * 4, ctx->s);
+  std::vector<int> z12(std::max(1, M->nn), 0), z21(std::max(1, M->nn), 0);
+  int rc = upload_values(ctx, M, leaves, U12, V12, r12 ? r12 : z12.data(), U21, V21, r21 ? r21 : z21.data());
+  if (rc != HODLR_OK) {
+    hodlr_free(M);
+    return rc;
+  }
+  *out = M;
+  return HODLR_OK;
+}
+
+int hodlr_upload(hodlr_ctx* ctx, hodlr_mat* A, const double* const* leaves, const double* const* U12,
+                 const double* const* V12, const int* r12, const double* const* U21, const double* const* V21,
+                 const int* r21) {
+  if (!ctx || !A) return HODLR_EINVAL;
+  std::vector<int> z(std::max(1, A->nn), 0);
+  // clear the factor columns beyond the new ranks is not needed: kernels read only r columns
+  return upload_values(ctx, A, leaves, U12, V12, r12 ? r12 : z.data(), U21, V21, r21 ? r21 : z.data());
+}
+
+int hodlr_snapshot(hodlr_ctx* ctx, hodlr_mat* A) {
+  if (!ctx || !A) return HODLR_EINVAL;
+  if (!A->snapshot) {
+    if (cudaMalloc(&A->snapshot, A->a_doubles * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&A->snap_ints, sizeof(int) * std::max(1, 3 * A->nn)) != cudaSuccess) {
+      cudaGetLastError();
+      return HODLR_ENOMEM;
+    }
+  }
+  HQ_CUDA_OK(cudaMemcpyAsync(A->snapshot, A->store, A->a_doubles * sizeof(double), cudaMemcpyDeviceToDevice, ctx->s));
+  if (A->nn)
+    HQ_CUDA_OK(cudaMemcpyAsync(A->snap_ints, A->devints, sizeof(int) * 3 * A->nn, cudaMemcpyDeviceToDevice, ctx->s));
+  return HODLR_OK;
+}
+
+int hodlr_restore(hodlr_ctx* ctx, hodlr_mat* A) {
+  if (!ctx || !A) return HODLR_EINVAL;
+  if (!A->snapshot) return HODLR_ESTATE;
+  HQ_CUDA_OK(cudaMemcpyAsync(A->store, A->snapshot, A->a_doubles * sizeof(double), cudaMemcpyDeviceToDevice, ctx->s));
+  if (A->nn)
+    HQ_CUDA_OK(cudaMemcpyAsync(A->devints, A->snap_ints, sizeof(int) * 3 * A->nn, cudaMemcpyDeviceToDevice, ctx->s));
+  A->factored = false;
+  return HODLR_OK;
+}
+
+static int ensure_plan(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm) {
+  bool est = !(anorm > 0);
+  if (A->planned && A->plan_tol == tol && ((A->plan_anorm > 0) == !est)) return HODLR_OK;
+  free_plan(A->plan);
+  if (A->gexec) {
+    cudaGraphExecDestroy(A->gexec);
+    A->gexec = nullptr;
+  }
+  int rc = build_plan(A, A->plan, ctx->cluster, tol, [&](Planner& pl) {
+    Rec z = {};
+    z.type = R_FILL; z.p0 = A->dscal + 1; z.cnt = 16; z.v = 0.0;
+    pl.P->recs.push_back(z);
+    Rec zs = {};
+    zs.type = R_MEMSET_INT; zs.ip = A->dstatus; zs.cnt = sizeof(int) * 4;
+    pl.P->recs.push_back(zs);
+    if (est) {
+      pl.norm_estimate(30);
+    }
+    pl.node(0);
+  });
+  if (rc != HODLR_OK) return rc;
+  A->planned = true;
+  A->plan_tol = tol;
+  A->plan_anorm = est ? -1.0 : 1.0;
+  return HODLR_OK;
+}
+
+static int qr_launch(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm) {
+  if (!(anorm > 0)) {
+    return run_plan(ctx, A, A->plan);
+  }
+  // set anorm on the device with a kernel (capturable), then run
+  HQ_CUDA_OK(launch_fill(A->dscal, 1, anorm, ctx->s));
+  return run_plan(ctx, A, A->plan);
+}
+
+int hodlr_qr(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm) {
+  if (!ctx || !A || !(tol >= 0)) return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  int rc = ensure_plan(ctx, A, tol, anorm);
+  if (rc) return rc;
+  rc = qr_launch(ctx, A, tol, anorm);
+  if (rc) return rc;
+  A->factored = true;
+  return HODLR_OK;
+}
+
+int hodlr_qr_graph(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm) {
+  if (!ctx || !A || !(tol >= 0)) return HODLR_EINVAL;
+  if (!A->snapshot) return HODLR_ESTATE;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  int rc = ensure_plan(ctx, A, tol, anorm);
+  if (rc) return rc;
+  if (!A->gexec || A->g_tol != tol || A->g_anorm != anorm) {
+    if (A->gexec) cudaGraphExecDestroy(A->gexec);
+    A->gexec = nullptr;
+    cudaGraph_t g;
+    HQ_CUDA_OK(cudaStreamBeginCapture(ctx->s, cudaStreamCaptureModeThreadLocal));
+    int r1 = hodlr_restore(ctx, A);
+    int r2 = r1 ? r1 : qr_launch(ctx, A, tol, anorm);
+    cudaError_t e = cudaStreamEndCapture(ctx->s, &g);
+    if (r2) return r2;
+    if (e != cudaSuccess) return cuda_fail(e, __FILE__, __LINE__);
+    e = cudaGraphInstantiate(&A->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, __FILE__, __LINE__);
+    A->g_tol = tol;
+    A->g_anorm = anorm;
+  }
+  HQ_CUDA_OK(cudaGraphLaunch(A->gexec, ctx->s));
+  A->factored = true;
+  return HODLR_OK;
+}
+
+int hodlr_qr_profile(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm, double* ms, int* launches,
+                     double* flops) {
+  if (!ctx || !A || !ms || !launches || !flops || !(tol >= 0)) return HODLR_EINVAL;
+  if (!A->snapshot) return HODLR_ESTATE;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  int rc = ensure_plan(ctx, A, tol, anorm);
+  if (rc) return rc;
+  rc = hodlr_restore(ctx, A);
+  if (rc) return rc;
+  Profiler prof;
+  if (anorm > 0) HQ_CUDA_OK(launch_fill(A->dscal, 1, anorm, ctx->s));
+  rc = run_plan(ctx, A, A->plan, &prof);
+  cudaError_t e = cudaStreamSynchronize(ctx->s);
+  for (int k = 0; k < 8; ++k) {
+    ms[k] = 0;
+    launches[k] = 0;
+    flops[k] = 0;
+  }
+  for (size_t i = 0; i < prof.kind.size(); ++i) {
+    float t = 0;
+    if (e == cudaSuccess && !rc) cudaEventElapsedTime(&t, prof.ev[2 * i], prof.ev[2 * i + 1]);
+    ms[prof.kind[i]] += t;
+    launches[prof.kind[i]] += 1;
+  }
+  for (auto ev : prof.ev) cudaEventDestroy(ev);
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, __FILE__, __LINE__);
+  double f[16];
+  HQ_CUDA_OK(cudaMemcpy(f, A->dscal + 1, sizeof(double) * 16, cudaMemcpyDeviceToHost));
+  for (int k = 0; k < 8 && kKindSlot + k < 16; ++k) flops[k] = f[kKindSlot + k];
+  A->factored = true;
+  return HODLR_OK;
+}
+
+int hodlr_status(hodlr_ctx* ctx, hodlr_mat* A, int* status, double* anorm_used) {
+  if (!ctx || !A) return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaStreamSynchronize(ctx->s));
+  int st = 0;
+  double an = 0;
+  HQ_CUDA_OK(cudaMemcpy(&st, A->dstatus, sizeof(int), cudaMemcpyDeviceToHost));
+  HQ_CUDA_OK(cudaMemcpy(&an, A->dscal, sizeof(double), cudaMemcpyDeviceToHost));
+  if (status) *status = st;
+  if (anorm_used) *anorm_used = an;
+  return HODLR_OK;
+}
+
+int hodlr_ranks(hodlr_ctx* ctx, const hodlr_mat* A, int* r12, int* r21, int* rT) {
+  if (!ctx || !A) return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaStreamSynchronize(ctx->s));
+  if (A->nn == 0) return HODLR_OK;
+  std::vector<int> h(3 * A->nn);
+  HQ_CUDA_OK(cudaMemcpy(h.data(), A->devints, sizeof(int) * 3 * A->nn, cudaMemcpyDeviceToHost));
+  if (r12) memcpy(r12, h.data(), sizeof(int) * A->nn);
+  if (r21) memcpy(r21, h.data() + A->nn, sizeof(int) * A->nn);
+  if (rT) memcpy(rT, h.data() + 2 * A->nn, sizeof(int) * A->nn);
+  return HODLR_OK;
+}
+
+int hodlr_flops(hodlr_ctx* ctx, const hodlr_mat* A, double* out) {
+  if (!ctx || !A || !out) return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaStreamSynchronize(ctx->s));
+  double f[8];
+  HQ_CUDA_OK(cudaMemcpy(f, A->dscal + 1, sizeof(double) * 8, cudaMemcpyDeviceToHost));
+  double tot = 0;
+  for (int i = 0; i < 7; ++i) {
+    out[i] = f[i];
+    tot += f[i];
+  }
+  out[7] = tot;
+  return HODLR_OK;
+}
+
+}  // extern "C"
+
+static int run_temp_plan(hodlr_ctx* ctx, hodlr_mat* A, Plan& P) {
+  int rc = run_plan(ctx, A, P);
+  cudaError_t e = cudaStreamSynchronize(ctx->s);
+  free_plan(P);
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, __FILE__, __LINE__);
+  return HODLR_OK;
+}
+
+// Temporary plans share the matrix arena: they are built with measuring + real pass.
+template <class F>
+static int temp_plan(hodlr_ctx* ctx, hodlr_mat* A, F&& body) {
+  Plan P;
+  // a temporary plan must not shrink the arena the factorization plan uses; build_plan only grows it
+  // but would rewrite pointers of the cached factorization plan if it reallocates: drop that plan then.
+  char* before = A->arena;
+  int rc = build_plan(A, P, ctx->cluster, 0.0, body);
+  if (rc) {
+    free_plan(P);
+    return rc;
+  }
+  if (A->arena != before && A->planned) {
+    free_plan(A->plan);
+    A->planned = false;
+    if (A->gexec) {
+      cudaGraphExecDestroy(A->gexec);
+      A->gexec = nullptr;
+    }
+  }
+  return run_temp_plan(ctx, A, P);
+}
+
+extern "C" {
+
+int hodlr_to_dense(hodlr_ctx* ctx, const hodlr_mat* Ac, int which, double* out, int ld) {
+  hodlr_mat* A = const_cast<hodlr_mat*>(Ac);
+  if (!ctx || !A || !out || ld < A->n || which < 0 || which > 3) return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  // dense = op(part) I: use the HODLR x block product with an identity block
+  return temp_plan(ctx, A, [&](Planner& pl) {
+    double* I = pl.alloc<double>((size_t)A->n * A->n);
+    Rec ri = {};
+    ri.type = R_IDENT; ri.p0 = I; ri.i0 = A->n; ri.i1 = A->n; ri.i2 = A->n;
+    pl.P->recs.push_back(ri);
+    View v = which == 3 ? pl.tview() : pl.aview();
+    int part = which == 0 ? 0 : (which == 1 ? 1 : 2);
+    pl.matvec(v, 0, part, 0, I, A->n, out, ld, A->n, -1, 1.0, 0.0, kStepNone);
+  });
+}
+
+int hodlr_matvec(hodlr_ctx* ctx, const hodlr_mat* Ac, int which, int trans, int nrhs, const double* X, int ldx,
+                 double* Y, int ldy) {
+  hodlr_mat* A = const_cast<hodlr_mat*>(Ac);
+  if (!ctx || !A || !X || !Y || nrhs <= 0 || ldx < A->n || ldy < A->n || which < 0 || which > 3)
+    return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  return temp_plan(ctx, A, [&](Planner& pl) {
+    View v = which == 3 ? pl.tview() : pl.aview();
+    int part = which == 0 ? 0 : (which == 1 ? 1 : 2);
+    pl.matvec(v, 0, part, trans ? 1 : 0, X, ldx, Y, ldy, nrhs, -1, 1.0, 0.0, kStepNone);
+  });
+}
+
+static void plan_apply(Planner& pl, hodlr_mat* A, int nrhs, double* B, int ldb, bool transposed_q) {
+  const int n = A->n;
+  double* W1 = pl.alloc<double>((size_t)n * nrhs);
+  double* W2 = pl.alloc<double>((size_t)n * nrhs);
+  View Y = pl.aview(), T = pl.tview();
+  pl.matvec(Y, 0, 1, 1, B, ldb, W1, n, nrhs, -1, 1.0, 0.0, kStepNone);                 // Y^T B
+  pl.matvec(T, 0, 2, transposed_q ? 1 : 0, W1, n, W2, n, nrhs, -1, 1.0, 0.0, kStepNone);  // T^T or T
+  pl.matvec(Y, 0, 1, 0, W2, n, B, ldb, nrhs, -1, -1.0, 1.0, kStepNone);                // B -= Y W2
+}
+
+int hodlr_apply_q(hodlr_ctx* ctx, const hodlr_mat* Ac, int nrhs, double* B, int ldb) {
+  hodlr_mat* A = const_cast<hodlr_mat*>(Ac);
+  if (!ctx || !A || !B || nrhs <= 0 || ldb < A->n) return HODLR_EINVAL;
+  if (!A->factored) return HODLR_ESTATE;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  return temp_plan(ctx, A, [&](Planner& pl) { plan_apply(pl, A, nrhs, B, ldb, false); });
+}
+
+int hodlr_apply_qt(hodlr_ctx* ctx, const hodlr_mat* Ac, int nrhs, double* B, int ldb) {
+  hodlr_mat* A = const_cast<hodlr_mat*>(Ac);
+  if (!ctx || !A || !B || nrhs <= 0 || ldb < A->n) return HODLR_EINVAL;
+  if (!A->factored) return HODLR_ESTATE;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  return temp_plan(ctx, A, [&](Planner& pl) { plan_apply(pl, A, nrhs, B, ldb, true); });
+}
+
+static void plan_upper_solve(Planner& pl, hodlr_mat* A, int v, double* B, int ldb, int nrhs) {
+  if (pl.is_leaf(v)) {
+    int j = v - (A->nleaf - 1);
+    Rec r = {};
+    r.type = R_TRSM; r.p0 = A->D + (size_t)j * A->ldl * A->ldl; r.i0 = A->ldl; r.i1 = pl.size(v);
+    r.ip = reinterpret_cast<int*>(B + A->lo[v]); r.i2 = ldb; r.i3 = nrhs;
+    pl.P->recs.push_back(r);
+    return;
+  }
+  int c1 = 2 * v + 1, c2 = 2 * v + 2;
+  plan_upper_solve(pl, A, c2, B, ldb, nrhs);
+  size_t mk = pl.mark();
+  const int kc = A->kc;
+  double* Z = pl.alloc<double>((size_t)kc * nrhs);
+  int a = pl.m1(v), b = pl.m2(v);
+  pl.gemm({Planner::gd(A->V12[v], b, 1, 0, B + A->lo[c2], ldb, 0, 0, Z, kc, kc, v, nrhs, -1, b, -1, 1.0, 0.0, kStepNone, -1)});
+  pl.gemm({Planner::gd(A->U12[v], a, 0, 0, Z, kc, 0, 0, B + A->lo[c1], ldb, a, -1, nrhs, -1, kc, v, -1.0, 1.0, kStepNone, -1)});
+  pl.release(mk);
+  plan_upper_solve(pl, A, c1, B, ldb, nrhs);
+}
+
+int hodlr_solve(hodlr_ctx* ctx, const hodlr_mat* Ac, int nrhs, double* B, int ldb) {
+  hodlr_mat* A = const_cast<hodlr_mat*>(Ac);
+  if (!ctx || !A || !B || nrhs <= 0 || ldb < A->n) return HODLR_EINVAL;
+  if (!A->factored) return HODLR_ESTATE;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  int rc = temp_plan(ctx, A, [&](Planner& pl) {
+    plan_apply(pl, A, nrhs, B, ldb, true);
+    plan_upper_solve(pl, A, 0, B, ldb, nrhs);
+  });
+  if (rc) return rc;
+  int* flag;
+  HQ_CUDA_OK(cudaMalloc(&flag, sizeof(int)));
+  cudaMemsetAsync(flag, 0, sizeof(int), ctx->s);
+  launch_check_finite(B, ldb, A->n, nrhs, flag, ctx->s);
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->s);
+  cudaStreamSynchronize(ctx->s);
+  cudaFree(flag);
+  if (e != cudaSuccess) return cuda_fail(e, __FILE__, __LINE__);
+  return h ? HODLR_ESINGULAR : HODLR_OK;
+}
+
+int hodlr_norm2_estimate(hodlr_ctx* ctx, const hodlr_mat* Ac, int iters, double* out) {
+  hodlr_mat* A = const_cast<hodlr_mat*>(Ac);
+  if (!ctx || !A || !out || iters < 0) return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  int rc = temp_plan(ctx, A, [&](Planner& pl) { pl.norm_estimate(iters); });
+  if (rc) return rc;
+  HQ_CUDA_OK(cudaMemcpy(out, A->dscal, sizeof(double), cudaMemcpyDeviceToHost));
+  return HODLR_OK;
+}
+
+size_t hodlr_storage_bytes(const hodlr_mat* A) {
+  if (!A) return 0;
+  return A->store_doubles * sizeof(double) + sizeof(int) * 3 * A->nn;
+}
+
+int hodlr_download(hodlr_ctx* ctx, const hodlr_mat* A, void* host, size_t bytes) {
+  if (!ctx || !A || !host || bytes < hodlr_storage_bytes(A)) return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaMemcpyAsync(host, A->store, A->store_doubles * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+  if (A->nn)
+    HQ_CUDA_OK(cudaMemcpyAsync((char*)host + A->store_doubles * sizeof(double), A->devints, sizeof(int) * 3 * A->nn,
+                               cudaMemcpyDeviceToHost, ctx->s));
+  HQ_CUDA_OK(cudaStreamSynchronize(ctx->s));
+  return HODLR_OK;
+}
+
+// ------------------------------------------------------------------------- primitives
+int hodlr_dense_qr(hodlr_ctx* ctx, int h, int w, double* A, int lda, double* T, int ldt) {
+  if (!ctx || !A || !T || h < 1 || w < 1 || w > 1024 || lda < h || ldt < std::min(h, w)) return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  int k = std::min(h, w);
+  double *tau, *G;
+  QRDesc* dq;
+  HQ_CUDA_OK(cudaMalloc(&tau, sizeof(double) * k));
+  HQ_CUDA_OK(cudaMalloc(&G, sizeof(double) * k * k));
+  HQ_CUDA_OK(cudaMalloc(&dq, sizeof(QRDesc)));
+  QRDesc q = {};
+  q.A = A; q.lda = lda; q.h = h; q.w = w; q.href = -1; q.wref = -1; q.tau = tau; q.T = T; q.ldt = ldt;
+  q.G = G; q.ldg = k; q.step = kStepNone; q.fmode = 0;
+  cudaMemcpy(dq, &q, sizeof(QRDesc), cudaMemcpyHostToDevice);
+  cudaError_t e = launch_qr(&q, 1, dq, nullptr, nullptr, ctx->cluster, ctx->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->s);
+  cudaFree(tau);
+  cudaFree(G);
+  cudaFree(dq);
+  if (e != cudaSuccess) return cuda_fail(e, __FILE__, __LINE__);
+  return HODLR_OK;
+}
+
+int hodlr_truncate(hodlr_ctx* ctx, int nL, int nR, int K, const double* L, const double* Rt, double thr,
+                   int kmax, double* Lout, double* Rout, int* k_out) {
+  if (!ctx || nL < 1 || nR < 1 || K < 0 || K > 256 || kmax < 1 || kmax > 256 || !k_out || (K && (!L || !Rt)) ||
+      !Lout || !Rout || !(thr >= 0))
+    return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  // a one-node shell matrix provides devints, status and arena
+  hodlr_mat M;
+  M.n = nL; M.nleaf = 1; M.nn = 0; M.kc = kmax; M.ldl = 1;
+  M.n_devints = 64;
+  int rc = HODLR_OK;
+  if (cudaMalloc(&M.devints, sizeof(int) * 64) != cudaSuccess || cudaMalloc(&M.dstatus, sizeof(int) * 4) != cudaSuccess ||
+      cudaMalloc(&M.dscal, sizeof(double) * 32) != cudaSuccess) {
+    cudaGetLastError();
+    rc = HODLR_ENOMEM;
+  }
+  Plan P;
+  if (!rc) {
+    cudaMemsetAsync(M.devints, 0, sizeof(int) * 64, ctx->s);
+    cudaMemsetAsync(M.dstatus, 0, sizeof(int) * 4, ctx->s);
+    cudaMemsetAsync(M.dscal, 0, sizeof(double) * 32, ctx->s);
+    rc = build_plan(&M, P, ctx->cluster, thr, [&](Planner& pl) {
+      Planner::Trunc t;
+      t.nL = nL; t.nR = nR;
+      t.L = {Planner::seg(L, nL, K, -1, 1.0)};
+      t.R = {Planner::seg(Rt, nR, K, -1, 1.0)};
+      t.thr = thr; t.thr_ref = nullptr; t.Uout = Lout; t.ldu = nL; t.Vout = Rout; t.ldv = nR;
+      t.kout_ref = pl.ints(1); t.step = kStepNone;
+      std::vector<Planner::Trunc> ts = {t};
+      if (K > 0) pl.truncate(ts);
+    });
+  }
+  if (!rc && K > 0) rc = run_plan(ctx, &M, P);
+  if (!rc) {
+    cudaStreamSynchronize(ctx->s);
+    int st = 0, k = 0;
+    cudaMemcpy(&k, M.devints, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaMemcpy(&st, M.dstatus, sizeof(int), cudaMemcpyDeviceToHost);
+    *k_out = K > 0 ? k : 0;
+    if (cudaGetLastError() != cudaSuccess) rc = HODLR_ECUDA;
+    else if (st == HODLR_ERANK) rc = HODLR_ERANK;
+  }
+  free_plan(P);
+  cudaFree(M.devints);
+  cudaFree(M.dstatus);
+  cudaFree(M.dscal);
+  if (M.arena) cudaFree(M.arena);
+  M.devints = nullptr; M.dstatus = nullptr; M.dscal = nullptr; M.arena = nullptr;
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,439 @@
+// FP64 kernels of the hQR hot path that are not factorizations: a descriptor-driven batched
+// GEMM (every HODLR-times-block product, low-rank product and WY application of Alg. 2),
+// column concatenation for the truncation inputs, the gather/scatter of the compressed leaf
+// column (Sec. 4, Eq. (12)), rank selection after the Jacobi SVD (Sec. 2.1.1, k_eps) and small
+// utilities.  GB300 has about 2 FP64 FMA per clock per SM, so these kernels are FP64-issue
+// bound; they are written to spread work over all 152 SMs rather than to stage operands.
+#include <cstdio>
+
+#include "common.cuh"
+
+namespace hq {
+
+int cuda_fail(cudaError_t e, const char* file, int line) {
+  fprintf(stderr, "hodlr_qr: CUDA error %s at %s:%d\n", cudaGetErrorString(e), file, line);
+  return 6;  // HODLR_ECUDA
+}
+
+__device__ inline double ldcg(const double* p) { return __ldcg(p); }
+
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ----------------------------------------------------------------------------------- GEMM
+constexpr int BM = 32, BN = 32, BK = 16, GT = 256;
+
+__device__ inline double masked(const double* M, int ld, int r, int c, int mask) {
+  if (mask == kMaskNone) return M[r + (size_t)c * ld];
+  if (mask == kMaskUpper) return r <= c ? M[r + (size_t)c * ld] : 0.0;
+  if (mask == kMaskLower) return r >= c ? M[r + (size_t)c * ld] : 0.0;
+  // unit lower
+  if (r > c) return M[r + (size_t)c * ld];
+  return r == c ? 1.0 : 0.0;
+}
+
+__global__ void __launch_bounds__(GT) gemm_kernel(const GemmDesc* __restrict__ descs, int ndesc,
+                                                  const int* __restrict__ di, double* flops) {
+  // locate descriptor: work items are contiguous per descriptor
+  int item = blockIdx.x;
+  int lo = 0, hi = ndesc - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (descs[mid].work0 <= item) lo = mid; else hi = mid - 1;
+  }
+  const GemmDesc& d = descs[lo];
+  int local = item - d.work0;
+  int tiles = d.tiles_m * d.tiles_n;
+  int split = local / tiles;
+  int t = local - split * tiles;
+  int tm = t % d.tiles_m, tn = t / d.tiles_m;
+  const int m = dimv(d.m, d.mref, di), n = dimv(d.n, d.nref, di), k = dimv(d.k, d.kref, di);
+  if (local == 0 && threadIdx.x == 0 && flops) {
+    double f = (double)m * n * k * (d.fmode == 1 ? 1.0 : 2.0);
+    if (f > 0) {
+      if (d.step >= 0 && d.fmode >= 0) atomicAdd(&flops[d.step], f);
+      atomicAdd(&flops[kKindSlot + 0], f);
+    }
+  }
+  const int row0 = tm * BM, col0 = tn * BN;
+  const bool to_part = d.ksplit > 1;
+  if (row0 >= m || col0 >= n) {
+    // nothing to compute; partial slots of an active split still need zeros
+    return;
+  }
+  int kchunk = (k + d.ksplit - 1) / d.ksplit;
+  kchunk = (kchunk + BK - 1) / BK * BK;
+  const int k0 = split * kchunk;
+  const int k1 = min(k, k0 + kchunk);
+
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int kk = k0; kk < k1; kk += BK) {
+    for (int e = threadIdx.x; e < BM * BK; e += GT) {
+      int i = e % BM, l = e / BM;
+      int gi = row0 + i, gl = kk + l;
+      double v = 0.0;
+      if (gi < m && gl < k1) {
+        v = d.ta ? masked(d.A, d.lda, gl, gi, d.mska) : masked(d.A, d.lda, gi, gl, d.mska);
+      }
+      As[l][i] = v;
+    }
+    for (int e = threadIdx.x; e < BN * BK; e += GT) {
+      int l = e % BK, j = e / BK;
+      int gl = kk + l, gj = col0 + j;
+      double v = 0.0;
+      if (gj < n && gl < k1) {
+        v = d.tb ? masked(d.B, d.ldb, gj, gl, d.mskb) : masked(d.B, d.ldb, gl, gj, d.mskb);
+      }
+      Bs[l][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < BK; ++l) {
+      double a0 = As[l][ty], a1 = As[l][ty + 16];
+      double b0 = Bs[l][tx], b1 = Bs[l][tx + 16];
+      acc[0][0] = fma(a0, b0, acc[0][0]);
+      acc[0][1] = fma(a0, b1, acc[0][1]);
+      acc[1][0] = fma(a1, b0, acc[1][0]);
+      acc[1][1] = fma(a1, b1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+  double alpha = d.alpha;
+  if (d.alpha_ref) alpha *= *d.alpha_ref;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      int gi = row0 + ty + 16 * a, gj = col0 + tx + 16 * b;
+      if (gi < m && gj < n) {
+        if (to_part) {
+          d.part[(size_t)split * d.m * d.n + gi + (size_t)gj * d.m] = acc[a][b];
+        } else {
+          double* c = d.C + gi + (size_t)gj * d.ldc;
+          double v = alpha * acc[a][b];
+          if (d.beta != 0.0) v = fma(d.beta, *c, v);
+          *c = v;
+        }
+      }
+    }
+}
+
+// Sum split-K partials: C = alpha * sum_s part_s + beta * C.  One block per 256 outputs.
+__global__ void gemm_reduce_kernel(const GemmDesc* __restrict__ descs, const int* __restrict__ rd,
+                                   int nred, const int* __restrict__ di) {
+  int item = blockIdx.x;
+  // rd: pairs (desc index, first block) sorted by first block
+  int lo = 0, hi = nred - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (rd[2 * mid + 1] <= item) lo = mid; else hi = mid - 1;
+  }
+  const GemmDesc& d = descs[rd[2 * lo]];
+  int e = (item - rd[2 * lo + 1]) * blockDim.x + threadIdx.x;
+  const int m = dimv(d.m, d.mref, di), n = dimv(d.n, d.nref, di), k = dimv(d.k, d.kref, di);
+  if (e >= d.m * d.n) return;
+  int i = e % d.m, j = e / d.m;
+  if (i >= m || j >= n) return;
+  int kchunk = (k + d.ksplit - 1) / d.ksplit;
+  kchunk = (kchunk + BK - 1) / BK * BK;
+  double s = 0.0;
+  for (int sp = 0; sp < d.ksplit; ++sp) {
+    if (sp * kchunk >= k) break;   // splits beyond k never wrote their slot
+    s += d.part[(size_t)sp * d.m * d.n + i + (size_t)j * d.m];
+  }
+  double alpha = d.alpha;
+  if (d.alpha_ref) alpha *= *d.alpha_ref;
+  double* c = d.C + i + (size_t)j * d.ldc;
+  double v = alpha * s;
+  if (d.beta != 0.0) v = fma(d.beta, *c, v);
+  *c = v;
+}
+
+cudaError_t launch_gemm(GemmDesc* h, int n, GemmDesc* d, const int* devints, double* flops,
+                        cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int total = h[n - 1].work0 + h[n - 1].tiles_m * h[n - 1].tiles_n * h[n - 1].ksplit;
+  if (total <= 0) return cudaSuccess;
+  gemm_kernel<<<total, GT, 0, s>>>(d, n, devints, flops);
+  return cudaGetLastError();
+}
+
+// Reduction launch helper: `rd` is a device array of (desc index, first block) pairs,
+// `nblocks` the total number of blocks.
+cudaError_t launch_gemm_reduce(const GemmDesc* d, const int* rd, int nred, int nblocks,
+                               const int* devints, cudaStream_t s) {
+  if (nred <= 0 || nblocks <= 0) return cudaSuccess;
+  gemm_reduce_kernel<<<nblocks, 256, 0, s>>>(d, rd, nred, devints);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- concat
+__global__ void concat_kernel(const ConcatDesc* __restrict__ descs, int* di) {
+  const ConcatDesc& d = descs[blockIdx.y];
+  int off = 0;
+  for (int s = 0; s < d.nseg; ++s) {
+    const ConcatSeg& g = d.seg[s];
+    int c = dimv(g.cols, g.colsref, di);
+    if (off + c > d.cap) c = d.cap - off;
+    const int rows = d.rows;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rows * c; e += gridDim.x * blockDim.x) {
+      int i = e % rows, j = e / rows;
+      d.dst[i + (size_t)(off + j) * d.ldd] = g.alpha * g.src[i + (size_t)j * g.lds];
+    }
+    off += c;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && d.kout_ref >= 0) {
+    di[d.kout_ref] = off;
+    di[d.kout_ref + 1] = off < d.rows ? off : d.rows;
+  }
+}
+
+cudaError_t launch_concat(const ConcatDesc* h, int n, ConcatDesc* d, int* devints, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int maxrows = 0;
+  for (int i = 0; i < n; ++i) maxrows = max(maxrows, h[i].rows);
+  int gx = min(64, max(1, maxrows * 8 / 256));
+  concat_kernel<<<dim3(gx, n), 256, 0, s>>>(d, devints);
+  return cudaGetLastError();
+}
+
+// -------------------------------------------------------------------- leaf panel gather
+__global__ void panel_gather_kernel(const PanelDesc* __restrict__ descs, int* di) {
+  const PanelDesc& d = descs[blockIdx.y];
+  const int w = d.w;
+  // leaf block
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < w * w; e += gridDim.x * blockDim.x) {
+    int i = e % w, j = e / w;
+    d.P[i + (size_t)j * d.ldP] = d.D[i + (size_t)j * d.ldD];
+  }
+  int off = w;
+  for (int s = 0; s < d.nsrc; ++s) {
+    int r = dimv(d.rcap[s], d.rref[s], di);
+    // rows off..off+r-1 of the panel are row i of B_R = column i of V21 (transposed)
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * w; e += gridDim.x * blockDim.x) {
+      int c = e % w, i = e / w;
+      d.P[(off + i) + (size_t)c * d.ldP] = d.src[s][c + (size_t)i * d.lds[s]];
+    }
+    off += r;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) di[d.href] = off;
+}
+
+__global__ void panel_scatter_kernel(const PanelDesc* __restrict__ descs, const int* __restrict__ di) {
+  const PanelDesc& d = descs[blockIdx.y];
+  const int w = d.w;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < w * w; e += gridDim.x * blockDim.x) {
+    int i = e % w, j = e / w;
+    d.D[i + (size_t)j * d.ldD] = d.P[i + (size_t)j * d.ldP];
+  }
+  int off = w;
+  for (int s = 0; s < d.nsrc; ++s) {
+    int r = dimv(d.rcap[s], d.rref[s], di);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * w; e += gridDim.x * blockDim.x) {
+      int c = e % w, i = e / w;
+      d.src[s][c + (size_t)i * d.lds[s]] = d.P[(off + i) + (size_t)c * d.ldP];
+    }
+    off += r;
+  }
+}
+
+cudaError_t launch_panel_gather(const PanelDesc* h, int n, PanelDesc* d, int* devints, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int gx = min(64, max(1, h[0].w * h[0].w / 1024));
+  panel_gather_kernel<<<dim3(gx, n), 256, 0, s>>>(d, devints);
+  return cudaGetLastError();
+}
+cudaError_t launch_panel_scatter(const PanelDesc* h, int n, PanelDesc* d, const int* devints, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int gx = min(64, max(1, h[0].w * h[0].w / 1024));
+  panel_scatter_kernel<<<dim3(gx, n), 256, 0, s>>>(d, devints);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------- rank selection
+// One block per truncation problem.  k_eps = #{sigma_i > thr} (Sec. 2.1.1); the kept columns
+// of W = M J are normalized to the left singular vectors and sorted by sigma descending.
+__global__ void select_kernel(const SelectDesc* __restrict__ descs, int* di, double* flops) {
+  const SelectDesc& d = descs[blockIdx.x];
+  const int q1 = dimv(d.q1, d.q1ref, di), q2 = dimv(d.q2, d.q2ref, di);
+  double thr = d.thr;
+  if (d.thr_ref) thr *= *d.thr_ref;
+  extern __shared__ int sh[];
+  int* order = sh;           // q2 entries: output slot of column j, or -1
+  __shared__ int kcount;
+  if (threadIdx.x == 0) kcount = 0;
+  __syncthreads();
+  for (int j = threadIdx.x; j < q2; j += blockDim.x) {
+    double nj = d.nrm[j];
+    int slot = -1;
+    if (sqrt(nj) > thr) {
+      int rank = 0;
+      for (int l = 0; l < q2; ++l) {
+        double nl = d.nrm[l];
+        if (sqrt(nl) > thr && (nl > nj || (nl == nj && l < j))) ++rank;
+      }
+      slot = rank;
+      atomicAdd(&kcount, 1);
+    }
+    order[j] = slot;
+  }
+  __syncthreads();
+  int k = kcount;
+  if (k > d.kcap) {
+    if (threadIdx.x == 0 && d.status) atomicMax(d.status, 3);
+    k = d.kcap;
+  }
+  for (int j = 0; j < q2; ++j) {
+    int slot = order[j];
+    if (slot < 0 || slot >= k) continue;
+    double inv = 1.0 / sqrt(d.nrm[j]);
+    for (int i = threadIdx.x; i < q1; i += blockDim.x)
+      d.U[i + (size_t)slot * d.ldu] = d.W[i + (size_t)j * d.ldw] * inv;
+  }
+  if (threadIdx.x == 0) {
+    di[d.kref] = k;
+    if (flops && d.step >= 0) {
+      // the oracle's count of one T_eps: two economy QRs with Q formed, the core product,
+      // an R-SVD of the q1 x q2 core and the two reconstructions
+      int K = d.Kref >= 0 ? di[d.Kref] : 0;
+      double f = 0;
+      if (K > 0 && d.nL > 0 && d.nR > 0) {
+        double a = min(d.nL, K), b = min(d.nR, K);
+        f += 4.0 * d.nL * K * a - 4.0 * a * a * a / 3.0;
+        f += 4.0 * d.nR * K * b - 4.0 * b * b * b / 3.0;
+        f += 2.0 * a * K * b;
+        double p = max(a, b), q = min(a, b);
+        f += 4.0 * p * p * q + 8.0 * p * q * q + 9.0 * q * q * q;
+        f += 2.0 * d.nL * a * k + 2.0 * d.nR * b * k;
+      }
+      atomicAdd(&flops[d.step], f);
+    }
+  }
+}
+
+cudaError_t launch_select(const SelectDesc* h, int n, SelectDesc* d, int* devints, double* flops,
+                          cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int maxq2 = 0;
+  for (int i = 0; i < n; ++i) maxq2 = max(maxq2, h[i].q2);
+  select_kernel<<<n, 256, sizeof(int) * (maxq2 + 1), s>>>(d, devints, flops);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------- copy
+__global__ void copy_kernel(const CopyDesc* __restrict__ descs, const int* __restrict__ di) {
+  const CopyDesc& d = descs[blockIdx.y];
+  int cols = dimv(d.cols, d.colsref, di);
+  int rs = dimv(d.rows_src, d.rows_src_ref, di);
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)d.rows * cols;
+       e += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(e % d.rows), j = (int)(e / d.rows);
+    double v = (i < rs && d.src) ? d.alpha * d.src[i + (size_t)j * d.lds] : 0.0;
+    d.dst[i + (size_t)j * d.ldd] = v;
+  }
+}
+
+cudaError_t launch_copy(const CopyDesc* h, int n, CopyDesc* d, const int* devints, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int maxe = 0;
+  for (int i = 0; i < n; ++i) maxe = max(maxe, h[i].rows * h[i].cols);
+  int gx = min(128, max(1, maxe / 1024));
+  copy_kernel<<<dim3(gx, n), 256, 0, s>>>(d, devints);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- utilities
+__global__ void fill_kernel(double* p, size_t n, double v) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+cudaError_t launch_fill(double* p, size_t n, double v, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  size_t gb = (n + 255) / 256;
+  int g = (int)(gb < 1024 ? gb : 1024);
+  fill_kernel<<<g, 256, 0, s>>>(p, n, v);
+  return cudaGetLastError();
+}
+
+__global__ void set_diag_identity_kernel(double* p, int ld, int rows, int cols) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rows * cols; e += gridDim.x * blockDim.x) {
+    int i = e % rows, j = e / rows;
+    p[i + (size_t)j * ld] = (i == j) ? 1.0 : 0.0;
+  }
+}
+cudaError_t launch_set_diag_identity(double* p, int ld, int rows, int cols, cudaStream_t s) {
+  int g = min(256, max(1, rows * cols / 256));
+  set_diag_identity_kernel<<<g, 256, 0, s>>>(p, ld, rows, cols);
+  return cudaGetLastError();
+}
+
+// ||x||_2 of an n-vector (one block).  mode 0: x <- x / ||x|| and out = ||x||;
+// mode 1: out = ||x|| only.  A zero vector is left unchanged and out = 0.
+__global__ void norm_scale_kernel(double* x, int n, double* out, int mode) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s = fma(x[i], x[i], s);
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) red[0] = sqrt(v);
+  }
+  __syncthreads();
+  double nrm = red[0];
+  if (threadIdx.x == 0) *out = nrm;
+  if (mode == 0 && nrm > 0.0) {
+    double inv = 1.0 / nrm;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] *= inv;
+  }
+}
+cudaError_t launch_norm_scale(double* x, int n, double* out, int mode, cudaStream_t s) {
+  norm_scale_kernel<<<1, 1024, 0, s>>>(x, n, out, mode);
+  return cudaGetLastError();
+}
+
+__global__ void check_finite_kernel(const double* p, int ld, int rows, int cols, int* flag) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rows * cols; e += gridDim.x * blockDim.x) {
+    int i = e % rows, j = e / rows;
+    double v = p[i + (size_t)j * ld];
+    if (!isfinite(v)) { atomicExch(flag, 1); return; }
+  }
+}
+cudaError_t launch_check_finite(const double* p, int ld, int rows, int cols, int* flag, cudaStream_t s) {
+  int g = min(256, max(1, rows * cols / 256));
+  check_finite_kernel<<<g, 256, 0, s>>>(p, ld, rows, cols, flag);
+  return cudaGetLastError();
+}
+
+// Dense upper-triangular back-substitution R x = b at one leaf, one warp per right-hand side.
+__global__ void trsm_leaf_kernel(const double* __restrict__ R, int ldr, int w, double* B, int ldb, int nrhs) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= nrhs) return;
+  double* b = B + (size_t)warp * ldb;
+  for (int i = w - 1; i >= 0; --i) {
+    double xi = 0.0;
+    if (lane == 0) xi = b[i] / R[i + (size_t)i * ldr];
+    xi = __shfl_sync(0xffffffffu, xi, 0);
+    __syncwarp();
+    if (lane == 0) b[i] = xi;
+    for (int r = lane; r < i; r += 32) b[r] = fma(-R[r + (size_t)i * ldr], xi, b[r]);
+    __syncwarp();
+  }
+}
+cudaError_t launch_trsm_leaf(const double* R, int ldr, int w, double* B, int ldb, int nrhs, cudaStream_t s) {
+  int threads = 128;
+  int blocks = (nrhs * 32 + threads - 1) / threads;
+  trsm_leaf_kernel<<<blocks, threads, 0, s>>>(R, ldr, w, B, ldb, nrhs);
+  return cudaGetLastError();
+}
+
+}  // namespace hq

@@ -1,0 +1,228 @@
+"""Parity of the CUDA hQR path with the CPU oracle, through the C ABI (include/hodlr_qr.h).
+
+Tolerances: for a truncation tolerance tol, the residual ||QR - A|| / ||A|| and the
+orthogonality ||Q^T Q - I|| must each be <= 100 tol and within 10x of the oracle's own values
+(plus a roundoff floor), and the sign-normalised diagonal of R must agree with the oracle's
+within 1e3 tol ||A||_2 (absolute, because truncation perturbs R by about tol ||A|| regardless
+of |r_ii|).  With tol = 0 nothing is truncated and (Y, T, R) must match LAPACK's compact-WY QR
+of the dense matrix to roundoff times the condition number.
+"""
+import numpy as np
+import pytest
+import scipy.linalg.lapack as lapack
+
+import oracle.core as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+from tests import gpu_util as U  # noqa: E402
+
+
+def dgeqrt_full(A):
+    n = A.shape[1]
+    v, t, info = lapack.dgeqrt(n, np.asfortranarray(A))
+    V = np.tril(v[:, :n], -1)
+    V[:n, :n] += np.eye(n)
+    return V, np.triu(t[:n, :n]), np.triu(v[:n, :n])
+
+
+# ------------------------------------------------------------------------- primitives
+@pytest.mark.parametrize("h,w,seed", [(1, 1, 0), (5, 5, 1), (40, 17, 2), (128, 128, 3), (306, 256, 4),
+                                      (500, 64, 5), (70, 70, 6)])
+def test_dense_qr_matches_oracle(h, w, seed):
+    A = np.random.default_rng(seed).standard_normal((h, w))
+    if h > 3:
+        A[:, min(2, w - 1)] *= 1e-9     # a tiny column, graded input
+    Y, T, R = O.block_qr(A)
+    ta, pa, lda = U.dev(A)
+    tt, pt, ldt = U.empty(w, w)
+    from paper_1809_10585_gb300 import binding as B
+    B.dense_qr(U.ctx(), h, w, pa, lda, pt, ldt)
+    Ag = U.host(ta, h, w)
+    Tg = U.host(tt, w, w)
+    Rg = np.triu(Ag[:w, :w])
+    Yg = np.tril(Ag, -1)
+    Yg[:w, :w] += np.eye(w)
+    sc = max(1.0, np.abs(A).max())
+    np.testing.assert_allclose(Rg, R, atol=1e-13 * sc * np.sqrt(h))
+    np.testing.assert_allclose(Yg, Y, atol=1e-11)
+    np.testing.assert_allclose(np.triu(Tg), T, atol=1e-12)
+
+
+@pytest.mark.parametrize("nL,nR,K,decay,thr", [(50, 40, 12, 1.0, 1e-6), (300, 200, 60, 0.7, 1e-10),
+                                               (10, 80, 25, 0.3, 1e-6), (1024, 1024, 100, 0.8, 1e-12),
+                                               (64, 64, 1, 1.0, 1e-3)])
+def test_truncate_matches_oracle(nL, nR, K, decay, thr):
+    rng = np.random.default_rng(nL + K)
+    L = rng.standard_normal((nL, K)) * (decay ** np.arange(K))[None, :]
+    Rt = rng.standard_normal((nR, K))
+    Lo, Ro = O.truncate(L, Rt, thr)
+    tl, pl, _ = U.dev(L)
+    tr, pr, _ = U.dev(Rt)
+    kmax = 128
+    to, po, _ = U.empty(nL, kmax)
+    tq, pq, _ = U.empty(nR, kmax)
+    from paper_1809_10585_gb300 import binding as B
+    rc, k = B.truncate(U.ctx(), nL, nR, K, pl, pr, thr, kmax, po, pq)
+    assert rc == 0
+    Lg, Rg = U.host(to, nL, k), U.host(tq, nR, k)
+    M = L @ Rt.T
+    s = np.linalg.svd(M, compute_uv=False)
+    assert abs(k - Lo.shape[1]) <= 1 and (k == Lo.shape[1] or np.min(np.abs(s - thr)) < 1e-6 * thr)
+    err = np.linalg.norm(M - Lg @ Rg.T, 2)
+    assert err <= thr * 1.01 + 1e-13 * s[0]
+    np.testing.assert_allclose(Lg @ Rg.T, Lo @ Ro.T, atol=2 * thr + 1e-13 * s[0])
+    if k:
+        np.testing.assert_allclose(Lg.T @ Lg, np.eye(k), atol=1e-12)
+
+
+@pytest.mark.parametrize("which,part", [(0, "full"), (1, "unit_lower"), (2, "upper")])
+@pytest.mark.parametrize("trans", [0, 1])
+def test_matvec_matches_oracle(which, part, trans):
+    inp = W.random_hodlr(1000, 100, 7, seed=3)
+    H = O.from_input(inp)
+    X = np.random.default_rng(1).standard_normal((1000, 9))
+    ref = O.matmat(H, X, bool(trans), part)
+    M = B_matrix(inp)
+    tx, px, ld = U.dev(X)
+    ty, py, _ = U.empty(1000, 9)
+    M.matvec(which, trans, 9, px, ld, py, 1000)
+    np.testing.assert_allclose(U.host(ty, 1000, 9), ref, atol=1e-12 * np.abs(ref).max())
+
+
+def B_matrix(inp, rank_cap=128):
+    from paper_1809_10585_gb300 import binding as B
+    return B.Matrix(U.ctx(), inp, rank_cap=rank_cap)
+
+
+def test_norm_estimate_matches_oracle():
+    inp = W.random_hodlr(1024, 128, 5, seed=0)
+    M = B_matrix(inp)
+    est = M.norm2_estimate(30)
+    ref = O.norm2_estimate(O.from_input(inp), 30)
+    assert abs(est - ref) <= 1e-12 * ref
+
+
+# ------------------------------------------------------------------------------ hQR
+def _check_against_oracle(inp, tol, rank_cap=128):
+    Ad = W.to_dense(inp)
+    an = np.linalg.norm(Ad, 2)
+    res = O.hqr(O.from_input(inp), tol)
+    M = U.gpu_qr(inp, tol, anorm=res.anorm, rank_cap=rank_cap)
+    st, an_used = M.status()
+    assert st == 0
+    Y, T, R = U.factors_dense(M)
+    A_t = torch.from_numpy(Ad).cuda()
+    eo, ea = U.errors_torch(Y, T, R, A_t)
+    Yo, To, Ro = (torch.from_numpy(x).cuda() for x in (res.Y_dense(), res.T_dense(), res.R_dense()))
+    eoo, eao = U.errors_torch(Yo, To, Ro, A_t)
+    floor = 1e-14 * np.sqrt(inp.n)
+    assert eo <= 100 * tol + floor and ea / an <= 100 * tol + floor
+    assert eo <= 10 * eoo + floor and ea <= 10 * eao + floor * an
+    dR = np.abs(np.abs(np.diag(R.cpu().numpy())) - np.abs(np.diag(res.R_dense())))
+    assert dR.max() <= 1e3 * tol * an + floor * an
+    Yn = Y.cpu().numpy()
+    assert np.all(np.triu(Yn, 1) == 0) and np.all(np.diag(Yn) == 1)
+    assert np.all(np.tril(R.cpu().numpy(), -1) == 0) and np.all(np.tril(T.cpu().numpy(), -1) == 0)
+    return M, res, (eo, ea, eoo, eao)
+
+
+@pytest.mark.parametrize("n,nmin,k,tol,dec,seed", [
+    (1024, 128, 5, 1e-10, 0.0, 0),      # the n = 1024, nmin = 128, rank-5 workload
+    (1000, 128, 5, 1e-10, 0.0, 1),      # ragged leaves
+    (777, 64, 4, 1e-12, 6.0, 2),        # ragged, column-scaled
+    (2048, 256, 10, 1e-12, 14.0, 0),    # the ill-conditioned family at n = 2048
+    (96, 128, 0, 1e-10, 0.0, 3),        # level 0: one dense block
+    (300, 20, 3, 1e-8, 0.0, 4),         # deep tree, small leaves
+])
+def test_hqr_matches_oracle(n, nmin, k, tol, dec, seed):
+    inp = W.random_hodlr(n, nmin, k, seed=seed, col_scale_decades=dec)
+    _check_against_oracle(inp, tol)
+
+
+@pytest.mark.parametrize("n,nmin,k,seed", [(96, 16, 3, 1), (200, 24, 4, 3), (256, 32, 5, 4)])
+def test_hqr_no_truncation_equals_lapack(n, nmin, k, seed):
+    inp = W.random_hodlr(n, nmin, k, seed=seed)
+    Ad = W.to_dense(inp)
+    M = U.gpu_qr(inp, 0.0, anorm=1.0, rank_cap=256)
+    st, _ = M.status()
+    assert st == 0
+    Y, T, R = (x.cpu().numpy() for x in U.factors_dense(M))
+    V, Tl, Rl = dgeqrt_full(Ad)
+    tolx = 1e-13 * np.linalg.cond(Ad)
+    np.testing.assert_allclose(R, Rl, atol=tolx * np.linalg.norm(Ad, 2))
+    np.testing.assert_allclose(Y, V, atol=tolx)
+    np.testing.assert_allclose(T, Tl, atol=tolx)
+
+
+def test_hqr_zero_rank_blocks():
+    inp = W.zero_rank(400, 50, seed=2)
+    M = U.gpu_qr(inp, 1e-10, anorm=1.0)
+    Y, T, R = (x.cpu().numpy() for x in U.factors_dense(M))
+    ranges = W.node_ranges(inp.leaf_sizes)
+    nl = len(inp.leaf_sizes)
+    for j in range(nl):
+        lo, hi = ranges[nl - 1 + j]
+        V, Tl, Rl = dgeqrt_full(inp.leaves[j])
+        np.testing.assert_allclose(R[lo:hi, lo:hi], Rl, atol=1e-12)
+        np.testing.assert_allclose(Y[lo:hi, lo:hi], V, atol=1e-12)
+        np.testing.assert_allclose(T[lo:hi, lo:hi], Tl, atol=1e-12)
+    r12, r21, rT = M.ranks()
+    assert r12.max() == 0 and r21.max() == 0 and rT.max() == 0
+
+
+def test_graph_replay_is_bitwise_equal_to_eager():
+    inp = W.random_hodlr(1024, 128, 5, seed=5)
+    M1 = U.gpu_qr(inp, 1e-10, anorm=0.0)
+    M2 = U.gpu_qr(inp, 1e-10, anorm=0.0, graph=True)
+    M2.qr_graph(1e-10, 0.0)     # second replay from the snapshot
+    U.ctx().sync()
+    for which in (1, 2, 3):
+        a = U.dense_of(M1, which).cpu().numpy()
+        b = U.dense_of(M2, which).cpu().numpy()
+        assert np.array_equal(a, b)
+
+
+def test_apply_and_solve():
+    inp = W.random_hodlr(1000, 125, 6, seed=6)
+    Ad = W.to_dense(inp)
+    res = O.hqr(O.from_input(inp), 1e-12)
+    M = U.gpu_qr(inp, 1e-12, anorm=res.anorm)
+    Bm = W.rhs(1000, 5, seed=1)
+    Q = res.Q_dense()
+    for fn, ref in (("apply_q", Q @ Bm), ("apply_qt", Q.T @ Bm)):
+        tb, pb, ld = U.dev(Bm)
+        getattr(M, fn)(5, pb, ld)
+        np.testing.assert_allclose(U.host(tb, 1000, 5), ref, atol=1e-10 * np.abs(ref).max())
+    tb, pb, ld = U.dev(Bm)
+    assert M.solve(5, pb, ld) == 0
+    x = U.host(tb, 1000, 5)
+    xo = O.solve(res, Bm)
+    np.testing.assert_allclose(Ad @ x, Bm, atol=1e-8 * np.abs(Bm).max())
+    np.testing.assert_allclose(x, xo, atol=1e-8 * np.abs(xo).max())
+
+
+def test_flop_counts_match_oracle():
+    inp = W.random_hodlr(1024, 128, 5, seed=0)
+    O.reset_counters()
+    res = O.hqr(O.from_input(inp), 1e-10)
+    M = U.gpu_qr(inp, 1e-10, anorm=0.0)
+    f = M.flops()
+    ref = dict(O.FLOPS)
+    assert abs(f["a4_leaf_qr"] - ref["a4_leaf_qr"]) <= 0.05 * ref["a4_leaf_qr"]
+    assert abs(f["total"] - sum(ref.values())) <= 0.15 * sum(ref.values())
+
+
+def test_invalid_arguments_are_rejected():
+    from paper_1809_10585_gb300 import binding as B
+    inp = W.random_hodlr(256, 32, 3, seed=0)
+    bad = W.HodlrInput(inp.n, list(inp.leaf_sizes), inp.leaves, inp.U12, inp.V12, inp.U21, inp.V21)
+    bad.leaf_sizes[0] += 1                   # sizes no longer sum to n
+    with pytest.raises(B.HodlrError) as e:
+        B.Matrix(U.ctx(), bad)
+    assert e.value.code == B.HODLR_EINVAL
+    M = B.Matrix(U.ctx(), inp)
+    tb, pb, ld = U.dev(np.ones((256, 1)))
+    assert B.lib().hodlr_solve(U.ctx().h, M.h, 1, B._VP(pb), ld) == B.HODLR_ESTATE   # before qr
