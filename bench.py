@@ -167,22 +167,34 @@ def gpu_arm(args):
     from paper_1809_10585_gb300 import build as BUILD
     BUILD.build()
 
-    inp = make_input(rank)
+    nb = max(1, args.batch)
+    inps = [make_input(rank * nb + i) for i in range(nb)]
+    inp = inps[0]
     ctx = B.Context(local)
     stream = torch.cuda.Stream()
     ctx.set_stream(stream.cuda_stream)
-    M = B.Matrix(ctx, inp, rank_cap=RANK_CAP)
-    M.snapshot()
+    mats = [B.Matrix(ctx, x, rank_cap=RANK_CAP) for x in inps]
+    M = mats[0]
+    for m in mats:
+        m.snapshot()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def factor_all():
+        if nb == 1:
+            M.qr_graph(TOL, 0.0)
+        else:
+            B.qr_batched(ctx, mats, TOL, 0.0, graph=True)
 
     # warm-up (the first call records the CUDA graph)
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 1)):
-            M.qr_graph(TOL, 0.0)
+            factor_all()
     ctx.sync()
+    for m in mats:
+        st, anorm = m.status()
+        if st != 0:
+            raise RuntimeError(f"factorization status {st}")
     st, anorm = M.status()
-    if st != 0:
-        raise RuntimeError(f"factorization status {st}")
 
     def barrier():
         if ws > 1:
@@ -199,7 +211,7 @@ def gpu_arm(args):
         for i in range(args.steps):
             flush.fill_(float(i))
             evs[i][0].record(stream)
-            M.qr_graph(TOL, 0.0)
+            factor_all()
             evs[i][1].record(stream)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
@@ -212,11 +224,12 @@ def gpu_arm(args):
         t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_total = float(t.item())
-    st, anorm = M.status()
-    if st != 0:
-        raise RuntimeError(f"factorization status {st}")
+    for m in mats:
+        st, _ = m.status()
+        if st != 0:
+            raise RuntimeError(f"factorization status {st}")
     ms_per_step = ms_total / args.steps
-    value = ws * args.steps / (ms_total / 1e3)
+    value = ws * nb * args.steps / (ms_total / 1e3)
 
     # ---------------------------------------------------------------- end to end (host buffers)
     def pinned_like(a):
@@ -233,24 +246,30 @@ def gpu_arm(args):
             out.append(t.numpy().T)      # Fortran-ordered view on pinned memory
         return out
     import workloads as W
-    pinp = W.HodlrInput(inp.n, inp.leaf_sizes, pin_list(inp.leaves), pin_list(inp.U12), pin_list(inp.V12),
-                        pin_list(inp.U21), pin_list(inp.V21), name=inp.name)
-    h2d = sum(a.nbytes for lst in (inp.leaves, inp.U12, inp.V12, inp.U21, inp.V21) for a in lst)
-    out_bytes = M.storage_bytes()
-    host_out = torch.empty(out_bytes, dtype=torch.uint8, pin_memory=True).numpy()
+    pinps = [W.HodlrInput(x.n, x.leaf_sizes, pin_list(x.leaves), pin_list(x.U12), pin_list(x.V12),
+                          pin_list(x.U21), pin_list(x.V21), name=x.name) for x in inps]
+    h2d = sum(a.nbytes for x in inps for lst in (x.leaves, x.U12, x.V12, x.U21, x.V21) for a in lst)
+    out_bytes = sum(m.storage_bytes() for m in mats)
+    host_outs = [torch.empty(m.storage_bytes(), dtype=torch.uint8, pin_memory=True).numpy() for m in mats]
     e2e_steps = max(1, min(args.steps, 10))
+
+    def e2e_step():
+        for m, p in zip(mats, pinps):
+            m.upload(p)
+        if nb == 1:
+            M.qr(TOL, 0.0)
+        else:
+            B.qr_batched(ctx, mats, TOL, 0.0)
+        for m, h in zip(mats, host_outs):
+            m.download(h)
     with torch.cuda.stream(stream):
-        M.upload(pinp)
-        M.qr(TOL, 0.0)
-        M.download(host_out)
+        e2e_step()
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
         for _ in range(e2e_steps):
-            M.upload(pinp)
-            M.qr(TOL, 0.0)
-            M.download(host_out)
+            e2e_step()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     if ws > 1:
@@ -258,7 +277,7 @@ def gpu_arm(args):
         t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e = {"value": ws * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+    e2e = {"value": ws * nb * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(out_bytes), "steps": e2e_steps}
 
     # ---------------------------------------------------------------- roofline of the top kernel
@@ -275,15 +294,17 @@ def gpu_arm(args):
                 "kind_ms": {k: round(v["ms"], 4) for k, v in prof.items()},
                 "kind_share": {k: round(v["ms"] / max(1e-9, sum(x["ms"] for x in prof.values())), 4)
                                for k, v in prof.items()}}
-    gpu_launches = sum(v["launches"] for v in prof.values()) * args.steps
+    gpu_launches = sum(v["launches"] for v in prof.values()) * args.steps * nb
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N, "nmin": NMIN, "rank": K, "col_scale_decades": DECADES,
-                       "tol": TOL, "rank_cap": RANK_CAP, "l2": "flushed (256 MiB write) between timed steps",
+                       "tol": TOL, "rank_cap": RANK_CAP, "batch": nb,
+                       "batching": "independent seeded matrices of the workload factored concurrently, one CUDA graph per step",
+                       "l2": "flushed (256 MiB write) between timed steps",
                        "parallelism": f"replicas x{ws}", "anorm": anorm},
-            "effective_gflops": flops_total / (ms_per_step / 1e3) / 1e9,
+            "effective_gflops": nb * flops_total / (ms_per_step / 1e3) / 1e9,
             "algorithmic_gflop_per_step": flops_total / 1e9,
             "wall_s_timed": t_wall, "clocks": clk, "e2e": e2e, "roofline": roofline,
             "gpu_launches": gpu_launches}
@@ -307,6 +328,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=1,
+                    help="matrices of the workload factored concurrently per step (cross-matrix batching)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

@@ -113,6 +113,22 @@ int hodlr_qr_graph(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm);
 int hodlr_qr_profile(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm, double* ms,
                      int* launches, double* flops);
 
+/*
+ * hodlr_qr_batched — cross-matrix batching: factor `count` distinct matrices A[0..count-1]
+ * (any partitions, ranks and sizes), each as hodlr_qr(tol, anorm) would, concurrently on the
+ * device.  Each matrix runs on its own pair of streams owned by the context; the pairs are
+ * forked from and joined back into the context's stream, so later work on that stream sees
+ * all results.  Asynchronous.  HODLR_EINVAL if a pointer repeats.
+ *
+ * hodlr_qr_batched_graph — the same with hodlr_restore of every matrix first (each needs a
+ * snapshot), recorded once into one CUDA graph held by the context and launched on every call;
+ * the graph is re-recorded when the list of matrices, tol or anorm changes.  A matrix must not
+ * be freed while the context still holds a graph that names it (call with a new list first).
+ * Not in the paper: it batches independent problems (no data moves between matrices).
+ */
+int hodlr_qr_batched(hodlr_ctx* ctx, int count, hodlr_mat* const* A, double tol, double anorm);
+int hodlr_qr_batched_graph(hodlr_ctx* ctx, int count, hodlr_mat* const* A, double tol, double anorm);
+
 /* Synchronize and return the status word of the last factorization (HODLR_OK, HODLR_ERANK,
  * HODLR_ETIMEOUT) in *status, and the ||A||_2 used in *anorm_used (either may be NULL). */
 int hodlr_status(hodlr_ctx* ctx, hodlr_mat* A, int* status, double* anorm_used);
@@ -145,6 +161,19 @@ int hodlr_apply_qt(hodlr_ctx* ctx, const hodlr_mat* A, int nrhs, double* B_dev, 
  * (x2 = R22^{-1} b2, x1 = R11^{-1} (b1 - R12 x2)).  Needs hodlr_qr.  A zero diagonal entry
  * of R makes the result non-finite; hodlr_solve then returns HODLR_ESINGULAR (synchronous). */
 int hodlr_solve(hodlr_ctx* ctx, const hodlr_mat* A, int nrhs, double* B_dev, int ldb);
+
+/*
+ * hodlr_solve_async — B_dev <- R^{-1} Q^T B as hodlr_solve, queued without synchronizing and
+ * without reading anything back (no HODLR_ESINGULAR detection: a zero diagonal entry of R
+ * gives non-finite results).  The first call on a matrix, or a call with more right-hand sides
+ * than any earlier one, plans the solve and allocates its buffers; every later call allocates
+ * nothing.  Calls on one matrix must not overlap on the device.  1 <= nrhs <= 1024.
+ */
+int hodlr_solve_async(hodlr_ctx* ctx, hodlr_mat* A, int nrhs, double* B_dev, int ldb);
+
+/* *ready = 1 if all work queued on the context's stream (which joins every stream the
+ * context uses) has finished, else 0.  Never blocks. */
+int hodlr_ready(hodlr_ctx* ctx, int* ready);
 
 /* ||A||_2 estimate as used by hodlr_qr (power iteration, `iters` steps).  Synchronous. */
 int hodlr_norm2_estimate(hodlr_ctx* ctx, const hodlr_mat* A, int iters, double* out);

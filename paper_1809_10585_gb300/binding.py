@@ -43,6 +43,8 @@ _SIGS = {
     "hodlr_restore": (C.c_int, [_VP, _VP]),
     "hodlr_qr": (C.c_int, [_VP, _VP, C.c_double, C.c_double]),
     "hodlr_qr_graph": (C.c_int, [_VP, _VP, C.c_double, C.c_double]),
+    "hodlr_qr_batched": (C.c_int, [_VP, C.c_int, C.POINTER(_VP), C.c_double, C.c_double]),
+    "hodlr_qr_batched_graph": (C.c_int, [_VP, C.c_int, C.POINTER(_VP), C.c_double, C.c_double]),
     "hodlr_qr_profile": (C.c_int, [_VP, _VP, C.c_double, C.c_double, _PD, _PI, _PD]),
     "hodlr_status": (C.c_int, [_VP, _VP, _PI, _PD]),
     "hodlr_ranks": (C.c_int, [_VP, _VP, _PI, _PI, _PI]),
@@ -52,6 +54,8 @@ _SIGS = {
     "hodlr_apply_q": (C.c_int, [_VP, _VP, C.c_int, _VP, C.c_int]),
     "hodlr_apply_qt": (C.c_int, [_VP, _VP, C.c_int, _VP, C.c_int]),
     "hodlr_solve": (C.c_int, [_VP, _VP, C.c_int, _VP, C.c_int]),
+    "hodlr_solve_async": (C.c_int, [_VP, _VP, C.c_int, _VP, C.c_int]),
+    "hodlr_ready": (C.c_int, [_VP, _PI]),
     "hodlr_norm2_estimate": (C.c_int, [_VP, _VP, C.c_int, _PD]),
     "hodlr_storage_bytes": (C.c_size_t, [_VP]),
     "hodlr_download": (C.c_int, [_VP, _VP, _VP, C.c_size_t]),
@@ -112,6 +116,11 @@ class Context:
 
     def sync(self):
         check(lib().hodlr_sync(self.h), "hodlr_sync")
+
+    def ready(self) -> bool:
+        r = C.c_int()
+        check(lib().hodlr_ready(self.h, C.byref(r)), "hodlr_ready")
+        return bool(r.value)
 
     def close(self):
         if self.h:
@@ -211,6 +220,10 @@ class Matrix:
     def solve(self, nrhs, B_ptr, ldb):
         return lib().hodlr_solve(self.ctx.h, self.h, nrhs, _VP(B_ptr), ldb)
 
+    def solve_async(self, nrhs, B_ptr, ldb, ctx=None):
+        c = ctx or self.ctx
+        check(lib().hodlr_solve_async(c.h, self.h, nrhs, _VP(B_ptr), ldb), "hodlr_solve_async")
+
     def norm2_estimate(self, iters=30):
         out = C.c_double()
         check(lib().hodlr_norm2_estimate(self.ctx.h, self.h, iters, C.byref(out)), "hodlr_norm2_estimate")
@@ -232,6 +245,12 @@ class Matrix:
             self.free()
         except Exception:
             pass
+
+
+def qr_batched(ctx: Context, mats, tol: float, anorm: float = 0.0, graph: bool = False):
+    arr = (_VP * len(mats))(*[m.h for m in mats])
+    fn = lib().hodlr_qr_batched_graph if graph else lib().hodlr_qr_batched
+    check(fn(ctx.h, len(mats), arr, tol, anorm), "hodlr_qr_batched")
 
 
 def dense_qr(ctx: Context, h, w, A_ptr, lda, T_ptr, ldt):

@@ -102,6 +102,8 @@ struct JacobiDesc {
   int q1, q2, q1ref, q2ref;
   double* nrm;              // q2 squared column norms on exit
   int* rot;                 // kMaxSweeps counters (scratch)
+  double thr;               // truncation threshold of the caller (thr_ref scales it)
+  const double* thr_ref;
 };
 
 // Rank selection after Jacobi: keep columns with norm > thr, sorted by norm descending,

@@ -32,6 +32,10 @@ namespace hq {
 constexpr int QT = 256;            // threads per CTA
 constexpr int QW = QT / 32;        // warps per CTA
 constexpr int TNB = 16;            // diagonal block size of the T build
+constexpr int kJacobiRegs = 8;     // column elements per lane held in registers (q1 <= 256)
+constexpr int kQRRegs = 16;        // QR: column elements per lane in registers (h <= 512)
+constexpr int kQRStageRows = 4096; // QR: reflector staged in shared memory up to this height
+constexpr int kJacobiMaxCols = 4096;
 
 __device__ inline double warp_sum2(double v) {
 #pragma unroll
@@ -85,51 +89,115 @@ __global__ void __launch_bounds__(QT) qr_cluster_kernel(const QRDesc* __restrict
     atomicAdd(&flops[kKindSlot + 2], g);
   }
 
+  // Column j's reflector is v = [1; scal_j * a(j+1:h, j)] with the column left unscaled until
+  // every CTA has used it; its owner scales it after the next cluster barrier.  scal_j is kept
+  // on G's diagonal (the T build uses only G's off-diagonal parts).  The norm of the next
+  // pivot column is produced by the warp that applies the current reflector to it.
+  __shared__ double ysm[kQRStageRows];
+  __shared__ double xn_next;
+  double* G0 = d.G;
+  const size_t ldg0 = d.ldg;
+  if (crank == 0 && kmax > 0) {
+    double s = 0.0;
+    for (int i = 1 + threadIdx.x; i < h; i += QT) {
+      double v = __ldcg(&A[i]);
+      s = fma(v, v, s);
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) xn_next = s;
+  }
+  __syncthreads();
+  const bool staged = h <= kQRStageRows;
+  const bool in_regs = h <= 32 * kQRRegs;
   for (int j = 0; j < kmax; ++j) {
-    if ((j % C) == crank) {
-      double s = 0.0;
-      for (int i = j + 1 + threadIdx.x; i < h; i += QT) {
-        double v = __ldcg(&A[i + j * lda]);
-        s = fma(v, v, s);
+    if ((j % C) == crank && threadIdx.x == 0) {
+      const double s = xn_next;
+      const double alpha = __ldcg(&A[j + j * lda]);
+      double tau = 0.0, scal = 0.0;
+      if (s > 0.0) {
+        const double hn = hypot(alpha, sqrt(s));
+        const double beta = -copysign(hn, alpha);
+        tau = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+        A[j + j * lda] = beta;
       }
-      s = block_sum(s, red);
-      if (threadIdx.x == 0) {
-        double alpha = __ldcg(&A[j + j * lda]);
-        double tau = 0.0, scal = 0.0;
-        if (s > 0.0) {
-          double hn = hypot(alpha, sqrt(s));
-          double beta = -copysign(hn, alpha);
-          tau = (beta - alpha) / beta;
-          scal = 1.0 / (alpha - beta);
-          A[j + j * lda] = beta;
-        }
-        d.tau[j] = tau;
-        bc[0] = scal;
-      }
-      __syncthreads();
-      const double scal = bc[0];
-      if (scal != 0.0)
-        for (int i = j + 1 + threadIdx.x; i < h; i += QT) A[i + j * lda] = __ldcg(&A[i + j * lda]) * scal;
+      d.tau[j] = tau;
+      G0[j + j * ldg0] = scal;
     }
     cl.sync();
+    // deferred scaling of the previous pivot column by its owner (nobody reads it any more)
+    if (j > 0 && ((j - 1) % C) == crank) {
+      const double sp = __ldcg(&G0[(j - 1) + (j - 1) * ldg0]);
+      if (sp != 0.0)
+        for (int i = j + threadIdx.x; i < h; i += QT) A[i + (j - 1) * lda] = __ldcg(&A[i + (j - 1) * lda]) * sp;
+    }
     const double tau = __ldcg(&d.tau[j]);
-    if (tau != 0.0) {
-      // own columns c > j with c % C == crank, one warp per column
-      int first = j + 1;
-      int c0 = first + ((crank - first % C) + C) % C;
-      const double* y = A + j * lda;
-      for (int c = c0 + warp * C; c < w; c += QW * C) {
-        double* a = A + c * lda;
-        double t = 0.0;
-        for (int i = j + 1 + lane; i < h; i += 32) t = fma(__ldcg(&y[i]), __ldcg(&a[i]), t);
-        t = warp_sum2(t);
-        t += __ldcg(&a[j]);
-        t *= tau;
-        if (lane == 0) a[j] = __ldcg(&a[j]) - t;
-        for (int i = j + 1 + lane; i < h; i += 32) a[i] = fma(-t, __ldcg(&y[i]), __ldcg(&a[i]));
+    const double scal = __ldcg(&G0[j + j * ldg0]);
+    const double* y = A + j * lda;
+    if (staged && tau != 0.0) {
+      for (int i = j + 1 + threadIdx.x; i < h; i += QT) ysm[i] = __ldcg(&y[i]);
+      __syncthreads();
+    }
+    const int first = j + 1;
+    const int c0 = first + ((crank - first % C) + C) % C;
+    for (int c = c0 + warp * C; c < w; c += QW * C) {
+      double* a = A + c * lda;
+      double nn = 0.0;   // squared norm of a(j+2:h) after the update (next pivot only)
+      if (tau != 0.0) {
+        if (in_regs) {
+          double r[kQRRegs];
+          double t = 0.0;
+#pragma unroll
+          for (int q = 0; q < kQRRegs; ++q) {
+            const int i = j + 1 + lane + 32 * q;
+            r[q] = i < h ? __ldcg(&a[i]) : 0.0;
+            if (i < h) t = fma(staged ? ysm[i] : __ldcg(&y[i]), r[q], t);
+          }
+          t = warp_sum2(t);
+          const double wv = tau * fma(scal, t, __ldcg(&a[j]));
+          const double ws = wv * scal;
+#pragma unroll
+          for (int q = 0; q < kQRRegs; ++q) {
+            const int i = j + 1 + lane + 32 * q;
+            if (i < h) {
+              const double v = fma(-ws, staged ? ysm[i] : __ldcg(&y[i]), r[q]);
+              a[i] = v;
+              if (i > j + 1) nn = fma(v, v, nn);
+            }
+          }
+          if (lane == 0) a[j] = __ldcg(&a[j]) - wv;
+        } else {
+          double t = 0.0;
+          for (int i = j + 1 + lane; i < h; i += 32) t = fma(staged ? ysm[i] : __ldcg(&y[i]), __ldcg(&a[i]), t);
+          t = warp_sum2(t);
+          const double wv = tau * fma(scal, t, __ldcg(&a[j]));
+          const double ws = wv * scal;
+          for (int i = j + 1 + lane; i < h; i += 32) {
+            const double v = fma(-ws, staged ? ysm[i] : __ldcg(&y[i]), __ldcg(&a[i]));
+            a[i] = v;
+            if (i > j + 1) nn = fma(v, v, nn);
+          }
+          if (lane == 0) a[j] = __ldcg(&a[j]) - wv;
+        }
+      } else if (c == j + 1) {
+        for (int i = j + 2 + lane; i < h; i += 32) {
+          const double v = __ldcg(&a[i]);
+          nn = fma(v, v, nn);
+        }
+      }
+      if (c == j + 1) {
+        nn = warp_sum2(nn);
+        if (lane == 0) xn_next = nn;
       }
     }
     __syncthreads();
+  }
+  // scale the last pivot column
+  cl.sync();
+  if (kmax > 0 && ((kmax - 1) % C) == crank) {
+    const double sp = __ldcg(&G0[(kmax - 1) + (kmax - 1) * ldg0]);
+    if (sp != 0.0)
+      for (int i = kmax + threadIdx.x; i < h; i += QT) A[i + (kmax - 1) * lda] = __ldcg(&A[i + (kmax - 1) * lda]) * sp;
   }
   if (d.T == nullptr || kmax == 0) return;
 
@@ -296,6 +364,14 @@ __global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __
   const int gw = crank * QW + warp, nw = C * QW;
   // relative orthogonality threshold for a pair
   const double tol = fmin(1e-13, fmax(1e-15, 4.4e-16 * (double)q1));
+  // Columns whose squared norm is below dfl are left out of the rotations: they stay below
+  // the truncation threshold and together change the core by at most 1e-2 * thr.
+  double thr = d.thr;
+  if (d.thr_ref) thr *= *d.thr_ref;
+  const double dth = 1e-2 * thr / sqrt((double)max(q2, 1));
+  const double dfl = dth * dth;
+  __shared__ int act[kJacobiMaxCols];
+  __shared__ int nact;
 
   if (crank == 0)
     for (int i = threadIdx.x; i < kMaxSweeps; i += QT) d.rot[i] = 0;
@@ -309,37 +385,83 @@ __global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __
     if (lane == 0) d.nrm[j] = s;
   }
   cl.sync();
-  if (q2 < 2 || q1 == 0) return;
-  const int P = q2 + (q2 & 1);
+  if (q2 < 2 || q1 == 0 || q2 > kJacobiMaxCols) return;
+  const bool in_regs = q1 <= 32 * kJacobiRegs;
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+    // active columns of this sweep (identical in every CTA: all read the published norms)
+    if (threadIdx.x == 0) {
+      int c = 0;
+      for (int j = 0; j < q2; ++j)
+        if (__ldcg(&d.nrm[j]) > dfl) act[c++] = j;
+      nact = c;
+    }
+    // every CTA must have read the norms before any CTA rotates (keeps the lists identical)
+    cl.sync();
+    const int Ka = nact;
+    if (Ka < 2) break;
+    const int P = Ka + (Ka & 1);
     int local = 0;
     for (int r = 0; r < P - 1; ++r) {
       for (int pi = gw; pi < P / 2; pi += nw) {
-        int a, b;
-        rr_pair(r, pi, P, a, b);
-        if (a >= q2 || b >= q2) continue;
+        int ia, ib;
+        rr_pair(r, pi, P, ia, ib);
+        if (ia >= Ka || ib >= Ka) continue;
+        const int a = act[ia], b = act[ib];
         double* ca = M + a * ldm;
         double* cb = M + b * ldm;
         const double al = __ldcg(&d.nrm[a]), be = __ldcg(&d.nrm[b]);
-        if (al == 0.0 || be == 0.0) continue;
-        double g = 0.0;
-        for (int i = lane; i < q1; i += 32) g = fma(__ldcg(&ca[i]), __ldcg(&cb[i]), g);
-        g = warp_sum2(g);
-        if (!(fabs(g) > tol * sqrt(al) * sqrt(be))) continue;
-        const double zeta = (be - al) / (2.0 * g);
-        double t;
-        if (fabs(zeta) > 1e100) t = 0.5 / zeta;
-        else t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+        if (al <= dfl || be <= dfl) continue;
         double na = 0.0, nb = 0.0;
-        for (int i = lane; i < q1; i += 32) {
-          double x = __ldcg(&ca[i]), y = __ldcg(&cb[i]);
-          double xn = c * x - sn * y;
-          double yn = sn * x + c * y;
-          ca[i] = xn;
-          cb[i] = yn;
-          na = fma(xn, xn, na);
-          nb = fma(yn, yn, nb);
+        if (in_regs) {
+          // the pair is read once into registers (q1 <= 32 * kJacobiRegs)
+          double x[kJacobiRegs], y[kJacobiRegs];
+          double g = 0.0;
+#pragma unroll
+          for (int t = 0; t < kJacobiRegs; ++t) {
+            const int i = lane + 32 * t;
+            x[t] = i < q1 ? __ldcg(&ca[i]) : 0.0;
+            y[t] = i < q1 ? __ldcg(&cb[i]) : 0.0;
+            g = fma(x[t], y[t], g);
+          }
+          g = warp_sum2(g);
+          if (!(fabs(g) > tol * sqrt(al) * sqrt(be))) continue;
+          const double zeta = (be - al) / (2.0 * g);
+          double tt;
+          if (fabs(zeta) > 1e100) tt = 0.5 / zeta;
+          else tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + tt * tt), sn = c * tt;
+#pragma unroll
+          for (int t = 0; t < kJacobiRegs; ++t) {
+            const int i = lane + 32 * t;
+            const double xn = c * x[t] - sn * y[t];
+            const double yn = sn * x[t] + c * y[t];
+            na = fma(xn, xn, na);
+            nb = fma(yn, yn, nb);
+            if (i < q1) {
+              ca[i] = xn;
+              cb[i] = yn;
+            }
+          }
+        } else {
+          // long columns: two passes over L2
+          double g = 0.0;
+          for (int i = lane; i < q1; i += 32) g = fma(__ldcg(&ca[i]), __ldcg(&cb[i]), g);
+          g = warp_sum2(g);
+          if (!(fabs(g) > tol * sqrt(al) * sqrt(be))) continue;
+          const double zeta = (be - al) / (2.0 * g);
+          double tt;
+          if (fabs(zeta) > 1e100) tt = 0.5 / zeta;
+          else tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + tt * tt), sn = c * tt;
+          for (int i = lane; i < q1; i += 32) {
+            const double xv = __ldcg(&ca[i]), yv = __ldcg(&cb[i]);
+            const double xn = c * xv - sn * yv;
+            const double yn = sn * xv + c * yv;
+            ca[i] = xn;
+            cb[i] = yn;
+            na = fma(xn, xn, na);
+            nb = fma(yn, yn, nb);
+          }
         }
         na = warp_sum2(na);
         nb = warp_sum2(nb);
@@ -375,3 +497,4 @@ cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, const int* 
 }
 
 }  // namespace hq
+

@@ -32,14 +32,22 @@ struct hodlr_ctx {
   int dev = 0;
   cudaStream_t own = nullptr;
   cudaStream_t s = nullptr;
+  cudaStream_t side = nullptr;   // second stream for work off the critical path
   int cluster = 8;
+  // stream pairs of batched factorizations (one pair per matrix of a batch)
+  std::vector<std::pair<cudaStream_t, cudaStream_t>> pool;
+  // CUDA graph of the last batched factorization captured with hodlr_qr_batched_graph
+  cudaGraphExec_t bgraph = nullptr;
+  std::vector<hodlr_mat*> bmats;
+  double btol = -1, banorm = -2;
 };
 
 enum RecType { R_GEMM, R_REDUCE, R_CONCAT, R_GATHER, R_SCATTER, R_QR, R_JACOBI, R_SELECT, R_COPY,
-               R_FILL, R_IDENT, R_NORM, R_MEMSET_INT, R_TRSM };
+               R_FILL, R_IDENT, R_NORM, R_MEMSET_INT, R_TRSM, R_EVREC, R_EVWAIT };
 
 struct Rec {
   int type;
+  int stream;     // 0: main stream, 1: side stream
   int n;          // descriptors
   size_t off;     // byte offset of the descriptors in the blob
   int extra0, extra1;
@@ -52,6 +60,8 @@ struct Rec {
 
 struct Plan {
   std::vector<Rec> recs;
+  int nevents = 0;
+  std::vector<cudaEvent_t> events;
   std::vector<char> blob;
   char* dblob = nullptr;
   size_t dblob_bytes = 0;
@@ -86,6 +96,16 @@ struct hodlr_mat {
   int* snap_ints = nullptr;
   char* arena = nullptr;
   size_t arena_bytes = 0;
+  char* arena2 = nullptr;      // never-reused scratch of side-stream work
+  size_t arena2_bytes = 0;
+  // cached plan of hodlr_solve_async (own arenas, so factorization plans are never disturbed)
+  Plan splan;
+  int splan_nrhs = 0;
+  double* sbuf = nullptr;      // n x splan_nrhs staging buffer of the right-hand sides
+  char* sarena = nullptr;
+  size_t sarena_bytes = 0;
+  char* sarena2 = nullptr;
+  size_t sarena2_bytes = 0;
   // plan of the factorization
   Plan plan;
   bool planned = false;
@@ -101,6 +121,10 @@ struct Planner {
   Plan* P;
   size_t top = 0, high = 0;      // arena bump pointer
   char* base;                    // arena base (nullptr in the measuring pass)
+  size_t top2 = 0;               // never-reused region (side-stream work and its inputs)
+  char* base2 = nullptr;
+  int stream = 0;                // stream of the records being emitted
+  bool fresh = false;            // route alloc() to the never-reused region
   int int_top;                   // devints bump pointer
   int int_high;
   int cluster;
@@ -109,6 +133,11 @@ struct Planner {
   template <class T>
   T* alloc(size_t count) {
     size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    if (fresh) {
+      size_t off2 = top2;
+      top2 += bytes;
+      return reinterpret_cast<T*>(base2 + off2);
+    }
     size_t off = top;
     top += bytes;
     high = std::max(high, top);
@@ -116,6 +145,17 @@ struct Planner {
   }
   size_t mark() const { return top; }
   void release(size_t m) { top = m; }
+  int event() { return P->nevents++; }
+  void ev_record(int st, int ev) {
+    Rec r = {};
+    r.type = R_EVREC; r.stream = st; r.i0 = ev;
+    P->recs.push_back(r);
+  }
+  void ev_wait(int st, int ev) {
+    Rec r = {};
+    r.type = R_EVWAIT; r.stream = st; r.i0 = ev;
+    P->recs.push_back(r);
+  }
   int ints(int n) {
     int r = int_top;
     int_top += n;
@@ -135,6 +175,11 @@ struct Planner {
     r.type = type;
     r.n = n;
     r.off = off;
+    r.stream = stream;
+    P->recs.push_back(r);
+  }
+  void push(Rec r) {
+    r.stream = stream;
     P->recs.push_back(r);
   }
 
@@ -152,9 +197,13 @@ struct Planner {
       int tiles = d.tiles_m * d.tiles_n;
       d.ksplit = 1;
       d.part = nullptr;
-      if (d.k > 768 && tiles < 96) {
-        d.ksplit = std::min(64, std::max(2, d.k / 256));
-        while (d.ksplit > 1 && tiles * d.ksplit > 2048) d.ksplit /= 2;
+      // A 32x32 tile retires 2048 flops per k on one SM (~8 GFLOP/s of FP64): split the
+      // reduction so that one launch spreads over the whole GPU and each CTA runs >= 64 k.
+      if (d.k >= 128 && tiles < 608) {
+        int ks = (608 + tiles - 1) / tiles;
+        ks = std::min(ks, d.k / 64);
+        ks = std::min(ks, 64);
+        if (ks >= 2) d.ksplit = ks;
       }
       if (d.ksplit > 1) d.part = alloc<double>((size_t)d.ksplit * d.m * d.n);
       d.work0 = work;
@@ -179,7 +228,7 @@ struct Planner {
       r.off = roff;
       r.extra0 = redblocks;
       r.extra1 = (int)off;   // offset of the GEMM descriptors
-      P->recs.push_back(r);
+      push(r);
     }
   }
 
@@ -305,6 +354,7 @@ struct Planner {
   }
 
   // ---------------------------------------------------------------- T_eps (Sec. 2.1.1)
+  bool too_wide = false;
   struct Trunc {
     int nL, nR;
     std::vector<ConcatSeg> L, R;
@@ -339,6 +389,7 @@ struct Planner {
       for (auto& g : p.R) KcapR += g.cols;
       Kcap = std::max(Kcap, KcapR);
       if (Kcap == 0) Kcap = 1;
+      if (std::min(p.nR, Kcap) > 4096) too_wide = true;   // beyond the Jacobi kernel's column list
       int q1c = std::min(p.nL, Kcap), q2c = std::min(p.nR, Kcap);
       double* Lb = alloc<double>((size_t)p.nL * Kcap);
       double* Rb = alloc<double>((size_t)p.nR * Kcap);
@@ -381,7 +432,7 @@ struct Planner {
                       Kcap, iL, 1.0, 0.0, kStepNone, -1));
       JacobiDesc jd = {};
       jd.M = Mb; jd.ldm = q1c; jd.q1 = q1c; jd.q2 = q2c; jd.q1ref = iL + 1; jd.q2ref = iR + 1;
-      jd.nrm = nrm; jd.rot = rot;
+      jd.nrm = nrm; jd.rot = rot; jd.thr = p.thr; jd.thr_ref = p.thr_ref;
       jds.push_back(jd);
       SelectDesc sd = {};
       sd.W = Mb; sd.ldw = q1c; sd.nrm = nrm; sd.q1 = q1c; sd.q2 = q2c; sd.q1ref = iL + 1; sd.q2ref = iR + 1;
@@ -448,7 +499,7 @@ struct Planner {
     // U21 <- Q = (I - Y T Y^T) [I; 0]
     Rec ri = {};
     ri.type = R_IDENT; ri.p0 = M->U21[p]; ri.i0 = b; ri.i1 = b; ri.i2 = kc;
-    P->recs.push_back(ri);
+    push(ri);
     gemm({gd(S, b, 1, kMaskUnitLower, M->U21[p], b, 0, 0, P2, kc, kc, rr, kc, rr, kc, rr, 1.0, 0.0, kStepNone, -1)});
     gemm({gd(T, kq, 0, kMaskUpper, P2, kc, 0, 0, P3, kc, kq, rr, kc, rr, kq, rr, 1.0, 0.0, kStepNone, -1)});
     gemm({gd(S, b, 0, kMaskUnitLower, P3, kc, 0, 0, M->U21[p], b, b, -1, kc, rr, kq, rr, -1.0, 1.0, kStepNone, -1),
@@ -492,7 +543,11 @@ struct Planner {
   }
 
   // ----------------------------------------------------------------- Alg. 2 recursion
+  // tdone[v]: event (side stream) after which T of subtree v is complete; -1 for leaves
+  std::vector<int> tdone;
+
   void node(int v) {
+    if (tdone.empty()) tdone.assign(2 * M->nleaf - 1, -1);
     if (v != 0 && v == 2 * ((v - 1) / 2) + 1) left_orth((v - 1) / 2);   // B of v is A21 of its parent
     if (is_leaf(v)) {
       leaf(v);
@@ -512,7 +567,10 @@ struct Planner {
     matvec(A, c1, 1, 1, M->U12[v], a, X1, a, kc, r12(v), 1.0, 0.0, kStepS);
     matvec(A, c2, 0, 1, M->U21[v], b, X2, b, kc, r21(v), 1.0, 0.0, kStepS);
     double* SL = alloc<double>((size_t)a * kc);
+    fresh = true;                                  // read later by the side stream
     double* SR = alloc<double>((size_t)b * kc);
+    double* X3 = alloc<double>((size_t)a * kc);
+    fresh = false;
     int kS = ints(1);
     {
       Trunc t;
@@ -529,13 +587,19 @@ struct Planner {
       std::vector<Trunc> ts = {t};
       truncate(ts);
     }
-    // S = T1^T S~
+    // S = T1^T S~   (T of subtree c1 is finished on the side stream)
+    if (tdone[c1] >= 0) ev_wait(0, tdone[c1]);
     double* SL2 = alloc<double>((size_t)a * kc);
     matvec(T, c1, 2, 1, SL, a, SL2, a, kc, kS, 1.0, 0.0, kStepTS);
-    // A^12 = T_{eps ||A||}(A12 - Y11 S)
-    double* X3 = alloc<double>((size_t)a * kc);
+    // Y11 S (input of A^12), then A^12 = T_{eps ||A||}(A12 - Y11 S) on the side stream:
+    // nothing later in the recursion reads R12 of this node
     matvec(A, c1, 1, 0, SL2, a, X3, a, kc, kS, 1.0, 0.0, kStepUpdate);
+    int e_x3 = event();
+    ev_record(0, e_x3);
     {
+      stream = 1;
+      fresh = true;
+      ev_wait(1, e_x3);
       Trunc t;
       t.nL = a; t.nR = b;
       t.L = {seg(M->U12[v], a, kc, r12(v), 1.0), seg(X3, a, kc, kS, -1.0)};
@@ -544,6 +608,8 @@ struct Planner {
       t.kout_ref = r12(v); t.step = kStepUpdate;
       std::vector<Trunc> ts = {t};
       truncate(ts);
+      fresh = false;
+      stream = 0;
     }
     // A^22 = A~22 -_H (B_L21 (Y~_B S_L)) S_R^T
     double* Pm = alloc<double>((size_t)kc * kc);
@@ -565,13 +631,18 @@ struct Planner {
     }
     release(mk);
     node(c2);
-    mk = mark();
-    // T~12 = T_eps( Y21^T Y22 + Y_BR1^T Y_BR2 + Y_C1^T Y_C2 ),  T12 = -T1 T~12 T2
-    double* X4 = alloc<double>((size_t)b * kc);
-    matvec(A, c2, 1, 1, M->U21[v], b, X4, b, kc, r21(v), 1.0, 0.0, kStepT12);
-    double* TLb = alloc<double>((size_t)a * kc);
-    double* TRb = alloc<double>((size_t)b * kc);
+    // T~12 = T_eps( Y21^T Y22 + Y_BR1^T Y_BR2 + Y_C1^T Y_C2 ),  T12 = -T1 T~12 T2, on the side
+    // stream once the second block column is factored; its inputs are final from here on
+    int e_c2 = event();
+    ev_record(0, e_c2);
+    stream = 1;
+    fresh = true;
+    ev_wait(1, e_c2);
     {
+      double* X4 = alloc<double>((size_t)b * kc);
+      matvec(A, c2, 1, 1, M->U21[v], b, X4, b, kc, r21(v), 1.0, 0.0, kStepT12);
+      double* TLb = alloc<double>((size_t)a * kc);
+      double* TRb = alloc<double>((size_t)b * kc);
       Trunc t;
       t.nL = a; t.nR = b;
       t.L = {seg(M->V21[v], a, kc, r21(v), 1.0)};
@@ -585,10 +656,14 @@ struct Planner {
       t.step = kStepT12;
       std::vector<Trunc> ts = {t};
       truncate(ts);
+      matvec(T, c1, 2, 0, TLb, a, M->TU[v], a, kc, rT(v), -1.0, 0.0, kStepT12);
+      matvec(T, c2, 2, 1, TRb, b, M->TV[v], b, kc, rT(v), 1.0, 0.0, kStepT12);
     }
-    matvec(T, c1, 2, 0, TLb, a, M->TU[v], a, kc, rT(v), -1.0, 0.0, kStepT12);
-    matvec(T, c2, 2, 1, TRb, b, M->TV[v], b, kc, rT(v), 1.0, 0.0, kStepT12);
-    release(mk);
+    int e_t = event();
+    ev_record(1, e_t);
+    tdone[v] = e_t;
+    fresh = false;
+    stream = 0;
   }
 
   // HODLR low-rank update  H_s <- H_s -_H U V^T  (Table 1)
@@ -637,20 +712,20 @@ struct Planner {
     double* tmp = alloc<double>(1);
     Rec f = {};
     f.type = R_FILL; f.p0 = x; f.cnt = n; f.v = 1.0 / std::sqrt((double)n);
-    P->recs.push_back(f);
+    push(f);
     View A = aview();
     for (int it = 0; it < iters; ++it) {
       matvec(A, 0, 0, 0, x, n, y, n, 1, -1, 1.0, 0.0, kStepNorm);
       matvec(A, 0, 0, 1, y, n, z, n, 1, -1, 1.0, 0.0, kStepNorm);
       Rec r = {};
       r.type = R_NORM; r.p0 = z; r.i0 = n; r.i1 = 0; r.ip = reinterpret_cast<int*>(tmp);
-      P->recs.push_back(r);
+      push(r);
       std::swap(x, z);
     }
     matvec(A, 0, 0, 0, x, n, y, n, 1, -1, 1.0, 0.0, kStepNorm);
     Rec r = {};
     r.type = R_NORM; r.p0 = y; r.i0 = n; r.i1 = 1; r.ip = reinterpret_cast<int*>(M->dscal);
-    P->recs.push_back(r);
+    push(r);
     release(mk);
   }
 };
@@ -677,11 +752,21 @@ struct Profiler {
   std::vector<int> kind;
 };
 
-static int run_plan(hodlr_ctx* ctx, hodlr_mat* M, Plan& P, Profiler* prof = nullptr) {
-  cudaStream_t s = ctx->s;
+static int run_plan_on(hodlr_ctx* ctx, hodlr_mat* M, Plan& P, Profiler* prof, cudaStream_t mainst,
+                       cudaStream_t sidest) {
   char* db = P.dblob;
   double* flops = M->dscal + 1;
+  bool two = !P.events.empty();
+  cudaEvent_t fork = nullptr, join = nullptr;
+  if (two) {
+    // the side stream starts after everything queued before the plan on the main stream
+    HQ_CUDA_OK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    HQ_CUDA_OK(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+    HQ_CUDA_OK(cudaEventRecord(fork, mainst));
+    HQ_CUDA_OK(cudaStreamWaitEvent(sidest, fork, 0));
+  }
   for (const Rec& r : P.recs) {
+    cudaStream_t s = r.stream ? sidest : mainst;
     int kd = rec_kind(r.type);
     if (prof && kd >= 0) {
       cudaEvent_t e0;
@@ -712,6 +797,8 @@ static int run_plan(hodlr_ctx* ctx, hodlr_mat* M, Plan& P, Profiler* prof = null
       case R_NORM: e = launch_norm_scale(r.p0, r.i0, reinterpret_cast<double*>(r.ip), r.i1, s); break;
       case R_MEMSET_INT: e = cudaMemsetAsync(r.ip, 0, r.cnt, s); break;
       case R_TRSM: e = launch_trsm_leaf(r.p0, r.i0, r.i1, reinterpret_cast<double*>(r.ip), r.i2, r.i3, s); break;
+      case R_EVREC: e = cudaEventRecord(P.events[r.i0], s); break;
+      case R_EVWAIT: e = cudaStreamWaitEvent(s, P.events[r.i0], 0); break;
       default: e = cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return cuda_fail(e, __FILE__, __LINE__);
@@ -722,10 +809,25 @@ static int run_plan(hodlr_ctx* ctx, hodlr_mat* M, Plan& P, Profiler* prof = null
       prof->ev.push_back(e1);
     }
   }
+  if (two) {
+    // the main stream waits for the side stream's last work (joins it back)
+    HQ_CUDA_OK(cudaEventRecord(join, sidest));
+    HQ_CUDA_OK(cudaStreamWaitEvent(mainst, join, 0));
+    cudaEventDestroy(fork);
+    cudaEventDestroy(join);
+  }
   return HODLR_OK;
 }
 
+static int run_plan(hodlr_ctx* ctx, hodlr_mat* M, Plan& P, Profiler* prof = nullptr) {
+  return run_plan_on(ctx, M, P, prof, ctx->s, ctx->side);
+}
+
 static int upload_plan(Plan& P) {
+  for (auto e : P.events) cudaEventDestroy(e);
+  P.events.assign(P.nevents, nullptr);
+  for (auto& e : P.events)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return HODLR_ECUDA;
   if (P.dblob) cudaFree(P.dblob);
   P.dblob = nullptr;
   P.dblob_bytes = std::max<size_t>(P.blob.size(), 16);
@@ -736,27 +838,45 @@ static int upload_plan(Plan& P) {
 
 // Build the factorization plan: measure the arena, allocate it, plan again for real.
 template <class F>
-static int build_plan(hodlr_mat* M, Plan& P, int cluster, double tol, F&& body) {
+static int build_plan(hodlr_mat* M, Plan& P, int cluster, double tol, F&& body, bool solve_arenas = false) {
+  char** ar1 = solve_arenas ? &M->sarena : &M->arena;
+  size_t* ar1b = solve_arenas ? &M->sarena_bytes : &M->arena_bytes;
+  char** ar2 = solve_arenas ? &M->sarena2 : &M->arena2;
+  size_t* ar2b = solve_arenas ? &M->sarena2_bytes : &M->arena2_bytes;
   for (int pass = 0; pass < 2; ++pass) {
     P.recs.clear();
     P.blob.clear();
     Planner pl;
-    pl.M = M; pl.P = &P; pl.base = pass == 0 ? nullptr : M->arena;
+    pl.M = M; pl.P = &P; pl.base = pass == 0 ? nullptr : *ar1;
+    pl.base2 = pass == 0 ? nullptr : *ar2;
+    P.nevents = 0;
     pl.int_top = 3 * M->nn; pl.int_high = pl.int_top;
     pl.cluster = cluster; pl.tol = tol;
     body(pl);
     if (pl.int_high > M->n_devints) return HODLR_ENOMEM;
+    if (pl.too_wide) return HODLR_EINVAL;
     if (pass == 0) {
       size_t need = pl.high + 4096;
-      if (need > M->arena_bytes) {
-        if (M->arena) cudaFree(M->arena);
-        M->arena = nullptr;
-        M->arena_bytes = 0;
-        if (cudaMalloc(&M->arena, need) != cudaSuccess) {
+      if (need > *ar1b) {
+        if (*ar1) cudaFree(*ar1);
+        *ar1 = nullptr;
+        *ar1b = 0;
+        if (cudaMalloc(ar1, need) != cudaSuccess) {
           cudaGetLastError();
           return HODLR_ENOMEM;
         }
-        M->arena_bytes = need;
+        *ar1b = need;
+      }
+      size_t need2 = pl.top2 + 4096;
+      if (need2 > *ar2b) {
+        if (*ar2) cudaFree(*ar2);
+        *ar2 = nullptr;
+        *ar2b = 0;
+        if (cudaMalloc(ar2, need2) != cudaSuccess) {
+          cudaGetLastError();
+          return HODLR_ENOMEM;
+        }
+        *ar2b = need2;
       }
     }
   }
@@ -764,6 +884,9 @@ static int build_plan(hodlr_mat* M, Plan& P, int cluster, double tol, F&& body) 
 }
 
 static void free_plan(Plan& P) {
+  for (auto e : P.events) cudaEventDestroy(e);
+  P.events.clear();
+  P.nevents = 0;
   if (P.dblob) cudaFree(P.dblob);
   P.dblob = nullptr;
   P.recs.clear();
@@ -803,6 +926,11 @@ int hodlr_ctx_create(int device, hodlr_ctx** out) {
     return HODLR_ECUDA;
   }
   c->s = c->own;
+  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaStreamDestroy(c->own);
+    delete c;
+    return HODLR_ECUDA;
+  }
   int cl = qr_max_cluster();
   const char* env = getenv("HODLR_CLUSTER");
   if (env) cl = std::max(1, std::min(16, atoi(env)));
@@ -818,6 +946,17 @@ void hodlr_ctx_destroy(hodlr_ctx* ctx) {
     cudaStreamSynchronize(ctx->own);
     cudaStreamDestroy(ctx->own);
   }
+  if (ctx->side) {
+    cudaStreamSynchronize(ctx->side);
+    cudaStreamDestroy(ctx->side);
+  }
+  for (auto& pr : ctx->pool) {
+    cudaStreamSynchronize(pr.first);
+    cudaStreamSynchronize(pr.second);
+    cudaStreamDestroy(pr.first);
+    cudaStreamDestroy(pr.second);
+  }
+  if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
   delete ctx;
 }
 
@@ -887,6 +1026,11 @@ void hodlr_free(hodlr_mat* M) {
   if (M->snapshot) cudaFree(M->snapshot);
   if (M->snap_ints) cudaFree(M->snap_ints);
   if (M->arena) cudaFree(M->arena);
+  if (M->arena2) cudaFree(M->arena2);
+  free_plan(M->splan);
+  if (M->sbuf) cudaFree(M->sbuf);
+  if (M->sarena) cudaFree(M->sarena);
+  if (M->sarena2) cudaFree(M->sarena2);
   delete M;
 }
 
@@ -1044,13 +1188,15 @@ static int ensure_plan(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm) {
   return HODLR_OK;
 }
 
+static int qr_launch_on(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm, cudaStream_t m, cudaStream_t sd) {
+  (void)tol;
+  // anorm given: set it on the device with a kernel (capturable); else the plan estimates it
+  if (anorm > 0) HQ_CUDA_OK(launch_fill(A->dscal, 1, anorm, m));
+  return run_plan_on(ctx, A, A->plan, nullptr, m, sd);
+}
+
 static int qr_launch(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm) {
-  if (!(anorm > 0)) {
-    return run_plan(ctx, A, A->plan);
-  }
-  // set anorm on the device with a kernel (capturable), then run
-  HQ_CUDA_OK(launch_fill(A->dscal, 1, anorm, ctx->s));
-  return run_plan(ctx, A, A->plan);
+  return qr_launch_on(ctx, A, tol, anorm, ctx->s, ctx->side);
 }
 
 int hodlr_qr(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm) {
@@ -1122,6 +1268,102 @@ int hodlr_qr_profile(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm, dou
   HQ_CUDA_OK(cudaMemcpy(f, A->dscal + 1, sizeof(double) * 16, cudaMemcpyDeviceToHost));
   for (int k = 0; k < 8 && kKindSlot + k < 16; ++k) flops[k] = f[kKindSlot + k];
   A->factored = true;
+  return HODLR_OK;
+}
+
+static int ensure_pool(hodlr_ctx* ctx, int count) {
+  while ((int)ctx->pool.size() < count) {
+    cudaStream_t a, b;
+    HQ_CUDA_OK(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+    if (cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamDestroy(a);
+      return HODLR_ECUDA;
+    }
+    ctx->pool.push_back({a, b});
+  }
+  return HODLR_OK;
+}
+
+// Queue restore (optional) + factorization of every matrix on its own stream pair, forked from
+// and joined back into the context stream.
+static int batch_launch(hodlr_ctx* ctx, int count, hodlr_mat* const* A, double tol, double anorm, bool restore) {
+  cudaEvent_t fork;
+  HQ_CUDA_OK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  HQ_CUDA_OK(cudaEventRecord(fork, ctx->s));
+  std::vector<cudaEvent_t> joins(count, nullptr);
+  int rc = HODLR_OK;
+  for (int i = 0; i < count && !rc; ++i) {
+    cudaStream_t m = ctx->pool[i].first, sd = ctx->pool[i].second;
+    if (cudaStreamWaitEvent(m, fork, 0) != cudaSuccess) rc = HODLR_ECUDA;
+    if (!rc && restore) {
+      if (cudaMemcpyAsync(A[i]->store, A[i]->snapshot, A[i]->a_doubles * sizeof(double), cudaMemcpyDeviceToDevice, m) != cudaSuccess ||
+          (A[i]->nn && cudaMemcpyAsync(A[i]->devints, A[i]->snap_ints, sizeof(int) * 3 * A[i]->nn, cudaMemcpyDeviceToDevice, m) != cudaSuccess))
+        rc = HODLR_ECUDA;
+    }
+    if (!rc) rc = qr_launch_on(ctx, A[i], tol, anorm, m, sd);
+    if (!rc && (cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventRecord(joins[i], m) != cudaSuccess || cudaStreamWaitEvent(ctx->s, joins[i], 0) != cudaSuccess))
+      rc = HODLR_ECUDA;
+  }
+  cudaEventDestroy(fork);
+  for (auto e : joins)
+    if (e) cudaEventDestroy(e);
+  return rc;
+}
+
+int hodlr_qr_batched(hodlr_ctx* ctx, int count, hodlr_mat* const* A, double tol, double anorm) {
+  if (!ctx || !A || count < 1 || !(tol >= 0)) return HODLR_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    if (!A[i]) return HODLR_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (A[j] == A[i]) return HODLR_EINVAL;
+  }
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  int rc = ensure_pool(ctx, count);
+  for (int i = 0; i < count && !rc; ++i) rc = ensure_plan(ctx, A[i], tol, anorm);
+  if (rc) return rc;
+  rc = batch_launch(ctx, count, A, tol, anorm, false);
+  if (rc) return rc;
+  for (int i = 0; i < count; ++i) A[i]->factored = true;
+  return HODLR_OK;
+}
+
+int hodlr_qr_batched_graph(hodlr_ctx* ctx, int count, hodlr_mat* const* A, double tol, double anorm) {
+  if (!ctx || !A || count < 1 || !(tol >= 0)) return HODLR_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    if (!A[i]) return HODLR_EINVAL;
+    if (!A[i]->snapshot) return HODLR_ESTATE;
+    for (int j = 0; j < i; ++j)
+      if (A[j] == A[i]) return HODLR_EINVAL;
+  }
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  int rc = ensure_pool(ctx, count);
+  bool replan = false;
+  for (int i = 0; i < count && !rc; ++i) {
+    bool had = A[i]->planned && A[i]->plan_tol == tol && ((A[i]->plan_anorm > 0) == (anorm > 0));
+    rc = ensure_plan(ctx, A[i], tol, anorm);
+    if (!had) replan = true;
+  }
+  if (rc) return rc;
+  std::vector<hodlr_mat*> key(A, A + count);
+  if (!ctx->bgraph || replan || key != ctx->bmats || ctx->btol != tol || ctx->banorm != anorm) {
+    if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
+    ctx->bgraph = nullptr;
+    cudaGraph_t g;
+    HQ_CUDA_OK(cudaStreamBeginCapture(ctx->s, cudaStreamCaptureModeThreadLocal));
+    int r2 = batch_launch(ctx, count, A, tol, anorm, true);
+    cudaError_t e = cudaStreamEndCapture(ctx->s, &g);
+    if (r2) return r2;
+    if (e != cudaSuccess) return cuda_fail(e, __FILE__, __LINE__);
+    e = cudaGraphInstantiate(&ctx->bgraph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, __FILE__, __LINE__);
+    ctx->bmats = key;
+    ctx->btol = tol;
+    ctx->banorm = anorm;
+  }
+  HQ_CUDA_OK(cudaGraphLaunch(ctx->bgraph, ctx->s));
+  for (int i = 0; i < count; ++i) A[i]->factored = true;
   return HODLR_OK;
 }
 
@@ -1297,6 +1539,53 @@ int hodlr_solve(hodlr_ctx* ctx, const hodlr_mat* Ac, int nrhs, double* B, int ld
   return h ? HODLR_ESINGULAR : HODLR_OK;
 }
 
+int hodlr_solve_async(hodlr_ctx* ctx, hodlr_mat* A, int nrhs, double* B, int ldb) {
+  if (!ctx || !A || !B || nrhs <= 0 || nrhs > 1024 || ldb < A->n) return HODLR_EINVAL;
+  if (!A->factored) return HODLR_ESTATE;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  const int n = A->n;
+  if (!A->splan.dblob || A->splan_nrhs < nrhs) {
+    free_plan(A->splan);
+    if (A->sbuf) cudaFree(A->sbuf);
+    A->sbuf = nullptr;
+    int cap = std::max(nrhs, std::max(1, A->splan_nrhs));
+    if (cudaMalloc(&A->sbuf, sizeof(double) * (size_t)n * cap) != cudaSuccess) {
+      cudaGetLastError();
+      return HODLR_ENOMEM;
+    }
+    int rc = build_plan(A, A->splan, ctx->cluster, 0.0, [&](Planner& pl) {
+      plan_apply(pl, A, cap, A->sbuf, n, true);
+      plan_upper_solve(pl, A, 0, A->sbuf, n, cap);
+    }, true);
+    if (rc) return rc;
+    A->splan_nrhs = cap;
+  }
+  // stage B (unused columns are zero: they solve to zero), solve in place, copy back
+  HQ_CUDA_OK(cudaMemsetAsync(A->sbuf, 0, sizeof(double) * (size_t)n * A->splan_nrhs, ctx->s));
+  HQ_CUDA_OK(cudaMemcpy2DAsync(A->sbuf, sizeof(double) * n, B, sizeof(double) * ldb, sizeof(double) * n, nrhs,
+                               cudaMemcpyDeviceToDevice, ctx->s));
+  int rc = run_plan(ctx, A, A->splan);
+  if (rc) return rc;
+  HQ_CUDA_OK(cudaMemcpy2DAsync(B, sizeof(double) * ldb, A->sbuf, sizeof(double) * n, sizeof(double) * n, nrhs,
+                               cudaMemcpyDeviceToDevice, ctx->s));
+  return HODLR_OK;
+}
+
+int hodlr_ready(hodlr_ctx* ctx, int* ready) {
+  if (!ctx || !ready) return HODLR_EINVAL;
+  cudaError_t e = cudaStreamQuery(ctx->s);
+  if (e == cudaSuccess) {
+    *ready = 1;
+    return HODLR_OK;
+  }
+  if (e == cudaErrorNotReady) {
+    cudaGetLastError();
+    *ready = 0;
+    return HODLR_OK;
+  }
+  return cuda_fail(e, __FILE__, __LINE__);
+}
+
 int hodlr_norm2_estimate(hodlr_ctx* ctx, const hodlr_mat* Ac, int iters, double* out) {
   hodlr_mat* A = const_cast<hodlr_mat*>(Ac);
   if (!ctx || !A || !out || iters < 0) return HODLR_EINVAL;
@@ -1392,7 +1681,8 @@ int hodlr_truncate(hodlr_ctx* ctx, int nL, int nR, int K, const double* L, const
   cudaFree(M.dstatus);
   cudaFree(M.dscal);
   if (M.arena) cudaFree(M.arena);
-  M.devints = nullptr; M.dstatus = nullptr; M.dscal = nullptr; M.arena = nullptr;
+  if (M.arena2) cudaFree(M.arena2);
+  M.devints = nullptr; M.dstatus = nullptr; M.dscal = nullptr; M.arena = nullptr; M.arena2 = nullptr;
   return rc;
 }
 

@@ -64,11 +64,30 @@ def factors_dense(M):
     return Y, T, R
 
 
-def errors_torch(Y, T, R, A):
-    """e_orth = ||Q^T Q - I||_2, e_acc = ||Q R - A||_2 (Sec. 5), dense on the GPU."""
+def norm2(E, iters=60):
+    """||E||_2 by power iteration on E^T E from a fixed start (dense, on E's device).  A lower
+    bound that converges to ||E||_2; the Frobenius norm gives the upper bound when needed."""
+    x = torch.ones(E.shape[1], 1, dtype=E.dtype, device=E.device)
+    x /= torch.linalg.vector_norm(x)
+    s = 0.0
+    for _ in range(iters):
+        z = E.T @ (E @ x)
+        nz = torch.linalg.vector_norm(z).item()
+        if nz == 0.0:
+            return 0.0
+        x = z / nz
+        s = nz
+    return float(np.sqrt(s))
+
+
+def errors_torch(Y, T, R, A, upper=False):
+    """e_orth = ||Q^T Q - I||_2, e_acc = ||Q R - A||_2 (Sec. 5), dense on the GPU; with
+    upper=True the Frobenius norms (upper bounds of the 2-norms) are returned."""
     n = Y.shape[0]
     I = torch.eye(n, dtype=torch.float64, device=Y.device)
-    Q = I - Y @ T @ Y.T
-    e_orth = torch.linalg.matrix_norm(Q.T @ Q - I, ord=2).item()
-    e_acc = torch.linalg.matrix_norm(Q @ R - A, ord=2).item()
-    return e_orth, e_acc
+    Q = I - Y @ (T @ Y.T)
+    E1 = Q.T @ Q - I
+    E2 = Q @ R - A
+    if upper:
+        return torch.linalg.matrix_norm(E1).item(), torch.linalg.matrix_norm(E2).item()
+    return norm2(E1), norm2(E2)

@@ -1,0 +1,57 @@
+"""Cross-matrix batching: matrices of different size, partition and rank factored together
+(hodlr_qr_batched, hodlr_qr_batched_graph) give bit-identical results to factoring each alone."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+from tests import gpu_util as U  # noqa: E402
+
+
+def _mixed_inputs():
+    specs = [(1024, 128, 5, 0.0, 0), (2048, 256, 12, 10.0, 1), (777, 64, 7, 0.0, 2), (4096, 256, 20, 10.0, 3),
+             (512, 128, 9, 10.0, 4)]
+    return [W.random_hodlr(n, nmin, k, seed=s, col_scale_decades=d) for n, nmin, k, d, s in specs]
+
+
+def _dense_all(M):
+    return [U.dense_of(M, w).cpu().numpy() for w in (1, 2, 3)]
+
+
+def test_batched_equals_alone_and_graph_replays():
+    from paper_1809_10585_gb300 import binding as B
+    tol = 1e-12
+    inps = _mixed_inputs()
+    alone = []
+    for inp in inps:
+        M = U.gpu_qr(inp, tol, anorm=0.0, rank_cap=256)
+        st, _ = M.status()
+        assert st == 0
+        alone.append(_dense_all(M))
+    mats = [B.Matrix(U.ctx(), inp, rank_cap=256) for inp in inps]
+    B.qr_batched(U.ctx(), mats, tol, 0.0)
+    U.ctx().sync()
+    for M, ref in zip(mats, alone):
+        assert M.status()[0] == 0
+        for a, b in zip(_dense_all(M), ref):
+            assert np.array_equal(a, b)
+    # the graph form: restore + factor all, replayed twice
+    mats2 = [B.Matrix(U.ctx(), inp, rank_cap=256) for inp in inps]
+    for M in mats2:
+        M.snapshot()
+    for _ in range(2):
+        B.qr_batched(U.ctx(), mats2, tol, 0.0, graph=True)
+        U.ctx().sync()
+        for M, ref in zip(mats2, alone):
+            for a, b in zip(_dense_all(M), ref):
+                assert np.array_equal(a, b)
+    # each factorization is accurate
+    for inp, (Yc, Rc, Tc) in zip(inps, alone):
+        Y, R, T = Yc.T, Rc.T, Tc.T           # dense_of() returns column-major storage
+        A = W.to_dense(inp)
+        At = torch.from_numpy(A).cuda()
+        an = U.norm2(At)
+        eo, ea = U.errors_torch(*(torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (Y, T, R)), At, upper=True)
+        assert eo <= 100 * tol and ea / an <= 100 * tol

@@ -116,10 +116,11 @@ def _check_against_oracle(inp, tol, rank_cap=128):
     Y, T, R = U.factors_dense(M)
     A_t = torch.from_numpy(Ad).cuda()
     eo, ea = U.errors_torch(Y, T, R, A_t)
+    eoF, eaF = U.errors_torch(Y, T, R, A_t, upper=True)
     Yo, To, Ro = (torch.from_numpy(x).cuda() for x in (res.Y_dense(), res.T_dense(), res.R_dense()))
     eoo, eao = U.errors_torch(Yo, To, Ro, A_t)
     floor = 1e-14 * np.sqrt(inp.n)
-    assert eo <= 100 * tol + floor and ea / an <= 100 * tol + floor
+    assert eoF <= 100 * tol + floor and eaF / an <= 100 * tol + floor
     assert eo <= 10 * eoo + floor and ea <= 10 * eao + floor * an
     dR = np.abs(np.abs(np.diag(R.cpu().numpy())) - np.abs(np.diag(res.R_dense())))
     assert dR.max() <= 1e3 * tol * an + floor * an
