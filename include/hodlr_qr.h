@@ -204,6 +204,27 @@ int hodlr_truncate(hodlr_ctx* ctx, int nL, int nR, int K, const double* L_dev,
                    const double* Rt_dev, double thr, int kmax, double* Lout_dev,
                    double* Rout_dev, int* k_out);
 
+/*
+ * hodlr_dense_qr_noalloc — the same compact-WY Householder QR as hodlr_dense_qr, for callers
+ * that must not allocate device memory: cudaMalloc and cudaFree synchronize the whole device
+ * and can stall unrelated streams, and some callers (latency-critical loops, services that
+ * reserve all their memory at start-up, hosts that route every allocation through their own
+ * pool) forbid allocation after initialization.  The paper has no counterpart: this is a
+ * deployment variant of one kernel of the hot path.
+ *
+ * It calls no cudaMalloc, cudaFree or allocating library routine.  Its scratch (the launch
+ * descriptor, tau and the G = Y^T Y work area) lives in one static device array of about
+ * 0.5 MiB that every GPU loading this library holds until the process exits.  Limit:
+ * min(h, w) <= 256 (HODLR_EINVAL beyond it, with nothing written); other arguments as in
+ * hodlr_dense_qr.  The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All calls share the one
+ * array and it keeps the last call's contents (every entry is written before it is read, so
+ * nothing needs clearing); calls that overlap on the GPU, e.g. from two contexts or streams,
+ * race on it.  Synchronous.
+ */
+int hodlr_dense_qr_noalloc(hodlr_ctx* ctx, int h, int w, double* A_dev, int lda, double* T_dev,
+                           int ldt);
+
 #ifdef __cplusplus
 }
 #endif

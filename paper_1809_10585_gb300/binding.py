@@ -61,6 +61,7 @@ _SIGS = {
     "hodlr_download": (C.c_int, [_VP, _VP, _VP, C.c_size_t]),
     "hodlr_dense_qr": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.c_int, _VP, C.c_int]),
     "hodlr_truncate": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, _VP, _VP, C.c_double, C.c_int, _VP, _VP, _PI]),
+    "hodlr_dense_qr_noalloc": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.c_int, _VP, C.c_int]),
 }
 
 SYMBOLS = tuple(_SIGS)

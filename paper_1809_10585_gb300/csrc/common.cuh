@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct hodlr_ctx;
+
 namespace hq {
 
 constexpr int kMaxSweeps = 40;      // one-sided Jacobi sweep cap

@@ -498,3 +498,52 @@ cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, const int* 
 
 }  // namespace hq
 
+// ----------------------------------------------------------------- allocation-free dense QR
+// Scratch of hodlr_dense_qr_noalloc: the launch descriptor, tau (kNoAllocMaxK) and the
+// G = Y^T Y work area (kNoAllocMaxK^2), in one file-scope device array.  Every GPU that loads
+// the library holds it (about 0.5 MiB) until the process exits.
+namespace hq {
+constexpr int kNoAllocMaxK = 256;
+constexpr size_t kNoAllocDescDoubles = (sizeof(QRDesc) + 255) / 256 * 256 / sizeof(double);
+constexpr size_t kNoAllocDoubles = kNoAllocDescDoubles + kNoAllocMaxK + (size_t)kNoAllocMaxK * kNoAllocMaxK;
+constexpr int kNoAllocMaxDevices = 64;
+cudaStream_t ctx_stream(hodlr_ctx* ctx);
+int ctx_cluster(hodlr_ctx* ctx);
+}  // namespace hq
+
+static __device__ __align__(256) double g_noalloc_scratch[hq::kNoAllocDoubles];
+
+extern "C" int hodlr_dense_qr_noalloc(hodlr_ctx* ctx, int h, int w, double* A, int lda, double* T, int ldt) {
+  using namespace hq;
+  if (!ctx || !A || !T || h < 1 || w < 1 || lda < h) return 1;             // HODLR_EINVAL
+  const int k = h < w ? h : w;
+  if (k > kNoAllocMaxK || ldt < k) return 1;                                // beyond the scratch size
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+    cudaGetLastError();
+    return 6;                                                               // HODLR_ECUDA
+  }
+  // once per device, with that device current: the device address of the scratch array
+  static double* scratch_addr[kNoAllocMaxDevices] = {};
+  if (!scratch_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e, __FILE__, __LINE__);
+    scratch_addr[dev] = static_cast<double*>(p);
+  }
+  double* base = scratch_addr[dev];
+  QRDesc q = {};
+  q.A = A; q.lda = lda; q.h = h; q.w = w; q.href = -1; q.wref = -1;
+  q.tau = base + kNoAllocDescDoubles;
+  q.G = q.tau + kNoAllocMaxK;
+  q.ldg = k;
+  q.T = T; q.ldt = ldt; q.step = kStepNone; q.fmode = 0;
+  cudaStream_t s = ctx_stream(ctx);
+  QRDesc* dq = reinterpret_cast<QRDesc*>(base);
+  // every entry of tau and G is written by the kernel before it is read: nothing to clear
+  cudaError_t e = cudaMemcpyAsync(dq, &q, sizeof(QRDesc), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_qr(&q, 1, dq, nullptr, nullptr, ctx_cluster(ctx), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, __FILE__, __LINE__);
+  return 0;
+}

@@ -23,6 +23,8 @@
 using namespace hq;
 
 namespace hq {
+cudaStream_t ctx_stream(hodlr_ctx* ctx);
+int ctx_cluster(hodlr_ctx* ctx);
 cudaError_t launch_gemm_reduce(const GemmDesc* d, const int* rd, int nred, int nblocks,
                                const int* devints, cudaStream_t s);
 }
@@ -114,6 +116,9 @@ struct hodlr_mat {
   double g_tol = -1, g_anorm = -2;
   bool factored = false;
 };
+
+cudaStream_t hq::ctx_stream(hodlr_ctx* ctx) { return ctx->s; }
+int hq::ctx_cluster(hodlr_ctx* ctx) { return ctx->cluster; }
 
 // ----------------------------------------------------------------------------- planner
 struct Planner {
