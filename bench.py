@@ -1,6 +1,7 @@
 """Benchmark of the hQR hot path on GB300: HODLR-QR factorizations per second (FP64).
 
-Workload (one step = one full factorization, Alg. 2 with every step on the device):
+Workload (one step = `--batch` independent full factorizations, Alg. 2 with every step on the
+device, factored concurrently as one CUDA graph; `--batch 1` is the plain one-matrix path):
   n = 8192, nmin = 256 (5 levels), off-diagonal rank 10 with Gaussian factors N(0,1)/sqrt(n),
   leaves N(0,1) + 4 I, columns scaled by 10^(-14 j/(n-1)) (condition number ~1e14), tol = 1e-12,
   synthetic and seeded.  ||A||_2 is estimated on the device inside every step.
@@ -37,8 +38,9 @@ UNIT = "factorizations/s"
 WORKLOAD = "hodlr_qr_n8192_nmin256_k10_colscaled1e-14_tol1e-12"
 N, NMIN, K, DECADES, TOL = 8192, 256, 10, 14.0, 1e-12
 RANK_CAP = 128
+BATCH_CLUSTER = 8          # default cluster size when several matrices are factored per step
 # FP64 ALU peak from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
-# (the DFMA rate per SM was measured on this GPU)
+# (the DFMA rate of one SM, 2 per clock, was measured with an FMA throughput loop)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
@@ -173,6 +175,11 @@ def gpu_arm(args):
     ctx = B.Context(local)
     stream = torch.cuda.Stream()
     ctx.set_stream(stream.cuda_stream)
+    # cluster size of the QR/Jacobi kernels: the device maximum serves one matrix best; with
+    # several matrices in flight smaller clusters keep more of them resident at once
+    cmax = ctx.cluster
+    ccl = args.cluster if args.cluster > 0 else (cmax if nb == 1 else min(cmax, BATCH_CLUSTER))
+    ctx.cluster = ccl
     mats = [B.Matrix(ctx, x, rank_cap=RANK_CAP) for x in inps]
     M = mats[0]
     for m in mats:
@@ -219,6 +226,22 @@ def gpu_arm(args):
     barrier()
     ms_steps = [a.elapsed_time(b) for a, b in evs]
     ms_total = float(sum(ms_steps))
+    # the plain one-matrix-at-a-time path on the same GPU (first matrix of the batch)
+    single = None
+    if nb > 1:
+        sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        ctx.cluster = cmax
+        with torch.cuda.stream(stream):
+            M.qr_graph(TOL, 0.0)
+            for i in range(args.steps):
+                flush.fill_(float(i))
+                sev[i][0].record(stream)
+                M.qr_graph(TOL, 0.0)
+                sev[i][1].record(stream)
+        torch.cuda.synchronize()
+        sms = sum(a.elapsed_time(b) for a, b in sev) / args.steps
+        single = {"value": 1e3 / sms, "unit": UNIT, "ms_per_step": sms, "cluster": cmax}
+        ctx.cluster = ccl
     if ws > 1:
         import torch.distributed as dist
         t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
@@ -254,12 +277,12 @@ def gpu_arm(args):
     e2e_steps = max(1, min(args.steps, 10))
 
     def e2e_step():
+        # pinned host -> device upload, factorization (the same CUDA graph as the device arm; its
+        # restore copies the just-uploaded values), device -> host read of every factorization
         for m, p in zip(mats, pinps):
             m.upload(p)
-        if nb == 1:
-            M.qr(TOL, 0.0)
-        else:
-            B.qr_batched(ctx, mats, TOL, 0.0)
+            m.snapshot()
+        factor_all()
         for m, h in zip(mats, host_outs):
             m.download(h)
     with torch.cuda.stream(stream):
@@ -300,13 +323,14 @@ def gpu_arm(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N, "nmin": NMIN, "rank": K, "col_scale_decades": DECADES,
-                       "tol": TOL, "rank_cap": RANK_CAP, "batch": nb,
+                       "tol": TOL, "rank_cap": RANK_CAP, "batch": nb, "cluster": ccl,
                        "batching": "independent seeded matrices of the workload factored concurrently, one CUDA graph per step",
                        "l2": "flushed (256 MiB write) between timed steps",
                        "parallelism": f"replicas x{ws}", "anorm": anorm},
             "effective_gflops": nb * flops_total / (ms_per_step / 1e3) / 1e9,
             "algorithmic_gflop_per_step": flops_total / 1e9,
             "wall_s_timed": t_wall, "clocks": clk, "e2e": e2e, "roofline": roofline,
+            "single_matrix": single,
             "gpu_launches": gpu_launches}
 
     if rank == 0 and not args.no_cpu_baseline:
@@ -328,8 +352,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batch", type=int, default=1,
+    ap.add_argument("--batch", type=int, default=16,
                     help="matrices of the workload factored concurrently per step (cross-matrix batching)")
+    ap.add_argument("--cluster", type=int, default=0,
+                    help="CTAs per thread-block cluster of the QR/Jacobi kernels (0: automatic)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

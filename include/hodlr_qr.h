@@ -50,6 +50,16 @@ int hodlr_ctx_create(int device, hodlr_ctx** out);
 void hodlr_ctx_destroy(hodlr_ctx* ctx);
 /* Use `stream` (a cudaStream_t, or NULL for the context's own stream) for later work. */
 int hodlr_ctx_set_stream(hodlr_ctx* ctx, void* stream);
+/* Thread-block cluster size (number of CTAs, 1..16) of the Householder QR and Jacobi kernels
+ * launched from this context from now on.  The default is the largest size the device can
+ * co-schedule (16 on GB300).  A single factorization is fastest with the default; several
+ * factorizations in flight at once (hodlr_qr_batched, concurrent contexts) reach more throughput
+ * with smaller clusters, since more of them are resident on the SMs at the same time.  Results
+ * depend on the size at the level of rounding only: partial sums are split over the cluster's
+ * CTAs.  Graphs captured earlier are re-captured on their next call.  HODLR_EINVAL for a size
+ * below 1 or above the device's maximum. */
+int hodlr_ctx_set_cluster(hodlr_ctx* ctx, int cluster);
+int hodlr_ctx_get_cluster(hodlr_ctx* ctx, int* cluster);
 /* Block until all queued work on the context's stream is done. */
 int hodlr_sync(hodlr_ctx* ctx);
 

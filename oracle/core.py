@@ -12,7 +12,7 @@ Sec. 2.1.1; the economy QR of the left-orthogonalization, Sec. 2.1), and the den
 triangular solve of ``scipy.linalg`` at the leaves of the back-substitution.  The Householder
 reflector and the recursive block QR (Alg. 1) and hQR itself (Alg. 2) are written out here.
 
-Readings of places where the paper is silent or ambiguous (each is listed in the design doc):
+Readings of places where the paper is silent or ambiguous:
 
 * Householder reflector (Alg. 1, n = 1): LAPACK dlarfg convention,
   beta = -sign(alpha) * ||x|| where sign takes the sign bit of alpha (so -0.0 counts as
@@ -27,9 +27,9 @@ Readings of places where the paper is silent or ambiguous (each is listed in DES
   sigma_{k+1} <= threshold (Sec. 2.1.1), i.e. the number of sigma > threshold.
 * ||A||_2: ``POWER_ITERS`` power iterations on A^T A from the normalized all-ones vector,
   returning ||A x|| for the final unit vector x.
-* S~ and T~12 are truncated once after concatenating all terms (the line of Alg. 2 as
-  written), not in (l+1)k separate additions.
-* Left-orthogonalization (Alg. 2, "if B_L is not orthonormal") is always performed; on an
+* S~ and T~12 are truncated once after concatenating all terms (as Alg. 2 writes these two
+  steps), not in (l+1)k separate additions.
+* Left-orthogonalization (Alg. 2, conditional on B_L lacking orthonormal columns) is always performed; on an
   already orthonormal B_L it only changes column signs up to rounding.
 * The HODLR low-rank update  A -_H U V^T  (Table 1) subtracts U_i V_i^T from every dense
   leaf and replaces every off-diagonal block L R^T by T_eps([L, -U_rows][R, V_cols]^T).
@@ -312,7 +312,7 @@ def hqr_node(At: HNode, BL, BR, C, epsA, epsT):
     m = At.m
     C = np.zeros((0, m)) if C is None else np.asarray(C, dtype=np.float64)
     if BL is not None:
-        BL, BR = left_orthogonalize(BL, np.asarray(BR, dtype=np.float64).T)   # Alg. 2 lines 2-3
+        BL, BR = left_orthogonalize(BL, np.asarray(BR, dtype=np.float64).T)   # Alg. 2, first step
         BR = BR.T
     else:
         BR = np.zeros((0, m))

@@ -35,6 +35,8 @@ _SIGS = {
     "hodlr_ctx_create": (C.c_int, [C.c_int, C.POINTER(_VP)]),
     "hodlr_ctx_destroy": (None, [_VP]),
     "hodlr_ctx_set_stream": (C.c_int, [_VP, _VP]),
+    "hodlr_ctx_set_cluster": (C.c_int, [_VP, C.c_int]),
+    "hodlr_ctx_get_cluster": (C.c_int, [_VP, _PI]),
     "hodlr_sync": (C.c_int, [_VP]),
     "hodlr_build": (C.c_int, [_VP, C.c_int, C.c_int, _PI, _PPD, _PPD, _PPD, _PI, _PPD, _PPD, _PI, C.c_int, C.POINTER(_VP)]),
     "hodlr_free": (None, [_VP]),
@@ -114,6 +116,16 @@ class Context:
 
     def set_stream(self, stream_handle: int | None):
         check(lib().hodlr_ctx_set_stream(self.h, _VP(stream_handle or 0)), "hodlr_ctx_set_stream")
+
+    @property
+    def cluster(self) -> int:
+        v = C.c_int()
+        check(lib().hodlr_ctx_get_cluster(self.h, C.byref(v)), "hodlr_ctx_get_cluster")
+        return v.value
+
+    @cluster.setter
+    def cluster(self, size: int):
+        check(lib().hodlr_ctx_set_cluster(self.h, int(size)), "hodlr_ctx_set_cluster")
 
     def sync(self):
         check(lib().hodlr_sync(self.h), "hodlr_sync")

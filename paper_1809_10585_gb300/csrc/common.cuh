@@ -47,6 +47,7 @@ struct GemmDesc {
   const double* alpha_ref;  // if set, alpha *= *alpha_ref
   int ksplit;               // >= 1
   double* part;             // ksplit * m * n partials when ksplit > 1
+  int* tile_count;          // per-tile arrival counters when ksplit > 1 (zero between uses)
   int work0;                // first work item of this descriptor in the launch
   int tiles_m, tiles_n;     // grid of tiles (capacity)
   int step, fmode;

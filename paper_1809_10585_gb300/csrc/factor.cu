@@ -56,6 +56,96 @@ __device__ double block_sum(double v, double* red) {
   return red[QW];
 }
 
+// T of the compact WY form from the Householder vectors stored below the diagonal of A
+// (unit diagonal implied): G = Y^T Y (strictly upper part), 16 x 16 diagonal blocks by the
+// column recurrence T(0:i,i) = -tau_i T(0:i,0:i) G(0:i,i), then T12 = -T1 G12 T2 (Sec. 3, Eq. (10))
+// for blocks of doubling size.  A and tau must be final and visible to every CTA of the cluster.
+__device__ void qr_build_T(const QRDesc& d, const double* A, const size_t lda, const int h, const int kmax,
+                           const int C, const int crank, cg::cluster_group& cl) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (d.T == nullptr || kmax == 0) return;
+
+  // ---- T from G = Y^T Y (strictly upper part), Y unit lower trapezoidal
+  double* G = d.G;
+  const size_t ldg = d.ldg;
+  double* T = d.T;
+  const size_t ldt = d.ldt;
+  cl.sync();   // all columns final
+  {
+    const int gw = crank * QW + warp, nw = C * QW;
+    const long npairs = (long)kmax * (kmax - 1) / 2;
+    for (long p = gw; p < npairs; p += nw) {
+      // decode p -> (i, jj) with i < jj, jj-major
+      int jj = (int)((1.0 + sqrt(1.0 + 8.0 * (double)p)) * 0.5);
+      while ((long)jj * (jj - 1) / 2 > p) --jj;
+      while ((long)(jj + 1) * jj / 2 <= p) ++jj;
+      int i = (int)(p - (long)jj * (jj - 1) / 2);
+      const double* yi = A + i * lda;
+      const double* yj = A + jj * lda;
+      double t = 0.0;
+      for (int r = jj + 1 + lane; r < h; r += 32) t = fma(__ldcg(&yi[r]), __ldcg(&yj[r]), t);
+      t = warp_sum2(t);
+      if (lane == 0) G[i + jj * ldg] = t + __ldcg(&yi[jj]);
+    }
+    // zero T's strictly lower part, then diagonal blocks by the column recurrence
+    for (long e = (long)crank * QT + threadIdx.x; e < (long)kmax * kmax; e += (long)C * QT) {
+      int i = (int)(e % kmax), jj = (int)(e / kmax);
+      if (i > jj) T[i + jj * ldt] = 0.0;
+    }
+  }
+  cl.sync();
+  {
+    const int gw = crank * QW + warp, nw = C * QW;
+    const int nblk = (kmax + TNB - 1) / TNB;
+    for (int b = gw; b < nblk; b += nw) {
+      const int b0 = b * TNB, b1 = min(kmax, b0 + TNB);
+      for (int jj = b0; jj < b1; ++jj) {
+        const double tj = __ldcg(&d.tau[jj]);
+        // lane l computes T[b0 + l, jj] for b0 + l < jj
+        int i = b0 + lane;
+        double v = 0.0;
+        if (i < jj && lane < TNB) {
+          double s = 0.0;
+          for (int l = i; l < jj; ++l) s = fma(T[i + l * ldt], __ldcg(&G[l + jj * ldg]), s);
+          v = -tj * s;
+        }
+        __syncwarp();
+        if (i < jj && lane < TNB) T[i + jj * ldt] = v;
+        if (lane == 0) T[jj + jj * ldt] = tj;
+        __syncwarp();
+      }
+    }
+  }
+  // ---- merges: T12 = -T1 G12 T2 for adjacent blocks of size s
+  for (int s = TNB; s < kmax; s *= 2) {
+    cl.sync();
+    const long tid = (long)crank * QT + threadIdx.x, nt = (long)C * QT;
+    const int npair = (kmax + 2 * s - 1) / (2 * s);
+    // X = T1 G12 stored transposed in G's strictly lower part: G[b + jj, a + i]
+    for (long e = tid; e < (long)npair * s * s; e += nt) {
+      int q = (int)(e / ((long)s * s));
+      int rem = (int)(e % ((long)s * s));
+      int i = rem % s, jj = rem / s;
+      int a = 2 * q * s, b = a + s;
+      if (b + jj >= kmax) continue;
+      double acc = 0.0;
+      for (int l = i; l < s; ++l) acc = fma(__ldcg(&T[(a + i) + (size_t)(a + l) * ldt]), __ldcg(&G[(a + l) + (size_t)(b + jj) * ldg]), acc);
+      G[(b + jj) + (size_t)(a + i) * ldg] = acc;
+    }
+    cl.sync();
+    for (long e = tid; e < (long)npair * s * s; e += nt) {
+      int q = (int)(e / ((long)s * s));
+      int rem = (int)(e % ((long)s * s));
+      int i = rem % s, jj = rem / s;
+      int a = 2 * q * s, b = a + s;
+      if (b + jj >= kmax) continue;
+      double acc = 0.0;
+      for (int l = 0; l <= jj; ++l) acc = fma(__ldcg(&G[(b + l) + (size_t)(a + i) * ldg]), __ldcg(&T[(b + l) + (size_t)(b + jj) * ldt]), acc);
+      T[(a + i) + (size_t)(b + jj) * ldt] = -acc;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(QT) qr_cluster_kernel(const QRDesc* __restrict__ descs,
                                                         const int* __restrict__ di, double* flops) {
   cg::cluster_group cl = cg::this_cluster();
@@ -147,22 +237,27 @@ __global__ void __launch_bounds__(QT) qr_cluster_kernel(const QRDesc* __restrict
         if (in_regs) {
           double r[kQRRegs];
           double t = 0.0;
+          const int nq = (h - j - 1 + 31) >> 5;   // warp-uniform live register slots
 #pragma unroll
           for (int q = 0; q < kQRRegs; ++q) {
-            const int i = j + 1 + lane + 32 * q;
-            r[q] = i < h ? __ldcg(&a[i]) : 0.0;
-            if (i < h) t = fma(staged ? ysm[i] : __ldcg(&y[i]), r[q], t);
+            if (q < nq) {
+              const int i = j + 1 + lane + 32 * q;
+              r[q] = i < h ? __ldcg(&a[i]) : 0.0;
+              if (i < h) t = fma(staged ? ysm[i] : __ldcg(&y[i]), r[q], t);
+            }
           }
           t = warp_sum2(t);
           const double wv = tau * fma(scal, t, __ldcg(&a[j]));
           const double ws = wv * scal;
 #pragma unroll
           for (int q = 0; q < kQRRegs; ++q) {
-            const int i = j + 1 + lane + 32 * q;
-            if (i < h) {
-              const double v = fma(-ws, staged ? ysm[i] : __ldcg(&y[i]), r[q]);
-              a[i] = v;
-              if (i > j + 1) nn = fma(v, v, nn);
+            if (q < nq) {
+              const int i = j + 1 + lane + 32 * q;
+              if (i < h) {
+                const double v = fma(-ws, staged ? ysm[i] : __ldcg(&y[i]), r[q]);
+                a[i] = v;
+                if (i > j + 1) nn = fma(v, v, nn);
+              }
             }
           }
           if (lane == 0) a[j] = __ldcg(&a[j]) - wv;
@@ -199,91 +294,176 @@ __global__ void __launch_bounds__(QT) qr_cluster_kernel(const QRDesc* __restrict
     if (sp != 0.0)
       for (int i = kmax + threadIdx.x; i < h; i += QT) A[i + (kmax - 1) * lda] = __ldcg(&A[i + (kmax - 1) * lda]) * sp;
   }
-  if (d.T == nullptr || kmax == 0) return;
-
-  // ---- T from G = Y^T Y (strictly upper part), Y unit lower trapezoidal
-  double* G = d.G;
-  const size_t ldg = d.ldg;
-  double* T = d.T;
-  const size_t ldt = d.ldt;
-  cl.sync();   // all columns final
-  {
-    const int gw = crank * QW + warp, nw = C * QW;
-    const long npairs = (long)kmax * (kmax - 1) / 2;
-    for (long p = gw; p < npairs; p += nw) {
-      // decode p -> (i, jj) with i < jj, jj-major
-      int jj = (int)((1.0 + sqrt(1.0 + 8.0 * (double)p)) * 0.5);
-      while ((long)jj * (jj - 1) / 2 > p) --jj;
-      while ((long)(jj + 1) * jj / 2 <= p) ++jj;
-      int i = (int)(p - (long)jj * (jj - 1) / 2);
-      const double* yi = A + i * lda;
-      const double* yj = A + jj * lda;
-      double t = 0.0;
-      for (int r = jj + 1 + lane; r < h; r += 32) t = fma(__ldcg(&yi[r]), __ldcg(&yj[r]), t);
-      t = warp_sum2(t);
-      if (lane == 0) G[i + jj * ldg] = t + __ldcg(&yi[jj]);
-    }
-    // zero T's strictly lower part, then diagonal blocks by the column recurrence
-    for (long e = (long)crank * QT + threadIdx.x; e < (long)kmax * kmax; e += (long)C * QT) {
-      int i = (int)(e % kmax), jj = (int)(e / kmax);
-      if (i > jj) T[i + jj * ldt] = 0.0;
-    }
-  }
-  cl.sync();
-  {
-    const int gw = crank * QW + warp, nw = C * QW;
-    const int nblk = (kmax + TNB - 1) / TNB;
-    for (int b = gw; b < nblk; b += nw) {
-      const int b0 = b * TNB, b1 = min(kmax, b0 + TNB);
-      for (int jj = b0; jj < b1; ++jj) {
-        const double tj = __ldcg(&d.tau[jj]);
-        // lane l computes T[b0 + l, jj] for b0 + l < jj
-        int i = b0 + lane;
-        double v = 0.0;
-        if (i < jj && lane < TNB) {
-          double s = 0.0;
-          for (int l = i; l < jj; ++l) s = fma(T[i + l * ldt], __ldcg(&G[l + jj * ldg]), s);
-          v = -tj * s;
-        }
-        __syncwarp();
-        if (i < jj && lane < TNB) T[i + jj * ldt] = v;
-        if (lane == 0) T[jj + jj * ldt] = tj;
-        __syncwarp();
-      }
-    }
-  }
-  // ---- merges: T12 = -T1 G12 T2 for adjacent blocks of size s
-  for (int s = TNB; s < kmax; s *= 2) {
-    cl.sync();
-    const long tid = (long)crank * QT + threadIdx.x, nt = (long)C * QT;
-    const int npair = (kmax + 2 * s - 1) / (2 * s);
-    // X = T1 G12 stored transposed in G's strictly lower part: G[b + jj, a + i]
-    for (long e = tid; e < (long)npair * s * s; e += nt) {
-      int q = (int)(e / ((long)s * s));
-      int rem = (int)(e % ((long)s * s));
-      int i = rem % s, jj = rem / s;
-      int a = 2 * q * s, b = a + s;
-      if (b + jj >= kmax) continue;
-      double acc = 0.0;
-      for (int l = i; l < s; ++l) acc = fma(__ldcg(&T[(a + i) + (size_t)(a + l) * ldt]), __ldcg(&G[(a + l) + (size_t)(b + jj) * ldg]), acc);
-      G[(b + jj) + (size_t)(a + i) * ldg] = acc;
-    }
-    cl.sync();
-    for (long e = tid; e < (long)npair * s * s; e += nt) {
-      int q = (int)(e / ((long)s * s));
-      int rem = (int)(e % ((long)s * s));
-      int i = rem % s, jj = rem / s;
-      int a = 2 * q * s, b = a + s;
-      if (b + jj >= kmax) continue;
-      double acc = 0.0;
-      for (int l = 0; l <= jj; ++l) acc = fma(__ldcg(&G[(b + l) + (size_t)(a + i) * ldg]), __ldcg(&T[(b + l) + (size_t)(b + jj) * ldt]), acc);
-      T[(a + i) + (size_t)(b + jj) * ldt] = -acc;
-    }
-  }
+  qr_build_T(d, A, lda, h, kmax, C, crank, cl);
 }
 
 __global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __restrict__ descs,
                                                             const int* __restrict__ di, double* flops);
+
+__global__ void __launch_bounds__(QT) jacobi_dsmem_kernel(const JacobiDesc* __restrict__ descs,
+                                                          const int* __restrict__ di, double* flops,
+                                                          int q1cap, int q2cap);
+constexpr size_t kJacobiSmemMax = 200 * 1024;
+
+
+// Householder QR with the matrix held in distributed shared memory: column c lives in the
+// shared memory of CTA c % C (slot c / C).  The owner of column j forms and scales its
+// reflector in place, one cluster barrier publishes it, and every CTA copies it once through
+// DSMEM into a local buffer before updating its own columns (one warp per column, the warp
+// that updates the next pivot also returns that column's norm).  The factored columns are
+// written back to global memory and T is built as in qr_cluster_kernel.
+__global__ void __launch_bounds__(QT) qr_dsmem_kernel(const QRDesc* __restrict__ descs,
+                                                      const int* __restrict__ di, double* flops,
+                                                      int hcap, int wcap) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int crank = (int)cl.block_rank();
+  const QRDesc& d = descs[blockIdx.y];
+  const int h = min(dimv(d.h, d.href, di), hcap), w = min(dimv(d.w, d.wref, di), wcap);
+  const int kmax = min(h, w);
+  double* A = d.A;
+  const size_t lda = d.lda;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  extern __shared__ double qsm[];
+  const int nloc = (wcap + C - 1) / C;
+  double* cols = qsm;                                   // nloc x hcap
+  double* ybuf = cols + (size_t)nloc * hcap;            // hcap
+  __shared__ double red[QW + 1];
+  __shared__ double sh_tau, xn_next;
+
+  if (crank == 0 && threadIdx.x == 0 && flops && kmax > 0) {
+    if (d.step >= 0) {
+      double f;
+      if (d.fmode == 0) {
+        f = 2.0 * h * (double)w * w - 2.0 * (double)w * w * w / 3.0 + (double)h * w * w - (double)w * w * w / 3.0;
+      } else {
+        double q = kmax;
+        f = 4.0 * h * (double)w * q - 4.0 * q * q * q / 3.0;
+      }
+      atomicAdd(&flops[d.step], f);
+    }
+    const double q = kmax;
+    double g = 2.0 * h * (double)w * q - q * q * (double)w - q * q * q / 3.0 + (double)w * q * q / 3.0;
+    if (g < 0) g = 0;
+    if (d.T) g += (double)h * q * q - q * q * q / 3.0;
+    atomicAdd(&flops[kKindSlot + 2], g);
+  }
+  for (int sl = 0; sl < nloc; ++sl) {
+    const int c = crank + sl * C;
+    if (c >= w) break;
+    for (int i = threadIdx.x; i < h; i += QT) cols[(size_t)sl * hcap + i] = A[i + (size_t)c * lda];
+  }
+  cl.sync();                                             // all CTAs running before any DSMEM access
+  if (crank == 0 && kmax > 0) {
+    double s = 0.0;
+    for (int i = 1 + threadIdx.x; i < h; i += QT) s = fma(cols[i], cols[i], s);
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) xn_next = s;
+  }
+  __syncthreads();
+  const bool in_regs = h <= 32 * kQRRegs;
+  for (int j = 0; j < kmax; ++j) {
+    const int owner = j % C;
+    if (owner == crank) {
+      double* cj = cols + (size_t)(j / C) * hcap;
+      if (threadIdx.x == 0) {
+        const double s = xn_next;
+        const double alpha = cj[j];
+        double tau = 0.0, scal = 0.0;
+        if (s > 0.0) {
+          const double hn = hypot(alpha, sqrt(s));
+          const double beta = -copysign(hn, alpha);
+          tau = (beta - alpha) / beta;
+          scal = 1.0 / (alpha - beta);
+          cj[j] = beta;
+        }
+        sh_tau = tau;
+        red[QW] = scal;
+        d.tau[j] = tau;
+      }
+      __syncthreads();
+      const double scal = red[QW];
+      if (scal != 0.0)
+        for (int i = j + 1 + threadIdx.x; i < h; i += QT) cj[i] *= scal;
+    }
+    cl.sync();
+    const double tau = *cl.map_shared_rank(&sh_tau, owner);
+    if (tau != 0.0) {
+      const double* yj = cl.map_shared_rank(cols, owner) + (size_t)(j / C) * hcap;
+      for (int i = j + 1 + threadIdx.x; i < h; i += QT) ybuf[i] = yj[i];
+      __syncthreads();
+    }
+    const int first = j + 1;
+    const int c0 = first + ((crank - first % C) + C) % C;
+    for (int c = c0 + warp * C; c < w; c += QW * C) {
+      double* a = cols + (size_t)(c / C) * hcap;
+      double nn = 0.0;
+      if (tau != 0.0) {
+        if (in_regs) {
+          double r[kQRRegs];
+          double t = 0.0;
+          const int nq = (h - j - 1 + 31) >> 5;   // warp-uniform live register slots
+#pragma unroll
+          for (int q = 0; q < kQRRegs; ++q) {
+            if (q < nq) {
+              const int i = j + 1 + lane + 32 * q;
+              r[q] = i < h ? a[i] : 0.0;
+              if (i < h) t = fma(ybuf[i], r[q], t);
+            }
+          }
+          t = warp_sum2(t);
+          const double wv = tau * (t + a[j]);
+#pragma unroll
+          for (int q = 0; q < kQRRegs; ++q) {
+            if (q < nq) {
+              const int i = j + 1 + lane + 32 * q;
+              if (i < h) {
+                const double v = fma(-wv, ybuf[i], r[q]);
+                a[i] = v;
+                if (i > j + 1) nn = fma(v, v, nn);
+              }
+            }
+          }
+          __syncwarp();
+          if (lane == 0) a[j] -= wv;
+        } else {
+          double t = 0.0;
+          for (int i = j + 1 + lane; i < h; i += 32) t = fma(ybuf[i], a[i], t);
+          t = warp_sum2(t);
+          const double wv = tau * (t + a[j]);
+          for (int i = j + 1 + lane; i < h; i += 32) {
+            const double v = fma(-wv, ybuf[i], a[i]);
+            a[i] = v;
+            if (i > j + 1) nn = fma(v, v, nn);
+          }
+          __syncwarp();
+          if (lane == 0) a[j] -= wv;
+        }
+      } else if (c == j + 1) {
+        for (int i = j + 2 + lane; i < h; i += 32) nn = fma(a[i], a[i], nn);
+      }
+      if (c == j + 1) {
+        nn = warp_sum2(nn);
+        if (lane == 0) xn_next = nn;
+      }
+    }
+    __syncthreads();
+    // the next owner may overwrite sh_tau / its pivot only after every CTA read this reflector
+    cl.sync();
+  }
+  for (int sl = 0; sl < nloc; ++sl) {
+    const int c = crank + sl * C;
+    if (c >= w) break;
+    for (int i = threadIdx.x; i < h; i += QT) A[i + (size_t)c * lda] = cols[(size_t)sl * hcap + i];
+  }
+  qr_build_T(d, A, lda, h, kmax, C, crank, cl);   // starts with a cluster barrier
+}
+
+size_t qr_dsmem_bytes(int hcap, int wcap, int cluster) {
+  const size_t nloc = (wcap + cluster - 1) / cluster;
+  return (nloc + 1) * (size_t)hcap * sizeof(double) + 64;
+}
+constexpr size_t kQRSmemMax = 200 * 1024;
 
 // Largest cluster size both cluster kernels can be launched with (16 needs the non-portable
 // attribute and enough SMs per GPC), probed once per process; attributes are set here, never
@@ -312,6 +492,11 @@ int qr_max_cluster() {
     }
   }
   cudaGetLastError();
+  cudaFuncSetAttribute(jacobi_dsmem_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(jacobi_dsmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kJacobiSmemMax);
+  cudaFuncSetAttribute(qr_dsmem_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(qr_dsmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQRSmemMax);
+  cudaGetLastError();
   cached = v;
   return v;
 }
@@ -331,18 +516,31 @@ cudaError_t launch_qr(const QRDesc* h, int n, QRDesc* d, const int* devints, dou
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  int hcap = 1, wcap = 1;
+  for (int i = 0; i < n; ++i) {
+    hcap = max(hcap, h[i].h);
+    wcap = max(wcap, h[i].w);
+  }
+  const size_t smem = qr_dsmem_bytes(hcap, wcap, cluster);
+  if (smem <= kQRSmemMax) {
+    cfg.dynamicSmemBytes = smem;
+    return cudaLaunchKernelEx(&cfg, qr_dsmem_kernel, (const QRDesc*)d, devints, flops, hcap, wcap);
+  }
   return cudaLaunchKernelEx(&cfg, qr_cluster_kernel, (const QRDesc*)d, devints, flops);
 }
 
 // --------------------------------------------------------------------------------- Jacobi
 __device__ inline void rr_pair(int r, int i, int P, int& a, int& b) {
-  // round-robin (circle) schedule on P (even) players, round r in [0, P-1)
+  // round-robin (circle) schedule on P (even) players, round r in [0, P-1); r, i < P - 1
   if (i == 0) {
     a = P - 1;
     b = r;
   } else {
-    a = (r + i) % (P - 1);
-    b = (r - i + (P - 1)) % (P - 1);
+    const int m = P - 1;
+    a = r + i;
+    if (a >= m) a -= m;
+    b = r - i;
+    if (b < 0) b += m;
   }
 }
 
@@ -479,9 +677,212 @@ __global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __
   }
 }
 
+// One-sided Jacobi with the core held in distributed shared memory: column j lives in the
+// shared memory of CTA j % C.  A pair (a, b), a < b, is rotated by one warp of the CTA that
+// holds a; it reads and writes column b through DSMEM.  alpha, beta and gamma are formed from
+// the loaded columns in one pass, so a round costs one remote load, one remote store and one
+// cluster barrier.  Same pair schedule, thresholds and deflation as jacobi_cluster_kernel.
+__global__ void __launch_bounds__(QT) jacobi_dsmem_kernel(const JacobiDesc* __restrict__ descs,
+                                                          const int* __restrict__ di, double* flops,
+                                                          int q1cap, int q2cap) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int crank = (int)cl.block_rank();
+  const JacobiDesc& d = descs[blockIdx.y];
+  const int q1 = min(dimv(d.q1, d.q1ref, di), q1cap), q2 = min(dimv(d.q2, d.q2ref, di), q2cap);
+  if (crank == 0 && threadIdx.x == 0 && flops && q1 > 0 && q2 > 0) {
+    double p = max(q1, q2), q = min(q1, q2);
+    atomicAdd(&flops[kKindSlot + 3], 4.0 * p * p * q + 8.0 * p * q * q + 9.0 * q * q * q);
+  }
+  extern __shared__ double jsm[];
+  const int nloc = (q2cap + C - 1) / C;
+  const int ldc = q1cap;
+  double* cols = jsm;                                    // nloc x ldc, slot s = column crank + s*C
+  double* cn = cols + (size_t)nloc * ldc;                // current squared norms of own columns
+  double* nall = cn + nloc;                              // squared norms of all columns (sweep start)
+  int* act = reinterpret_cast<int*>(nall + q2cap);       // active columns of the sweep
+  __shared__ int nact;
+  double* M = d.M;
+  const size_t ldm = d.ldm;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double tol = fmin(1e-13, fmax(1e-15, 4.4e-16 * (double)q1));
+  double thr = d.thr;
+  if (d.thr_ref) thr *= *d.thr_ref;
+  const double dth = 1e-2 * thr / sqrt((double)max(q2, 1));
+  const double dfl = dth * dth;
+
+  if (crank == 0)
+    for (int i = threadIdx.x; i < kMaxSweeps; i += QT) d.rot[i] = 0;
+  for (int sl = 0; sl < nloc; ++sl) {
+    const int j = crank + sl * C;
+    if (j >= q2) break;
+    for (int i = threadIdx.x; i < q1; i += QT) cols[(size_t)sl * ldc + i] = M[i + (size_t)j * ldm];
+  }
+  // every CTA of the cluster must be running before any distributed shared memory access
+  cl.sync();
+
+  const int gw = crank * QW + warp, nw = C * QW;
+  for (int sweep = 0; sweep <= kMaxSweeps; ++sweep) {
+    // exact squared norms of own columns, broadcast into every CTA's copy
+    for (int sl = warp; sl < nloc; sl += QW) {
+      const int j = crank + sl * C;
+      if (j >= q2) break;
+      double v = 0.0;
+      for (int i = lane; i < q1; i += 32) {
+        const double x = cols[(size_t)sl * ldc + i];
+        v = fma(x, x, v);
+      }
+      v = warp_sum2(v);
+      if (lane < C) cl.map_shared_rank(nall, lane)[j] = v;
+      if (lane == 0) {
+        cn[sl] = v;
+        d.nrm[j] = v;
+      }
+    }
+    cl.sync();
+    if (sweep == kMaxSweeps || q2 < 2 || q1 == 0) break;
+    if (threadIdx.x == 0) {
+      int c = 0;
+      for (int j = 0; j < q2; ++j)
+        if (nall[j] > dfl) act[c++] = j;
+      nact = c;
+    }
+    __syncthreads();
+    const int Ka = nact;
+    if (Ka < 2) break;
+    const int P = Ka + (Ka & 1);
+    int local = 0;
+    for (int r = 0; r < P - 1; ++r) {
+      for (int pi = gw; pi < P / 2; pi += nw) {
+        int ia, ib;
+        rr_pair(r, pi, P, ia, ib);
+        if (ia >= Ka || ib >= Ka) continue;
+        const int a = act[ia], b = act[ib];
+        double* xa = cl.map_shared_rank(cols, a % C) + (size_t)(a / C) * ldc;
+        double* yb = cl.map_shared_rank(cols, b % C) + (size_t)(b / C) * ldc;
+        // alpha, beta: squared norms tracked through the sweep (exact at every sweep start);
+        // gamma is summed from the columns
+        double* na_p = cl.map_shared_rank(cn, a % C) + a / C;
+        double* nb_p = cl.map_shared_rank(cn, b % C) + b / C;
+        const double al = *na_p, be = *nb_p;
+        const bool inreg = q1 <= 32 * kJacobiRegs;
+        const int nreg = (q1 + 31) >> 5;   // warp-uniform: register slots beyond it are skipped
+        double x[kJacobiRegs], y[kJacobiRegs];
+        double g = 0.0;
+        if (inreg) {
+#pragma unroll
+          for (int t = 0; t < kJacobiRegs; ++t) {
+            if (t < nreg) {
+              const int i = lane + 32 * t;
+              x[t] = i < q1 ? xa[i] : 0.0;
+              y[t] = i < q1 ? yb[i] : 0.0;
+              g = fma(x[t], y[t], g);
+            }
+          }
+        } else {
+          for (int i = lane; i < q1; i += 32) g = fma(xa[i], yb[i], g);
+        }
+        g = warp_sum2(g);
+        // convergence test and rotation on one lane (FP64 divide and square root are scarce),
+        // broadcast to the warp.  The test keeps the scale-safe form |g| > tol sqrt(al) sqrt(be):
+        // squaring underflows once a column decays to denormal size.
+        double c = 0.0, sn = 0.0, tt = 0.0;
+        int doit = 0;
+        if (lane == 0 && al > dfl && be > dfl && fabs(g) > tol * sqrt(al) * sqrt(be)) {
+          doit = 1;
+          const double zeta = (be - al) / (2.0 * g);
+          if (fabs(zeta) > 1e100) tt = 0.5 / zeta;
+          else tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          c = rsqrt(1.0 + tt * tt);
+          sn = c * tt;
+        }
+        doit = __shfl_sync(0xffffffffu, doit, 0);
+        if (!doit) continue;
+        c = __shfl_sync(0xffffffffu, c, 0);
+        sn = __shfl_sync(0xffffffffu, sn, 0);
+        tt = __shfl_sync(0xffffffffu, tt, 0);
+        // alpha' = alpha - t gamma, beta' = beta + t gamma; the shrinking column's norm is summed
+        // exactly when it loses more than half of its mass (cancellation)
+        const double tg = tt * g;
+        const bool a_shrinks = tg > 0.0;
+        const bool exact = a_shrinks ? (tg > 0.5 * al) : (-tg > 0.5 * be);
+        double ss = 0.0;
+        if (inreg) {
+#pragma unroll
+          for (int t = 0; t < kJacobiRegs; ++t) {
+            if (t < nreg) {
+              const double xn = c * x[t] - sn * y[t];
+              const double yn = sn * x[t] + c * y[t];
+              x[t] = xn;
+              y[t] = yn;
+              const int i = lane + 32 * t;
+              if (i < q1) {
+                xa[i] = xn;
+                yb[i] = yn;
+              }
+            }
+          }
+          if (exact) {
+#pragma unroll
+            for (int t = 0; t < kJacobiRegs; ++t) {
+              if (t < nreg) {
+                const double v = a_shrinks ? x[t] : y[t];
+                ss = fma(v, v, ss);
+              }
+            }
+          }
+        } else {
+          for (int i = lane; i < q1; i += 32) {
+            const double xv = xa[i], yv = yb[i];
+            const double xn = c * xv - sn * yv;
+            const double yn = sn * xv + c * yv;
+            xa[i] = xn;
+            yb[i] = yn;
+            if (exact) {
+              const double v = a_shrinks ? xn : yn;
+              ss = fma(v, v, ss);
+            }
+          }
+        }
+        if (exact) ss = warp_sum2(ss);
+        if (lane == 0) {
+          const double na = fma(-tt, g, al), nb = fma(tt, g, be);
+          *na_p = (exact && a_shrinks) ? ss : na;
+          *nb_p = (exact && !a_shrinks) ? ss : nb;
+        }
+        ++local;
+      }
+      cl.sync();
+    }
+    if (lane == 0 && local) atomicAdd(&d.rot[sweep], local);
+    cl.sync();
+    if (*(volatile int*)&d.rot[sweep] == 0) sweep = kMaxSweeps - 1;   // converged: final norms next pass
+  }
+  // write the rotated columns back (the rank selection reads them from global memory)
+  for (int sl = 0; sl < nloc; ++sl) {
+    const int j = crank + sl * C;
+    if (j >= q2) break;
+    for (int i = threadIdx.x; i < q1; i += QT) M[i + (size_t)j * ldm] = cols[(size_t)sl * ldc + i];
+  }
+  cl.sync();   // no CTA may exit while others still access its shared memory
+}
+
+size_t jacobi_dsmem_bytes(int q1cap, int q2cap, int cluster) {
+  const size_t nloc = (q2cap + cluster - 1) / cluster;
+  return nloc * (q1cap + 1) * sizeof(double) + (size_t)q2cap * sizeof(double) + (size_t)q2cap * sizeof(int) + 64;
+}
+
 cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, const int* devints, double* flops,
                           int cluster, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  int q1cap = 0, q2cap = 0;
+  for (int i = 0; i < n; ++i) {
+    q1cap = max(q1cap, h[i].q1);
+    q2cap = max(q2cap, h[i].q2);
+  }
+  q1cap = max(q1cap, 1);
+  q2cap = max(q2cap, 1);
+  const size_t smem = jacobi_dsmem_bytes(q1cap, q2cap, cluster);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cluster, n, 1);
   cfg.blockDim = dim3(QT, 1, 1);
@@ -493,6 +894,10 @@ cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, const int* 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (smem <= kJacobiSmemMax && q2cap <= kJacobiMaxCols) {
+    cfg.dynamicSmemBytes = smem;
+    return cudaLaunchKernelEx(&cfg, jacobi_dsmem_kernel, (const JacobiDesc*)d, devints, flops, q1cap, q2cap);
+  }
   return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel, (const JacobiDesc*)d, devints, flops);
 }
 

@@ -42,6 +42,7 @@ struct hodlr_ctx {
   cudaGraphExec_t bgraph = nullptr;
   std::vector<hodlr_mat*> bmats;
   double btol = -1, banorm = -2;
+  int bcluster = 0;
 };
 
 enum RecType { R_GEMM, R_REDUCE, R_CONCAT, R_GATHER, R_SCATTER, R_QR, R_JACOBI, R_SELECT, R_COPY,
@@ -67,6 +68,8 @@ struct Plan {
   std::vector<char> blob;
   char* dblob = nullptr;
   size_t dblob_bytes = 0;
+  int* counters = nullptr;       // split-K tile counters of this plan (zero between uses)
+  size_t counters_n = 0;
   // host copies of descriptors needed for launch-time grid sizing live inside blob
 };
 
@@ -114,6 +117,7 @@ struct hodlr_mat {
   double plan_tol = -1, plan_anorm = -2;
   cudaGraphExec_t gexec = nullptr;
   double g_tol = -1, g_anorm = -2;
+  int g_cluster = 0;
   bool factored = false;
 };
 
@@ -132,6 +136,8 @@ struct Planner {
   bool fresh = false;            // route alloc() to the never-reused region
   int int_top;                   // devints bump pointer
   int int_high;
+  size_t cnt_top = 0;            // split-K tile counters (never reused, zero between uses)
+  int* cnt_base = nullptr;
   int cluster;
   double tol;
 
@@ -210,7 +216,12 @@ struct Planner {
         ks = std::min(ks, 64);
         if (ks >= 2) d.ksplit = ks;
       }
-      if (d.ksplit > 1) d.part = alloc<double>((size_t)d.ksplit * d.m * d.n);
+      d.tile_count = nullptr;
+      if (d.ksplit > 1) {
+        d.part = alloc<double>((size_t)d.ksplit * d.m * d.n);
+        d.tile_count = cnt_base + cnt_top;
+        cnt_top += tiles;
+      }
       d.work0 = work;
       work += tiles * d.ksplit;
       out.push_back(d);
@@ -218,13 +229,7 @@ struct Planner {
     if (out.empty()) return;
     size_t off = put(out);
     rec(R_GEMM, (int)out.size(), off);
-    for (size_t i = 0; i < out.size(); ++i) {
-      if (out[i].ksplit > 1) {
-        red.push_back((int)i);
-        red.push_back(redblocks);
-        redblocks += (out[i].m * out[i].n + 255) / 256;
-      }
-    }
+    (void)redblocks;
     if (!red.empty()) {
       size_t roff = put(red);
       Rec r = {};
@@ -838,6 +843,9 @@ static int upload_plan(Plan& P) {
   P.dblob_bytes = std::max<size_t>(P.blob.size(), 16);
   HQ_CUDA_OK(cudaMalloc(&P.dblob, P.dblob_bytes));
   if (!P.blob.empty()) HQ_CUDA_OK(cudaMemcpy(P.dblob, P.blob.data(), P.blob.size(), cudaMemcpyHostToDevice));
+  // a pageable upload may still be in flight when cudaMemcpy returns, and the context's streams
+  // do not wait for the legacy stream: finish it before any launch reads the descriptors
+  HQ_CUDA_OK(cudaStreamSynchronize(cudaStreamLegacy));
   return HODLR_OK;
 }
 
@@ -854,6 +862,7 @@ static int build_plan(hodlr_mat* M, Plan& P, int cluster, double tol, F&& body, 
     Planner pl;
     pl.M = M; pl.P = &P; pl.base = pass == 0 ? nullptr : *ar1;
     pl.base2 = pass == 0 ? nullptr : *ar2;
+    pl.cnt_base = pass == 0 ? nullptr : P.counters;
     P.nevents = 0;
     pl.int_top = 3 * M->nn; pl.int_high = pl.int_top;
     pl.cluster = cluster; pl.tol = tol;
@@ -871,6 +880,18 @@ static int build_plan(hodlr_mat* M, Plan& P, int cluster, double tol, F&& body, 
           return HODLR_ENOMEM;
         }
         *ar1b = need;
+      }
+      if (pl.cnt_top > P.counters_n) {
+        if (P.counters) cudaFree(P.counters);
+        P.counters = nullptr;
+        P.counters_n = 0;
+        if (cudaMalloc(&P.counters, sizeof(int) * pl.cnt_top) != cudaSuccess) {
+          cudaGetLastError();
+          return HODLR_ENOMEM;
+        }
+        P.counters_n = pl.cnt_top;
+        HQ_CUDA_OK(cudaMemset(P.counters, 0, sizeof(int) * pl.cnt_top));
+        HQ_CUDA_OK(cudaStreamSynchronize(cudaStreamLegacy));
       }
       size_t need2 = pl.top2 + 4096;
       if (need2 > *ar2b) {
@@ -894,6 +915,9 @@ static void free_plan(Plan& P) {
   P.nevents = 0;
   if (P.dblob) cudaFree(P.dblob);
   P.dblob = nullptr;
+  if (P.counters) cudaFree(P.counters);
+  P.counters = nullptr;
+  P.counters_n = 0;
   P.recs.clear();
   P.blob.clear();
 }
@@ -936,10 +960,7 @@ int hodlr_ctx_create(int device, hodlr_ctx** out) {
     delete c;
     return HODLR_ECUDA;
   }
-  int cl = qr_max_cluster();
-  const char* env = getenv("HODLR_CLUSTER");
-  if (env) cl = std::max(1, std::min(16, atoi(env)));
-  c->cluster = cl;
+  c->cluster = qr_max_cluster();
   *out = c;
   return HODLR_OK;
 }
@@ -968,6 +989,20 @@ void hodlr_ctx_destroy(hodlr_ctx* ctx) {
 int hodlr_ctx_set_stream(hodlr_ctx* ctx, void* stream) {
   if (!ctx) return HODLR_EINVAL;
   ctx->s = stream ? (cudaStream_t)stream : ctx->own;
+  return HODLR_OK;
+}
+
+int hodlr_ctx_set_cluster(hodlr_ctx* ctx, int cluster) {
+  if (!ctx) return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  if (cluster < 1 || cluster > qr_max_cluster()) return HODLR_EINVAL;
+  ctx->cluster = cluster;
+  return HODLR_OK;
+}
+
+int hodlr_ctx_get_cluster(hodlr_ctx* ctx, int* cluster) {
+  if (!ctx || !cluster) return HODLR_EINVAL;
+  *cluster = ctx->cluster;
   return HODLR_OK;
 }
 
@@ -1221,7 +1256,7 @@ int hodlr_qr_graph(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm) {
   HQ_CUDA_OK(cudaSetDevice(ctx->dev));
   int rc = ensure_plan(ctx, A, tol, anorm);
   if (rc) return rc;
-  if (!A->gexec || A->g_tol != tol || A->g_anorm != anorm) {
+  if (!A->gexec || A->g_tol != tol || A->g_anorm != anorm || A->g_cluster != ctx->cluster) {
     if (A->gexec) cudaGraphExecDestroy(A->gexec);
     A->gexec = nullptr;
     cudaGraph_t g;
@@ -1236,6 +1271,7 @@ int hodlr_qr_graph(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm) {
     if (e != cudaSuccess) return cuda_fail(e, __FILE__, __LINE__);
     A->g_tol = tol;
     A->g_anorm = anorm;
+    A->g_cluster = ctx->cluster;
   }
   HQ_CUDA_OK(cudaGraphLaunch(A->gexec, ctx->s));
   A->factored = true;
@@ -1351,7 +1387,8 @@ int hodlr_qr_batched_graph(hodlr_ctx* ctx, int count, hodlr_mat* const* A, doubl
   }
   if (rc) return rc;
   std::vector<hodlr_mat*> key(A, A + count);
-  if (!ctx->bgraph || replan || key != ctx->bmats || ctx->btol != tol || ctx->banorm != anorm) {
+  if (!ctx->bgraph || replan || key != ctx->bmats || ctx->btol != tol || ctx->banorm != anorm ||
+      ctx->bcluster != ctx->cluster) {
     if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
     ctx->bgraph = nullptr;
     cudaGraph_t g;
@@ -1366,6 +1403,7 @@ int hodlr_qr_batched_graph(hodlr_ctx* ctx, int count, hodlr_mat* const* A, doubl
     ctx->bmats = key;
     ctx->btol = tol;
     ctx->banorm = anorm;
+    ctx->bcluster = ctx->cluster;
   }
   HQ_CUDA_OK(cudaGraphLaunch(ctx->bgraph, ctx->s));
   for (int i = 0; i < count; ++i) A[i]->factored = true;
@@ -1428,12 +1466,13 @@ static int temp_plan(hodlr_ctx* ctx, hodlr_mat* A, F&& body) {
   // a temporary plan must not shrink the arena the factorization plan uses; build_plan only grows it
   // but would rewrite pointers of the cached factorization plan if it reallocates: drop that plan then.
   char* before = A->arena;
+  char* before2 = A->arena2;
   int rc = build_plan(A, P, ctx->cluster, 0.0, body);
   if (rc) {
     free_plan(P);
     return rc;
   }
-  if (A->arena != before && A->planned) {
+  if ((A->arena != before || A->arena2 != before2) && A->planned) {
     free_plan(A->plan);
     A->planned = false;
     if (A->gexec) {
@@ -1629,8 +1668,8 @@ int hodlr_dense_qr(hodlr_ctx* ctx, int h, int w, double* A, int lda, double* T, 
   QRDesc q = {};
   q.A = A; q.lda = lda; q.h = h; q.w = w; q.href = -1; q.wref = -1; q.tau = tau; q.T = T; q.ldt = ldt;
   q.G = G; q.ldg = k; q.step = kStepNone; q.fmode = 0;
-  cudaMemcpy(dq, &q, sizeof(QRDesc), cudaMemcpyHostToDevice);
-  cudaError_t e = launch_qr(&q, 1, dq, nullptr, nullptr, ctx->cluster, ctx->s);
+  cudaError_t e = cudaMemcpyAsync(dq, &q, sizeof(QRDesc), cudaMemcpyHostToDevice, ctx->s);
+  if (e == cudaSuccess) e = launch_qr(&q, 1, dq, nullptr, nullptr, ctx->cluster, ctx->s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->s);
   cudaFree(tau);
   cudaFree(G);

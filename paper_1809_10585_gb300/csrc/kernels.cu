@@ -122,6 +122,37 @@ __global__ void __launch_bounds__(GT) gemm_kernel(const GemmDesc* __restrict__ d
         }
       }
     }
+  if (!to_part || d.tile_count == nullptr) return;
+  // split-K: the last split to finish this tile sums the partials in split order (the result
+  // does not depend on arrival order) and resets the counter for the next use
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int* cnt = d.tile_count + t;
+    last = (atomicAdd(cnt, 1) == d.ksplit - 1);
+    if (last) *cnt = 0;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  int nsp = 0;
+  for (int sp = 0; sp < d.ksplit; ++sp)
+    if (sp * kchunk < k) nsp = sp + 1;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      int gi = row0 + ty + 16 * a, gj = col0 + tx + 16 * b;
+      if (gi < m && gj < n) {
+        double sacc = 0.0;
+        for (int sp = 0; sp < nsp; ++sp) sacc += __ldcg(&d.part[(size_t)sp * d.m * d.n + gi + (size_t)gj * d.m]);
+        double* c = d.C + gi + (size_t)gj * d.ldc;
+        double v = alpha * sacc;
+        if (d.beta != 0.0) v = fma(d.beta, *c, v);
+        *c = v;
+      }
+    }
 }
 
 // Sum split-K partials: C = alpha * sum_s part_s + beta * C.  One block per 256 outputs.

@@ -68,6 +68,7 @@ class Server:
         import torch
         self.torch = torch
         self.device = device
+        self.dev = f"cuda:{device}"      # where right-hand sides are staged
         self.slots = [B.Context(device) for _ in range(slots)]
         self.free = deque(range(slots))
         self.budget = float(hbm_budget)
@@ -143,27 +144,39 @@ class Server:
             M.free()
             self.used -= b
 
+    def _producer_pending(self, key):
+        """A FactorSolve that will keep factors under `key` is waiting or running."""
+        if any(isinstance(r, FactorSolve) and r.keep and r.key == key for _, r, _ in self.waiting):
+            return True
+        return any(a[6] == "factor_solve" and a[1].keep and a[1].key == key for a in self.active.values())
+
     def _admit(self):
         torch = self.torch
-        while self.waiting and self.free:
-            rid, req, t_arr = self.waiting[0]
-            need = self._bytes_of(req)
+        # first come, first served, except that a solve whose factors are not ready yet (still
+        # being factored, or busy with another solve) lets later requests pass
+        for item in list(self.waiting):
+            if not self.free:
+                return
+            rid, req, t_arr = item
             if isinstance(req, Solve):
                 if req.key not in self.resident:
+                    if self._producer_pending(req.key):
+                        continue
                     raise KeyError(f"no resident factors under {req.key!r}")
                 if any(a[2] is self.resident[req.key][0] for a in self.active.values()):
-                    return                       # one solve per resident matrix at a time
+                    continue                     # one solve per resident matrix at a time
+            need = self._bytes_of(req)
             self._evict_for(need)
             if self.used + need > self.budget and self.active:
                 return                           # wait for memory to free up
-            self.waiting.popleft()
+            self.waiting = deque(x for x in self.waiting if x[0] != rid)
             slot = self.free.popleft()
             ctx = self.slots[slot]
             rhs = np.asarray(req.rhs, dtype=np.float64)
             if rhs.ndim == 1:
                 rhs = rhs[:, None]
             nrhs = rhs.shape[1]
-            bt = torch.from_numpy(np.ascontiguousarray(rhs.T)).to(f"cuda:{self.device}")
+            bt = torch.from_numpy(np.ascontiguousarray(rhs.T)).to(self.dev)
             if isinstance(req, Solve):
                 M, _ = self.resident[req.key]
                 self.resident.move_to_end(req.key)

@@ -18,6 +18,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 from tests import gpu_util as U  # noqa: E402
+from paper_1809_10585_gb300 import binding as B  # noqa: E402
 
 
 def dgeqrt_full(A):
@@ -158,6 +159,57 @@ def test_hqr_no_truncation_equals_lapack(n, nmin, k, seed):
     np.testing.assert_allclose(T, Tl, atol=tolx)
 
 
+@pytest.mark.parametrize("cluster", [1, 2, 4, 8])
+@pytest.mark.parametrize("n,nmin,k,tol,dec,seed", [
+    (2048, 256, 10, 1e-12, 14.0, 0),    # the ill-conditioned family at n = 2048
+    (777, 64, 4, 1e-12, 6.0, 2),        # ragged, column-scaled
+])
+def test_hqr_matches_oracle_at_every_cluster_size(cluster, n, nmin, k, tol, dec, seed):
+    c = U.ctx()
+    cmax = c.cluster
+    c.cluster = cluster
+    try:
+        inp = W.random_hodlr(n, nmin, k, seed=seed, col_scale_decades=dec)
+        _check_against_oracle(inp, tol)
+    finally:
+        c.cluster = cmax
+
+
+@pytest.mark.parametrize("cluster", [1, 4])
+def test_hqr_no_truncation_equals_lapack_small_clusters(cluster):
+    c = U.ctx()
+    cmax = c.cluster
+    c.cluster = cluster
+    try:
+        test_hqr_no_truncation_equals_lapack(200, 24, 4, 3)
+    finally:
+        c.cluster = cmax
+
+
+def test_cluster_size_is_validated_and_graphs_follow_it():
+    c = U.ctx()
+    cmax = c.cluster
+    assert 1 <= cmax <= 16
+    for bad in (0, -1, cmax + 1):
+        with pytest.raises(B.HodlrError):
+            c.cluster = bad
+    assert c.cluster == cmax
+    inp = W.random_hodlr(1024, 128, 5, seed=5)
+    M = U.gpu_qr(inp, 1e-10, anorm=0.0, graph=True)
+    R16 = U.dense_of(M, 2).cpu().numpy()
+    try:
+        c.cluster = 2
+        M.qr_graph(1e-10, 0.0)          # re-captured with 2-CTA clusters
+        c.sync()
+        R2 = U.dense_of(M, 2).cpu().numpy()
+        E = U.gpu_qr(inp, 1e-10, anorm=0.0)     # eager, same cluster size
+        assert np.array_equal(U.dense_of(E, 2).cpu().numpy(), R2)
+    finally:
+        c.cluster = cmax
+    an = np.linalg.norm(W.to_dense(inp), 2)
+    assert np.abs(np.abs(np.diag(R2)) - np.abs(np.diag(R16))).max() <= 1e-8 * an
+
+
 def test_hqr_zero_rank_blocks():
     inp = W.zero_rank(400, 50, seed=2)
     M = U.gpu_qr(inp, 1e-10, anorm=1.0)
@@ -227,3 +279,24 @@ def test_invalid_arguments_are_rejected():
     M = B.Matrix(U.ctx(), inp)
     tb, pb, ld = U.dev(np.ones((256, 1)))
     assert B.lib().hodlr_solve(U.ctx().h, M.h, 1, B._VP(pb), ld) == B.HODLR_ESTATE   # before qr
+
+
+@pytest.mark.parametrize("nL,nR,K", [(12, 40, 13), (30, 30, 45), (64, 20, 70)])
+def test_truncate_without_threshold_keeps_an_orthonormal_basis(nL, nR, K):
+    """thr = 0 keeps every nonzero singular value.  When the core has more columns than rows,
+    one-sided Jacobi drives some columns to noise (even denormal) size; they are kept, so they
+    must still come out orthonormal and the product must be reproduced."""
+    rng = np.random.default_rng(nL * K)
+    L = rng.standard_normal((nL, K))
+    Rt = rng.standard_normal((nR, K))
+    tl, pl, _ = U.dev(L)
+    tr, pr, _ = U.dev(Rt)
+    to, po, _ = U.empty(nL, 128)
+    tq, pq, _ = U.empty(nR, 128)
+    from paper_1809_10585_gb300 import binding as B
+    rc, k = B.truncate(U.ctx(), nL, nR, K, pl, pr, 0.0, 128, po, pq)
+    assert rc == 0 and k >= min(nL, nR, K)
+    Lg, Rg = U.host(to, nL, k), U.host(tq, nR, k)
+    M = L @ Rt.T
+    np.testing.assert_allclose(Lg @ Rg.T, M, atol=1e-12 * np.abs(M).max())
+    np.testing.assert_allclose(Lg.T @ Lg, np.eye(k), atol=1e-12)
