@@ -12,7 +12,10 @@ Timed arms (one JSON line on rank 0):
              (256 MiB write) between steps outside the timed events.
   e2e        the same through the public C ABI with host buffers: pinned host -> device upload of
              the matrix, factorization, and a device -> host read of the whole factorization.
+  single_matrix  the plain one-matrix-at-a-time path (16-CTA clusters) on the same GPU.
   roofline   the dominant kernel kind from an event-instrumented run of the same factorization.
+  served     p50/p99 latency of a Poisson stream of factorize+solve and repeat-solve requests
+             through the continuously batched server.
   cpu_baseline  the CPU oracle timed on the host cores on one factorization of the same workload.
 
 `--impl reference` times the CPU oracle itself (the paper publishes no code and no timings).
@@ -29,6 +32,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -38,7 +43,7 @@ UNIT = "factorizations/s"
 WORKLOAD = "hodlr_qr_n8192_nmin256_k10_colscaled1e-14_tol1e-12"
 N, NMIN, K, DECADES, TOL = 8192, 256, 10, 14.0, 1e-12
 RANK_CAP = 128
-BATCH_CLUSTER = 8          # default cluster size when several matrices are factored per step
+BATCH_CLUSTER = 4          # default cluster size when several matrices are factored per step
 # FP64 ALU peak from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
 # (the DFMA rate of one SM, 2 per clock, was measured with an FMA throughput loop)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -133,6 +138,57 @@ def time_oracle(inp, reps=1):
     return min(ts)
 
 
+def served_requests(seed=4242, count=32, mean_gap_s=0.05):
+    """A factorize+solve request stream: Poisson arrivals; matrices from the random (n = 1024,
+    2048), ill-conditioned column-scaled (n = 2048, 4096), kernel-generated (n = 2048) and
+    symmetric banded (b = 8, n = 4096, 8192) families; 1-64 right-hand sides; a third of the
+    requests are repeat solves with factors kept on the device."""
+    import workloads as W
+    from paper_1809_10585_gb300 import server as S
+    rng = np.random.default_rng(seed)
+    makers = [
+        lambda i: W.random_hodlr(int(rng.choice([1024, 2048])), 128, 5, seed=seed + i),
+        lambda i: W.scaled_config1(int(rng.choice([2048, 4096])), 256, 10, seed=seed + i, decades=10.0),
+        lambda i: W.kernel_hodlr(2048, 256, 1e-12, seed=seed + i),
+        lambda i: W.banded_hodlr(int(rng.choice([4096, 8192])), 8, 256, seed=seed + i),
+    ]
+    reqs, kept, t = [], [], 0.0
+    for i in range(count):
+        t += float(rng.exponential(mean_gap_s))
+        nrhs = int(rng.integers(1, 65))
+        if kept and rng.uniform() < 1.0 / 3.0:
+            key, n = kept[int(rng.integers(len(kept)))]
+            reqs.append(S.Solve(key, W.rhs(n, nrhs, seed=seed + 1000 + i), arrival=t))
+            continue
+        inp = makers[i % len(makers)](i)
+        keep = bool(rng.uniform() < 0.5)
+        key = f"r{i}" if keep else None
+        reqs.append(S.FactorSolve(inp, W.rhs(inp.n, nrhs, seed=seed + 2000 + i), TOL, keep, key, arrival=t))
+        if keep:
+            kept.append((key, inp.n))
+    return reqs
+
+
+def served_leg(device):
+    """Run the request stream through the continuously batched server; p50/p99 latency is from
+    arrival to the solution being back on the host."""
+    from paper_1809_10585_gb300 import server as S
+    reqs = served_requests()
+    nfac = sum(1 for r in reqs if isinstance(r, S.FactorSolve))
+    srv = S.Server(device, slots=8, hbm_budget=120e9, rank_cap=256)
+    t0 = time.perf_counter()
+    out = srv.run(reqs)
+    wall = time.perf_counter() - t0
+    lat = srv.latencies()
+    srv.close()
+    return {"p50_s": lat["p50_s"], "p99_s": lat["p99_s"], "requests": len(out), "factorizations": nfac,
+            "solves_on_resident_factors": len(out) - nfac, "wall_s": wall,
+            "requests_per_s": len(out) / wall, "arrivals": "Poisson, mean gap 50 ms",
+            "families": "random n=1024/2048; column-scaled kappa~1e10 n=2048/4096; kernel 1/(x-y) n=2048; "
+                        "banded b=8 n=4096/8192; 1-64 right-hand sides",
+            "slots": 8, "hbm_budget_gb": 120}
+
+
 def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -157,7 +213,6 @@ def reference_arm(args):
 
 
 def gpu_arm(args):
-    import numpy as np
     import torch
 
     ws, rank, local = dist_env()
@@ -333,6 +388,8 @@ def gpu_arm(args):
             "single_matrix": single,
             "gpu_launches": gpu_launches}
 
+    if rank == 0 and not args.no_served:
+        line["served"] = served_leg(local)
     if rank == 0 and not args.no_cpu_baseline:
         t = time_oracle(inp)
         line["cpu_baseline"] = {"value": 1.0 / t, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
@@ -352,8 +409,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batch", type=int, default=16,
+    ap.add_argument("--batch", type=int, default=32,
                     help="matrices of the workload factored concurrently per step (cross-matrix batching)")
+    ap.add_argument("--no-served", action="store_true",
+                    help="skip the served request stream (p50/p99 latency)")
     ap.add_argument("--cluster", type=int, default=0,
                     help="CTAs per thread-block cluster of the QR/Jacobi kernels (0: automatic)")
     args = ap.parse_args()

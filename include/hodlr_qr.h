@@ -153,6 +153,29 @@ int hodlr_ranks(hodlr_ctx* ctx, const hodlr_mat* A, int* r12, int* r21, int* rT)
 int hodlr_flops(hodlr_ctx* ctx, const hodlr_mat* A, double* out);
 
 /*
+ * hodlr_build_dense — HODLR approximation of a dense n x n matrix held on the device (Sec. 2.1.1,
+ * the construction of a HODLR matrix by truncated SVDs of the off-diagonal blocks).
+ *   A_dev: column-major n x n FP64 device array, leading dimension lda >= n (read only, owned
+ *   by the caller).  Partition and rank capacity as in hodlr_build.  Diagonal leaf blocks are
+ *   copied.  Every off-diagonal block B of the cluster tree is sampled by a randomized range
+ *   finder (Halko, Martinsson and Tropp 2011, Alg. 4.1) with min(rank_cap + 16, rows, cols)
+ *   Gaussian columns drawn from the counter-based stream `seed`, orthonormalized by Householder
+ *   QR, and the sampled block Q Q^T B is truncated to its singular triplets with sigma > tol
+ *   (absolute), as T_eps does.  With at least 16 columns of oversampling beyond the kept rank
+ *   the sampling error stays at the level of the first discarded singular value.
+ * Synchronous.  HODLR_ERANK (nothing allocated) if a block keeps more than rank_cap terms;
+ * HODLR_EINVAL for bad arguments; HODLR_ENOMEM.  The result is an ordinary matrix handle.
+ */
+int hodlr_build_dense(hodlr_ctx* ctx, int n, int nleaf, const int* leaf_sizes, const double* A_dev, int lda,
+                      double tol, int rank_cap, unsigned long long seed, hodlr_mat** out);
+
+/* Largest stored rank of the lower blocks (Y's after hodlr_qr, A's before), of T and of the
+ * upper blocks (R's after hodlr_qr), and the device bytes of the matrix storage (the paper's
+ * Table 3 quantities).  Any pointer may be NULL.  Synchronous. */
+int hodlr_stats(hodlr_ctx* ctx, const hodlr_mat* A, int* max_rank_Y, int* max_rank_T, int* max_rank_R,
+                size_t* bytes);
+
+/*
  * Dense n x n copy of a part of the stored matrix into out_dev (leading dimension ld >= n):
  * which = 0: A as stored (full), 1: Y (unit lower part), 2: R (upper part), 3: T.
  */

@@ -118,6 +118,33 @@ def from_input(inp) -> HNode:
     return build(0)
 
 
+def compress(A, leaf_sizes, thr) -> HNode:
+    """HODLR approximation of a dense matrix by the construction of Sec. 2.1.1: on the cluster
+    tree of the partition ``leaf_sizes`` (first half of every split to the first child), the
+    diagonal blocks of the leaves are kept dense and every off-diagonal block A12 / A21 of an
+    internal node is replaced by its truncated SVD, the singular triplets with sigma > thr
+    (U = left vectors, V = right vectors times sigma)."""
+    A = np.asarray(A, dtype=np.float64)
+    offs = np.concatenate([[0], np.cumsum(leaf_sizes)]).astype(int)
+    nleaf = len(leaf_sizes)
+
+    def block_svd(B):
+        u, sv, vt = _svd(B)
+        k = int(np.sum(sv > thr))
+        return np.asfortranarray(u[:, :k]), np.asfortranarray(vt[:k].T * sv[:k][None, :])
+
+    def build(first, count):
+        lo, hi = offs[first], offs[first + count]
+        if count == 1:
+            return HNode.make_leaf(np.asfortranarray(A[lo:hi, lo:hi]))
+        h = count // 2
+        mid = offs[first + h]
+        U12, V12 = block_svd(A[lo:mid, mid:hi])
+        U21, V21 = block_svd(A[mid:hi, lo:mid])
+        return HNode.make_internal(build(first, h), build(first + h, count - h), U12, V12, U21, V21)
+
+    return build(0, nleaf)
+
 def to_dense(H: HNode, part="full") -> np.ndarray:
     """Dense matrix of a HODLR node.  part='full' | 'unit_lower' (strictly lower leaves, unit
     diagonal, lower blocks) | 'upper' (upper-triangular leaves and upper blocks)."""
@@ -195,6 +222,16 @@ def _econ_qr(A, step):
     return np.linalg.qr(A, mode="reduced")
 
 
+def _svd(M):
+    """Economy SVD (the SVD of Sec. 2.1.1).  LAPACK's divide-and-conquer driver (dgesdd) can
+    fail to converge on rare, strongly graded cores; the QR-iteration driver (dgesvd) then
+    computes the same decomposition."""
+    try:
+        return np.linalg.svd(M, full_matrices=False)
+    except np.linalg.LinAlgError:
+        return scipy.linalg.svd(M, full_matrices=False, lapack_driver="gesvd")
+
+
 def left_orthogonalize(L, Rt, step="a3_left_orth"):
     """Left-orthogonal form of the block L Rt^T (Sec. 2.1): L = Q R, L <- Q, Rt <- Rt R^T."""
     Q, R = _econ_qr(L, step)
@@ -218,7 +255,7 @@ def truncate(L, Rt, eps, step="a9_recompress"):
     M = _mm(R1, R2.T, step)
     p, q = max(M.shape), min(M.shape)
     FLOPS[step] += 4 * p * p * q + 8 * p * q * q + 9 * q ** 3
-    Ut, s, Vth = np.linalg.svd(M, full_matrices=False)
+    Ut, s, Vth = _svd(M)
     k = int(np.sum(s > eps))
     if TRACE_ON:
         TRACE.append((step, nL, nR, K, k))

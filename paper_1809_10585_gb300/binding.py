@@ -39,6 +39,9 @@ _SIGS = {
     "hodlr_ctx_get_cluster": (C.c_int, [_VP, _PI]),
     "hodlr_sync": (C.c_int, [_VP]),
     "hodlr_build": (C.c_int, [_VP, C.c_int, C.c_int, _PI, _PPD, _PPD, _PPD, _PI, _PPD, _PPD, _PI, C.c_int, C.POINTER(_VP)]),
+    "hodlr_build_dense": (C.c_int, [_VP, C.c_int, C.c_int, _PI, _VP, C.c_int, C.c_double, C.c_int, C.c_ulonglong,
+                                    C.POINTER(_VP)]),
+    "hodlr_stats": (C.c_int, [_VP, _VP, _PI, _PI, _PI, C.POINTER(C.c_size_t)]),
     "hodlr_free": (None, [_VP]),
     "hodlr_upload": (C.c_int, [_VP, _VP, _PPD, _PPD, _PPD, _PI, _PPD, _PPD, _PI]),
     "hodlr_snapshot": (C.c_int, [_VP, _VP]),
@@ -174,6 +177,27 @@ class Matrix:
         check(lib().hodlr_build(ctx.h, self.n, self.nleaf, sizes, leaves, U12, V12, r12, U21, V21, r21,
                                 rank_cap, C.byref(self.h)), "hodlr_build")
         self.rank_cap = rank_cap
+
+    @classmethod
+    def from_dense(cls, ctx: Context, n: int, leaf_sizes, A_ptr: int, lda: int, tol: float, rank_cap: int = 128,
+                   seed: int = 0):
+        """HODLR approximation of a dense column-major device matrix (hodlr_build_dense)."""
+        self = cls.__new__(cls)
+        self.ctx = ctx
+        self.n = int(n)
+        self.nleaf = len(leaf_sizes)
+        self.h = _VP()
+        sizes = (C.c_int * self.nleaf)(*[int(x) for x in leaf_sizes])
+        check(lib().hodlr_build_dense(ctx.h, self.n, self.nleaf, sizes, _VP(A_ptr), lda, tol, rank_cap, seed,
+                                      C.byref(self.h)), "hodlr_build_dense")
+        self.rank_cap = rank_cap
+        return self
+
+    def stats(self):
+        y, t, r = C.c_int(), C.c_int(), C.c_int()
+        b = C.c_size_t()
+        check(lib().hodlr_stats(self.ctx.h, self.h, C.byref(y), C.byref(t), C.byref(r), C.byref(b)), "hodlr_stats")
+        return {"max_rank_Y": y.value, "max_rank_T": t.value, "max_rank_R": r.value, "bytes": b.value}
 
     def upload(self, inp):
         sizes, leaves, U12, V12, r12, U21, V21, r21, keep = _marshal(inp)

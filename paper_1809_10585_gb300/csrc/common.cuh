@@ -166,6 +166,7 @@ cudaError_t launch_select(const SelectDesc* h, int n, SelectDesc* d, int* devint
 cudaError_t launch_copy(const CopyDesc* h, int n, CopyDesc* d, const int* devints, cudaStream_t s);
 cudaError_t launch_set_ints(int* devints, const int* idx_vals, int n, int* scratch, cudaStream_t s);
 cudaError_t launch_fill(double* p, size_t n, double v, cudaStream_t s);
+cudaError_t launch_gauss(double* p, size_t n, unsigned long long seed, cudaStream_t s);
 cudaError_t launch_norm_scale(double* x, int n, double* out_norm, int mode, cudaStream_t s);
 cudaError_t launch_set_diag_identity(double* p, int ld, int rows, int cols, cudaStream_t s);
 cudaError_t launch_check_finite(const double* p, int ld, int rows, int cols, int* flag, cudaStream_t s);

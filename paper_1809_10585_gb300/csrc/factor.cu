@@ -72,7 +72,7 @@ __device__ void qr_build_T(const QRDesc& d, const double* A, const size_t lda, c
   const size_t ldt = d.ldt;
   cl.sync();   // all columns final
   {
-    const int gw = crank * QW + warp, nw = C * QW;
+    const int gw = warp * C + crank, nw = C * QW;   // consecutive items on different SMs
     const long npairs = (long)kmax * (kmax - 1) / 2;
     for (long p = gw; p < npairs; p += nw) {
       // decode p -> (i, jj) with i < jj, jj-major
@@ -95,7 +95,7 @@ __device__ void qr_build_T(const QRDesc& d, const double* A, const size_t lda, c
   }
   cl.sync();
   {
-    const int gw = crank * QW + warp, nw = C * QW;
+    const int gw = warp * C + crank, nw = C * QW;   // consecutive items on different SMs
     const int nblk = (kmax + TNB - 1) / TNB;
     for (int b = gw; b < nblk; b += nw) {
       const int b0 = b * TNB, b1 = min(kmax, b0 + TNB);
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(QT) qr_cluster_kernel(const QRDesc* __restrict
       const double alpha = __ldcg(&A[j + j * lda]);
       double tau = 0.0, scal = 0.0;
       if (s > 0.0) {
-        const double hn = hypot(alpha, sqrt(s));
+        const double hn = sqrt(fma(alpha, alpha, s));   // s: plain sum of squares
         const double beta = -copysign(hn, alpha);
         tau = (beta - alpha) / beta;
         scal = 1.0 / (alpha - beta);
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __
 
 __global__ void __launch_bounds__(QT) jacobi_dsmem_kernel(const JacobiDesc* __restrict__ descs,
                                                           const int* __restrict__ di, double* flops,
-                                                          int q1cap, int q2cap);
+                                                          int q1cap, int q2cap, int owner_form);
 constexpr size_t kJacobiSmemMax = 200 * 1024;
 
 
@@ -371,7 +371,8 @@ __global__ void __launch_bounds__(QT) qr_dsmem_kernel(const QRDesc* __restrict__
         const double alpha = cj[j];
         double tau = 0.0, scal = 0.0;
         if (s > 0.0) {
-          const double hn = hypot(alpha, sqrt(s));
+          // s is already a plain sum of squares, so |(alpha, x)| needs no further scaling
+          const double hn = sqrt(fma(alpha, alpha, s));
           const double beta = -copysign(hn, alpha);
           tau = (beta - alpha) / beta;
           scal = 1.0 / (alpha - beta);
@@ -401,18 +402,22 @@ __global__ void __launch_bounds__(QT) qr_dsmem_kernel(const QRDesc* __restrict__
       if (tau != 0.0) {
         if (in_regs) {
           double r[kQRRegs];
-          double t = 0.0;
+          double t0 = 0.0, t1 = 0.0;             // two chains: half the dependent FMA latency
           const int nq = (h - j - 1 + 31) >> 5;   // warp-uniform live register slots
 #pragma unroll
           for (int q = 0; q < kQRRegs; ++q) {
             if (q < nq) {
               const int i = j + 1 + lane + 32 * q;
               r[q] = i < h ? a[i] : 0.0;
-              if (i < h) t = fma(ybuf[i], r[q], t);
+              if (i < h) {
+                if (q & 1) t1 = fma(ybuf[i], r[q], t1);
+                else t0 = fma(ybuf[i], r[q], t0);
+              }
             }
           }
-          t = warp_sum2(t);
+          double t = warp_sum2(t0 + t1);
           const double wv = tau * (t + a[j]);
+          double nn1 = 0.0;
 #pragma unroll
           for (int q = 0; q < kQRRegs; ++q) {
             if (q < nq) {
@@ -420,10 +425,14 @@ __global__ void __launch_bounds__(QT) qr_dsmem_kernel(const QRDesc* __restrict__
               if (i < h) {
                 const double v = fma(-wv, ybuf[i], r[q]);
                 a[i] = v;
-                if (i > j + 1) nn = fma(v, v, nn);
+                if (i > j + 1) {
+                  if (q & 1) nn1 = fma(v, v, nn1);
+                  else nn = fma(v, v, nn);
+                }
               }
             }
           }
+          nn += nn1;
           __syncwarp();
           if (lane == 0) a[j] -= wv;
         } else {
@@ -447,9 +456,11 @@ __global__ void __launch_bounds__(QT) qr_dsmem_kernel(const QRDesc* __restrict__
         if (lane == 0) xn_next = nn;
       }
     }
+    // One cluster barrier per column suffices.  sh_tau of a CTA is rewritten only when it owns
+    // a column again, C >= 2 columns later, after every CTA has arrived at the barrier of the
+    // column before that one, i.e. after every CTA finished reading this reflector; the rows of
+    // column j read remotely are final; ybuf and xn_next are private to the CTA.
     __syncthreads();
-    // the next owner may overwrite sh_tau / its pivot only after every CTA read this reflector
-    cl.sync();
   }
   for (int sl = 0; sl < nloc; ++sl) {
     const int c = crank + sl * C;
@@ -530,6 +541,58 @@ cudaError_t launch_qr(const QRDesc* h, int n, QRDesc* d, const int* devints, dou
 }
 
 // --------------------------------------------------------------------------------- Jacobi
+// 2^k as a double, for -1022 <= k <= 1023 (exact).
+__device__ inline double pow2i(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
+
+// Plane rotation of one column pair of one-sided Jacobi from alpha = |x|^2 > 0, beta = |y|^2 > 0
+// and gamma = x.y.  Returns false when the pair is orthogonal to the relative tolerance tol
+// (gamma^2 <= tol^2 alpha beta).  Otherwise t = tan(theta) is the root of magnitude <= 1 of
+// gamma t^2 + (beta - alpha) t - gamma = 0 and (c, s) = (1, t) / sqrt(1 + t^2).
+//
+// FP64 instructions are the scarce resource here (an SM retires one FP64 warp instruction per
+// ~16 cycles, each with ~67 cycles of latency; divide and square root are sequences of
+// 450-700 cycles), so only what needs FP64 uses it.  The inputs are scaled by one power of two
+// to O(1) (exact; the test and t are scale-invariant), the test and t are formed in FP32, and
+// (c, s) are taken from FP32 values c0, s0 and normalized in FP64 with the series
+// (1 + d)^(-1/2) = 1 - d/2 + 3 d^2 / 8, d = c0^2 + s0^2 - 1 = O(1e-7), so that c^2 + s^2 = 1
+// to FP64 rounding: the rotation is orthogonal to working precision, only the angle carries the
+// FP32 error (a slightly less effective rotation, never a less accurate one).  Pairs whose
+// scaled values leave the normal FP32 range (norms more than ~1e30 apart, or gamma below
+// 1e-30 max(alpha, beta)) take the plain FP64 formulas.
+__device__ inline bool jacobi_rotation(double al, double be, double g, double tol2, float tolf, double& c,
+                                       double& s, double& t) {
+  const long long im = max(__double_as_longlong(al), __double_as_longlong(be));  // order of
+  int ex = (int)(im >> 52) - 1023;                                                // positive doubles
+  ex = min(max(ex, -1000), 1000);
+  const double sc = pow2i(-ex);
+  const double a2 = al * sc, b2 = be * sc, g2 = g * sc;
+  const float af = (float)a2, bf = (float)b2, gf = (float)g2;
+  if (fminf(af, bf) > 1e-30f && fabsf(gf) > 1e-30f) {
+    // |g| > tol sqrt(a) sqrt(b): every factor stays in the normal FP32 range here (a squared
+    // form would underflow for columns far apart in norm and wrongly stop rotations)
+    if (!(fabsf(gf) > tolf * sqrtf(af) * sqrtf(bf))) return false;
+    const float zf = __fdividef(bf - af, 2.0f * gf);
+    float tf;
+    if (fabsf(zf) > 1e18f) tf = __fdividef(0.5f, zf);
+    else tf = __fdividef(copysignf(1.0f, zf), fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)));
+    const float cf = rsqrtf(fmaf(tf, tf, 1.0f));
+    const double c0 = (double)cf, s0 = (double)(cf * tf);
+    const double dd = fma(c0, c0, fma(s0, s0, -1.0));
+    const double pc = fma(fma(0.375, dd, -0.5), dd, 1.0);
+    c = c0 * pc;
+    s = s0 * pc;
+    t = (double)tf;
+    return true;
+  }
+  if (!(g2 * g2 > tol2 * a2 * b2)) return false;
+  const double zeta = (b2 - a2) / (2.0 * g2);
+  if (fabs(zeta) > 1e100) t = 0.5 / zeta;
+  else t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  c = 1.0 / sqrt(1.0 + t * t);
+  s = c * t;
+  return true;
+}
+
 __device__ inline void rr_pair(int r, int i, int P, int& a, int& b) {
   // round-robin (circle) schedule on P (even) players, round r in [0, P-1); r, i < P - 1
   if (i == 0) {
@@ -559,9 +622,11 @@ __global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __
   double* M = d.M;
   const size_t ldm = d.ldm;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gw = crank * QW + warp, nw = C * QW;
-  // relative orthogonality threshold for a pair
-  const double tol = fmin(1e-13, fmax(1e-15, 4.4e-16 * (double)q1));
+  const int gw = warp * C + crank, nw = C * QW;   // consecutive items on different SMs
+  // relative orthogonality threshold for a pair: 4 eps sqrt(q1) sits above the rounding noise of
+  // a computed cosine (about eps sqrt(q1)), so converged pairs stop, and keeps the kept basis
+  // orthogonal enough that the reconstruction error tol * sigma_1 stays far below thr
+  const double tol = fmin(1e-13, fmax(1e-15, 8.8e-16 * sqrt((double)q1)));
   // Columns whose squared norm is below dfl are left out of the rotations: they stay below
   // the truncation threshold and together change the core by at most 1e-2 * thr.
   double thr = d.thr;
@@ -622,12 +687,8 @@ __global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __
             g = fma(x[t], y[t], g);
           }
           g = warp_sum2(g);
-          if (!(fabs(g) > tol * sqrt(al) * sqrt(be))) continue;
-          const double zeta = (be - al) / (2.0 * g);
-          double tt;
-          if (fabs(zeta) > 1e100) tt = 0.5 / zeta;
-          else tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double c = 1.0 / sqrt(1.0 + tt * tt), sn = c * tt;
+          double c, sn, tt;
+          if (!(al > 0.0 && be > 0.0) || !jacobi_rotation(al, be, g, tol * tol, (float)tol, c, sn, tt)) continue;
 #pragma unroll
           for (int t = 0; t < kJacobiRegs; ++t) {
             const int i = lane + 32 * t;
@@ -645,12 +706,8 @@ __global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __
           double g = 0.0;
           for (int i = lane; i < q1; i += 32) g = fma(__ldcg(&ca[i]), __ldcg(&cb[i]), g);
           g = warp_sum2(g);
-          if (!(fabs(g) > tol * sqrt(al) * sqrt(be))) continue;
-          const double zeta = (be - al) / (2.0 * g);
-          double tt;
-          if (fabs(zeta) > 1e100) tt = 0.5 / zeta;
-          else tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double c = 1.0 / sqrt(1.0 + tt * tt), sn = c * tt;
+          double c, sn, tt;
+          if (!(al > 0.0 && be > 0.0) || !jacobi_rotation(al, be, g, tol * tol, (float)tol, c, sn, tt)) continue;
           for (int i = lane; i < q1; i += 32) {
             const double xv = __ldcg(&ca[i]), yv = __ldcg(&cb[i]);
             const double xn = c * xv - sn * yv;
@@ -678,13 +735,19 @@ __global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __
 }
 
 // One-sided Jacobi with the core held in distributed shared memory: column j lives in the
-// shared memory of CTA j % C.  A pair (a, b), a < b, is rotated by one warp of the CTA that
-// holds a; it reads and writes column b through DSMEM.  alpha, beta and gamma are formed from
-// the loaded columns in one pass, so a round costs one remote load, one remote store and one
-// cluster barrier.  Same pair schedule, thresholds and deflation as jacobi_cluster_kernel.
-__global__ void __launch_bounds__(QT) jacobi_dsmem_kernel(const JacobiDesc* __restrict__ descs,
-                                                          const int* __restrict__ di, double* flops,
-                                                          int q1cap, int q2cap) {
+// shared memory of CTA j % C.  Each warp rotates 32 / LG column pairs at once, one pair per
+// group of LG lanes (LG = 8, 16 or 32, the smallest with q1 <= LG * kJacobiRegs): the FP64
+// instructions that form the rotation (the scarce resource, see jacobi_rotation) are then
+// shared by several pairs, and the dot product needs only log2(LG) shuffle levels.  Control
+// flow stays warp-uniform: a group whose pair is converged, deflated or absent applies the
+// identity and stores nothing.  Pair (a, b) reads and writes both columns through DSMEM; per
+// round that is one remote load, one remote store and one cluster barrier.  Same pair schedule,
+// thresholds and deflation as jacobi_cluster_kernel.  Columns longer than LG * kJacobiRegs
+// (q1 > 256 for LG = 32) are streamed from shared memory twice instead of held in registers.
+template <int LG>
+__device__ __forceinline__ void jacobi_dsmem_impl(const JacobiDesc* __restrict__ descs, const int* __restrict__ di,
+                                                  double* flops, int q1cap, int q2cap) {
+  constexpr int PPW = 32 / LG;                            // pairs per warp and step
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int crank = (int)cl.block_rank();
@@ -705,11 +768,15 @@ __global__ void __launch_bounds__(QT) jacobi_dsmem_kernel(const JacobiDesc* __re
   double* M = d.M;
   const size_t ldm = d.ldm;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const double tol = fmin(1e-13, fmax(1e-15, 4.4e-16 * (double)q1));
+  const int sub = lane / LG, gl = lane % LG;             // pair slot in the warp, lane in the group
+  const double tol = fmin(1e-13, fmax(1e-15, 8.8e-16 * sqrt((double)q1)));   // as jacobi_cluster_kernel
+  const double tol2 = tol * tol;
+  const float tolf = (float)tol;
   double thr = d.thr;
   if (d.thr_ref) thr *= *d.thr_ref;
   const double dth = 1e-2 * thr / sqrt((double)max(q2, 1));
   const double dfl = dth * dth;
+  const long long dfl_bits = __double_as_longlong(dfl);
 
   if (crank == 0)
     for (int i = threadIdx.x; i < kMaxSweeps; i += QT) d.rot[i] = 0;
@@ -721,7 +788,9 @@ __global__ void __launch_bounds__(QT) jacobi_dsmem_kernel(const JacobiDesc* __re
   // every CTA of the cluster must be running before any distributed shared memory access
   cl.sync();
 
-  const int gw = crank * QW + warp, nw = C * QW;
+  const int gw = warp * C + crank, nw = C * QW;   // consecutive items on different SMs
+  const int nreg = (q1 + LG - 1) / LG;                   // register slots in use (uniform)
+  const bool inreg = nreg <= kJacobiRegs;
   for (int sweep = 0; sweep <= kMaxSweeps; ++sweep) {
     // exact squared norms of own columns, broadcast into every CTA's copy
     for (int sl = warp; sl < nloc; sl += QW) {
@@ -753,108 +822,104 @@ __global__ void __launch_bounds__(QT) jacobi_dsmem_kernel(const JacobiDesc* __re
     const int P = Ka + (Ka & 1);
     int local = 0;
     for (int r = 0; r < P - 1; ++r) {
-      for (int pi = gw; pi < P / 2; pi += nw) {
-        int ia, ib;
-        rr_pair(r, pi, P, ia, ib);
-        if (ia >= Ka || ib >= Ka) continue;
-        const int a = act[ia], b = act[ib];
+      for (int pb = gw * PPW; pb < P / 2; pb += nw * PPW) {
+        const int pi = pb + sub;
+        int ia = 0, ib = 0;
+        bool valid = pi < P / 2;
+        if (valid) {
+          rr_pair(r, pi, P, ia, ib);
+          valid = ia < Ka && ib < Ka;
+        }
+        const int a = valid ? act[ia] : 0, b = valid ? act[ib] : 0;
         double* xa = cl.map_shared_rank(cols, a % C) + (size_t)(a / C) * ldc;
         double* yb = cl.map_shared_rank(cols, b % C) + (size_t)(b / C) * ldc;
-        // alpha, beta: squared norms tracked through the sweep (exact at every sweep start);
-        // gamma is summed from the columns
         double* na_p = cl.map_shared_rank(cn, a % C) + a / C;
         double* nb_p = cl.map_shared_rank(cn, b % C) + b / C;
-        const double al = *na_p, be = *nb_p;
-        const bool inreg = q1 <= 32 * kJacobiRegs;
-        const int nreg = (q1 + 31) >> 5;   // warp-uniform: register slots beyond it are skipped
+        const double al = valid ? *na_p : 0.0, be = valid ? *nb_p : 0.0;
         double x[kJacobiRegs], y[kJacobiRegs];
-        double g = 0.0;
+        double g0 = 0.0, g1 = 0.0;
         if (inreg) {
 #pragma unroll
           for (int t = 0; t < kJacobiRegs; ++t) {
             if (t < nreg) {
-              const int i = lane + 32 * t;
-              x[t] = i < q1 ? xa[i] : 0.0;
-              y[t] = i < q1 ? yb[i] : 0.0;
-              g = fma(x[t], y[t], g);
+              const int i = gl + LG * t;
+              const bool in = valid && i < q1;
+              x[t] = in ? xa[i] : 0.0;
+              y[t] = in ? yb[i] : 0.0;
+              if (t & 1) g1 = fma(x[t], y[t], g1);
+              else g0 = fma(x[t], y[t], g0);
             }
           }
-        } else {
-          for (int i = lane; i < q1; i += 32) g = fma(xa[i], yb[i], g);
+        } else if (valid) {
+          for (int i = gl; i < q1; i += 2 * LG) {
+            g0 = fma(xa[i], yb[i], g0);
+            if (i + LG < q1) g1 = fma(xa[i + LG], yb[i + LG], g1);
+          }
         }
-        g = warp_sum2(g);
-        // convergence test and rotation on one lane (FP64 divide and square root are scarce),
-        // broadcast to the warp.  The test keeps the scale-safe form |g| > tol sqrt(al) sqrt(be):
-        // squaring underflows once a column decays to denormal size.
-        double c = 0.0, sn = 0.0, tt = 0.0;
-        int doit = 0;
-        if (lane == 0 && al > dfl && be > dfl && fabs(g) > tol * sqrt(al) * sqrt(be)) {
-          doit = 1;
-          const double zeta = (be - al) / (2.0 * g);
-          if (fabs(zeta) > 1e100) tt = 0.5 / zeta;
-          else tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          c = rsqrt(1.0 + tt * tt);
-          sn = c * tt;
+        double g = g0 + g1;
+#pragma unroll
+        for (int o = LG / 2; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+        // every lane of a group holds g and forms the same rotation (an FP64 instruction costs
+        // the same for one lane as for 32); the deflation test runs on the bit patterns
+        double c = 1.0, sn = 0.0, tt = 0.0;
+        const bool doit = valid && __double_as_longlong(al) > dfl_bits && __double_as_longlong(be) > dfl_bits &&
+                          jacobi_rotation(al, be, g, tol2, tolf, c, sn, tt);
+        if (!doit) {
+          c = 1.0;
+          sn = 0.0;
+          tt = 0.0;
         }
-        doit = __shfl_sync(0xffffffffu, doit, 0);
-        if (!doit) continue;
-        c = __shfl_sync(0xffffffffu, c, 0);
-        sn = __shfl_sync(0xffffffffu, sn, 0);
-        tt = __shfl_sync(0xffffffffu, tt, 0);
         // alpha' = alpha - t gamma, beta' = beta + t gamma; the shrinking column's norm is summed
         // exactly when it loses more than half of its mass (cancellation)
         const double tg = tt * g;
         const bool a_shrinks = tg > 0.0;
-        const bool exact = a_shrinks ? (tg > 0.5 * al) : (-tg > 0.5 * be);
-        double ss = 0.0;
+        const bool exact = doit && (a_shrinks ? (tg > 0.5 * al) : (-tg > 0.5 * be));
+        const bool any_exact = __any_sync(0xffffffffu, exact);
+        double s0 = 0.0, s1 = 0.0;
         if (inreg) {
 #pragma unroll
           for (int t = 0; t < kJacobiRegs; ++t) {
             if (t < nreg) {
               const double xn = c * x[t] - sn * y[t];
               const double yn = sn * x[t] + c * y[t];
-              x[t] = xn;
-              y[t] = yn;
-              const int i = lane + 32 * t;
-              if (i < q1) {
+              const int i = gl + LG * t;
+              if (doit && i < q1) {
                 xa[i] = xn;
                 yb[i] = yn;
               }
-            }
-          }
-          if (exact) {
-#pragma unroll
-            for (int t = 0; t < kJacobiRegs; ++t) {
-              if (t < nreg) {
-                const double v = a_shrinks ? x[t] : y[t];
-                ss = fma(v, v, ss);
+              if (any_exact) {
+                const double v = a_shrinks ? xn : yn;
+                if (t & 1) s1 = fma(v, v, s1);
+                else s0 = fma(v, v, s0);
               }
             }
           }
-        } else {
-          for (int i = lane; i < q1; i += 32) {
+        } else if (doit) {
+          for (int i = gl; i < q1; i += LG) {
             const double xv = xa[i], yv = yb[i];
             const double xn = c * xv - sn * yv;
             const double yn = sn * xv + c * yv;
             xa[i] = xn;
             yb[i] = yn;
-            if (exact) {
-              const double v = a_shrinks ? xn : yn;
-              ss = fma(v, v, ss);
-            }
+            const double v = a_shrinks ? xn : yn;
+            s0 = fma(v, v, s0);
           }
         }
-        if (exact) ss = warp_sum2(ss);
-        if (lane == 0) {
+        double ss = s0 + s1;
+        if (any_exact) {
+#pragma unroll
+          for (int o = LG / 2; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        }
+        if (doit && gl == 0) {
           const double na = fma(-tt, g, al), nb = fma(tt, g, be);
           *na_p = (exact && a_shrinks) ? ss : na;
           *nb_p = (exact && !a_shrinks) ? ss : nb;
+          ++local;
         }
-        ++local;
       }
       cl.sync();
     }
-    if (lane == 0 && local) atomicAdd(&d.rot[sweep], local);
+    if (local) atomicAdd(&d.rot[sweep], local);
     cl.sync();
     if (*(volatile int*)&d.rot[sweep] == 0) sweep = kMaxSweeps - 1;   // converged: final norms next pass
   }
@@ -867,14 +932,246 @@ __global__ void __launch_bounds__(QT) jacobi_dsmem_kernel(const JacobiDesc* __re
   cl.sync();   // no CTA may exit while others still access its shared memory
 }
 
+// One-sided Jacobi, owner-computes form.  Column j lives in the shared memory of CTA j % C, in
+// two buffers: round r reads buffer r & 1 and writes buffer (r + 1) & 1.  For every pair (a, b)
+// of a round, the CTA owning a and the CTA owning b both form the same rotation from the same
+// data (identical instruction sequences on identical inputs give identical results) and each
+// writes only its own column and norm, into its own shared memory.  Remote traffic is therefore
+// loads only; the one cluster barrier per round orders the round's writes before the next
+// round's reads and the round's reads before the buffer is written again.  A column without a
+// partner in a round is copied to the other buffer.  Lane groups, thresholds, deflation and the
+// exact-norm rule as in jacobi_dsmem_impl.
+template <int LG>
+__device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__ descs, const int* __restrict__ di,
+                                                  double* flops, int q1cap, int q2cap) {
+  constexpr int PPW = 32 / LG;                            // pair tasks per warp and step
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int crank = (int)cl.block_rank();
+  const JacobiDesc& d = descs[blockIdx.y];
+  const int q1 = min(dimv(d.q1, d.q1ref, di), q1cap), q2 = min(dimv(d.q2, d.q2ref, di), q2cap);
+  if (crank == 0 && threadIdx.x == 0 && flops && q1 > 0 && q2 > 0) {
+    double p = max(q1, q2), q = min(q1, q2);
+    atomicAdd(&flops[kKindSlot + 3], 4.0 * p * p * q + 8.0 * p * q * q + 9.0 * q * q * q);
+  }
+  extern __shared__ double jsm[];
+  const int nloc = (q2cap + C - 1) / C;
+  const int ldc = q1cap;
+  double* cols0 = jsm;                                   // [2][nloc][ldc], slot s = column crank + s*C
+  double* cn0 = cols0 + 2 * (size_t)nloc * ldc;          // [2][nloc] tracked squared norms
+  double* nall = cn0 + 2 * nloc;                         // squared norms of all columns (sweep start)
+  int* act = reinterpret_cast<int*>(nall + q2cap);       // active columns of the sweep
+  int* own = act + q2cap;                                // positions (in act) of own active columns
+  __shared__ int nact, nown;
+  double* M = d.M;
+  const size_t ldm = d.ldm;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sub = lane / LG, gl = lane % LG;
+  const double tol = fmin(1e-13, fmax(1e-15, 8.8e-16 * sqrt((double)q1)));   // as jacobi_cluster_kernel
+  const double tol2 = tol * tol;
+  const float tolf = (float)tol;
+  double thr = d.thr;
+  if (d.thr_ref) thr *= *d.thr_ref;
+  const double dth = 1e-2 * thr / sqrt((double)max(q2, 1));
+  const double dfl = dth * dth;
+  const long long dfl_bits = __double_as_longlong(dfl);
+  const size_t bufstride = (size_t)nloc * ldc;
+
+  if (crank == 0)
+    for (int i = threadIdx.x; i < kMaxSweeps; i += QT) d.rot[i] = 0;
+  for (int sl = 0; sl < nloc; ++sl) {
+    const int j = crank + sl * C;
+    if (j >= q2) break;
+    for (int i = threadIdx.x; i < q1; i += QT) cols0[(size_t)sl * ldc + i] = M[i + (size_t)j * ldm];
+  }
+  // every CTA of the cluster must be running before any distributed shared memory access
+  cl.sync();
+
+  const int nreg = (q1 + LG - 1) / LG;
+  const bool inreg = nreg <= kJacobiRegs;
+  int cur = 0;                                           // buffer holding the current columns
+  for (int sweep = 0; sweep <= kMaxSweeps; ++sweep) {
+    double* cols = cols0 + cur * bufstride;
+    double* cn = cn0 + cur * nloc;
+    // exact squared norms of own columns, broadcast into every CTA's copy
+    for (int sl = warp; sl < nloc; sl += QW) {
+      const int j = crank + sl * C;
+      if (j >= q2) break;
+      double v = 0.0;
+      for (int i = lane; i < q1; i += 32) {
+        const double x = cols[(size_t)sl * ldc + i];
+        v = fma(x, x, v);
+      }
+      v = warp_sum2(v);
+      if (lane < C) cl.map_shared_rank(nall, lane)[j] = v;
+      if (lane == 0) {
+        cn[sl] = v;
+        d.nrm[j] = v;
+      }
+    }
+    cl.sync();
+    if (sweep == kMaxSweeps || q2 < 2 || q1 == 0) break;
+    if (threadIdx.x == 0) {
+      int c = 0, o = 0;
+      for (int j = 0; j < q2; ++j)
+        if (nall[j] > dfl) {
+          if (j % C == crank) own[o++] = c;
+          act[c++] = j;
+        }
+      nact = c;
+      nown = o;
+    }
+    __syncthreads();
+    const int Ka = nact, No = nown;
+    if (Ka < 2) break;
+    const int P = Ka + (Ka & 1), m = P - 1;
+    int local = 0;
+    for (int r = 0; r < P - 1; ++r) {
+      const int rb = cur, wb = cur ^ 1;                  // read / write buffers of this round
+      for (int tb = warp * PPW; tb < No; tb += QW * PPW) {
+        const int t = tb + sub;
+        const bool task = t < No;
+        const int x = task ? own[t] : 0;
+        // partner of player x in round r of the circle schedule on P players
+        const int y = (x == m) ? r : (x == r ? m : ((2 * r - x) % m + m) % m);
+        const bool valid = task && y < Ka;
+        const int lo = min(x, y), hi = max(x, y);
+        const int a = valid ? act[lo] : 0, b = valid ? act[hi] : 0;
+        const bool mine_a = x == lo;                     // this task writes column a (else b)
+        const int me = task ? act[x] : 0;
+        const double* xa = cl.map_shared_rank(cols0, a % C) + rb * bufstride + (size_t)(a / C) * ldc;
+        const double* yb = cl.map_shared_rank(cols0, b % C) + rb * bufstride + (size_t)(b / C) * ldc;
+        const double al = valid ? cl.map_shared_rank(cn0, a % C)[rb * nloc + a / C] : 0.0;
+        const double be = valid ? cl.map_shared_rank(cn0, b % C)[rb * nloc + b / C] : 0.0;
+        double* dst = cols0 + wb * bufstride + (size_t)(me / C) * ldc;
+        const double* src = cols0 + rb * bufstride + (size_t)(me / C) * ldc;
+        double xr[kJacobiRegs], yr[kJacobiRegs];
+        double g0 = 0.0, g1 = 0.0;
+        if (inreg) {
+#pragma unroll
+          for (int u = 0; u < kJacobiRegs; ++u) {
+            if (u < nreg) {
+              const int i = gl + LG * u;
+              const bool in = valid && i < q1;
+              xr[u] = in ? xa[i] : 0.0;
+              yr[u] = in ? yb[i] : 0.0;
+              if (u & 1) g1 = fma(xr[u], yr[u], g1);
+              else g0 = fma(xr[u], yr[u], g0);
+            }
+          }
+        } else if (valid) {
+          for (int i = gl; i < q1; i += 2 * LG) {
+            g0 = fma(xa[i], yb[i], g0);
+            if (i + LG < q1) g1 = fma(xa[i + LG], yb[i + LG], g1);
+          }
+        }
+        double g = g0 + g1;
+#pragma unroll
+        for (int o = LG / 2; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+        double c = 1.0, sn = 0.0, tt = 0.0;
+        const bool doit = valid && __double_as_longlong(al) > dfl_bits && __double_as_longlong(be) > dfl_bits &&
+                          jacobi_rotation(al, be, g, tol2, tolf, c, sn, tt);
+        if (!doit) {
+          c = 1.0;
+          sn = 0.0;
+          tt = 0.0;
+        }
+        // own new column: x' = c x - s y (a), y' = s x + c y (b); the identity when not rotated
+        const double ca = mine_a ? c : sn, cb = mine_a ? -sn : c;
+        const double tg = tt * g;
+        const bool a_shrinks = tg > 0.0;
+        const bool exact = doit && (mine_a == a_shrinks) && (a_shrinks ? (tg > 0.5 * al) : (-tg > 0.5 * be));
+        const bool any_exact = __any_sync(0xffffffffu, exact);
+        double s0 = 0.0, s1 = 0.0;
+        if (inreg) {
+#pragma unroll
+          for (int u = 0; u < kJacobiRegs; ++u) {
+            if (u < nreg) {
+              const int i = gl + LG * u;
+              const double v = doit ? fma(ca, xr[u], cb * yr[u]) : 0.0;
+              if (task && i < q1) dst[i] = doit ? v : src[i];
+              if (any_exact) {
+                if (u & 1) s1 = fma(v, v, s1);
+                else s0 = fma(v, v, s0);
+              }
+            }
+          }
+        } else if (task) {
+          for (int i = gl; i < q1; i += LG) {
+            const double v = doit ? fma(ca, xa[i], cb * yb[i]) : src[i];
+            dst[i] = v;
+            s0 = fma(v, v, s0);
+          }
+        }
+        double ss = s0 + s1;
+        if (any_exact) {
+#pragma unroll
+          for (int o = LG / 2; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        }
+        if (task && gl == 0) {
+          const int sl = me / C;
+          const double nw = doit ? (mine_a ? fma(-tt, g, al) : fma(tt, g, be)) : cn0[rb * nloc + sl];
+          cn0[wb * nloc + sl] = exact ? ss : nw;
+          if (doit && mine_a) ++local;
+        }
+      }
+      cl.sync();
+      cur ^= 1;
+    }
+    if (local) atomicAdd(&d.rot[sweep], local);
+    // inactive (deflated) own columns: bring them into the current buffer before the norm pass
+    for (int sl = 0; sl < nloc; ++sl) {
+      const int j = crank + sl * C;
+      if (j >= q2) break;
+      if (!(nall[j] > dfl) && ((P - 1) & 1))
+        for (int i = threadIdx.x; i < q1; i += QT) cols0[cur * bufstride + (size_t)sl * ldc + i] =
+                                                      cols0[(cur ^ 1) * bufstride + (size_t)sl * ldc + i];
+    }
+    cl.sync();
+    if (*(volatile int*)&d.rot[sweep] == 0) sweep = kMaxSweeps - 1;   // converged: final norms next pass
+  }
+  // write the rotated columns back (the rank selection reads them from global memory)
+  for (int sl = 0; sl < nloc; ++sl) {
+    const int j = crank + sl * C;
+    if (j >= q2) break;
+    for (int i = threadIdx.x; i < q1; i += QT) M[i + (size_t)j * ldm] = cols0[cur * bufstride + (size_t)sl * ldc + i];
+  }
+  cl.sync();   // no CTA may exit while others still access its shared memory
+}
+
+// Lane-group width from the actual column length of this cluster's core (ranks are known only
+// on the device; every CTA of the cluster reads the same descriptor, so the choice is uniform).
+__global__ void __launch_bounds__(QT) jacobi_dsmem_kernel(const JacobiDesc* __restrict__ descs,
+                                                          const int* __restrict__ di, double* flops,
+                                                          int q1cap, int q2cap, int owner_form) {
+  const JacobiDesc& d = descs[blockIdx.y];
+  const int q1 = min(dimv(d.q1, d.q1ref, di), q1cap);
+  if (owner_form) {
+    if (q1 <= 8 * kJacobiRegs) jacobi_owner_impl<8>(descs, di, flops, q1cap, q2cap);
+    else if (q1 <= 16 * kJacobiRegs) jacobi_owner_impl<16>(descs, di, flops, q1cap, q2cap);
+    else jacobi_owner_impl<32>(descs, di, flops, q1cap, q2cap);
+  } else {
+    if (q1 <= 8 * kJacobiRegs) jacobi_dsmem_impl<8>(descs, di, flops, q1cap, q2cap);
+    else if (q1 <= 16 * kJacobiRegs) jacobi_dsmem_impl<16>(descs, di, flops, q1cap, q2cap);
+    else jacobi_dsmem_impl<32>(descs, di, flops, q1cap, q2cap);
+  }
+}
+
 size_t jacobi_dsmem_bytes(int q1cap, int q2cap, int cluster) {
   const size_t nloc = (q2cap + cluster - 1) / cluster;
   return nloc * (q1cap + 1) * sizeof(double) + (size_t)q2cap * sizeof(double) + (size_t)q2cap * sizeof(int) + 64;
 }
 
+size_t jacobi_owner_bytes(int q1cap, int q2cap, int cluster) {
+  const size_t nloc = (q2cap + cluster - 1) / cluster;
+  return 2 * nloc * (q1cap + 1) * sizeof(double) + (size_t)q2cap * sizeof(double) +
+         ((size_t)q2cap + nloc) * sizeof(int) + 64;
+}
+
 cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, const int* devints, double* flops,
                           int cluster, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  const int cluster_max = cluster;
   int q1cap = 0, q2cap = 0;
   for (int i = 0; i < n; ++i) {
     q1cap = max(q1cap, h[i].q1);
@@ -882,6 +1179,13 @@ cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, const int* 
   }
   q1cap = max(q1cap, 1);
   q2cap = max(q2cap, 1);
+  // Cluster size for this launch: enough CTAs that each has about two warps of pair groups per
+  // round (more CTAs only add barrier cost: a round is one dependent chain per pair), at most
+  // the context's size, and enough that the columns fit in shared memory.
+  const int ppw = q1cap <= 8 * kJacobiRegs ? 4 : (q1cap <= 16 * kJacobiRegs ? 2 : 1);   // from the caps
+  const int pairs = (q2cap + 1) / 2;
+  cluster = max(1, min(cluster, (pairs + 2 * ppw - 1) / (2 * ppw)));
+  while (cluster < cluster_max && jacobi_dsmem_bytes(q1cap, q2cap, cluster) > kJacobiSmemMax) ++cluster;
   const size_t smem = jacobi_dsmem_bytes(q1cap, q2cap, cluster);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cluster, n, 1);
@@ -894,9 +1198,14 @@ cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, const int* 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  const size_t smem2 = jacobi_owner_bytes(q1cap, q2cap, cluster);
+  if (smem2 <= kJacobiSmemMax && q2cap <= kJacobiMaxCols) {
+    cfg.dynamicSmemBytes = smem2;
+    return cudaLaunchKernelEx(&cfg, jacobi_dsmem_kernel, (const JacobiDesc*)d, devints, flops, q1cap, q2cap, 1);
+  }
   if (smem <= kJacobiSmemMax && q2cap <= kJacobiMaxCols) {
     cfg.dynamicSmemBytes = smem;
-    return cudaLaunchKernelEx(&cfg, jacobi_dsmem_kernel, (const JacobiDesc*)d, devints, flops, q1cap, q2cap);
+    return cudaLaunchKernelEx(&cfg, jacobi_dsmem_kernel, (const JacobiDesc*)d, devints, flops, q1cap, q2cap, 0);
   }
   return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel, (const JacobiDesc*)d, devints, flops);
 }

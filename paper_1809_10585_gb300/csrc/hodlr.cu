@@ -46,7 +46,7 @@ struct hodlr_ctx {
 };
 
 enum RecType { R_GEMM, R_REDUCE, R_CONCAT, R_GATHER, R_SCATTER, R_QR, R_JACOBI, R_SELECT, R_COPY,
-               R_FILL, R_IDENT, R_NORM, R_MEMSET_INT, R_TRSM, R_EVREC, R_EVWAIT };
+               R_FILL, R_IDENT, R_NORM, R_MEMSET_INT, R_TRSM, R_EVREC, R_EVWAIT, R_GAUSS };
 
 struct Rec {
   int type;
@@ -482,6 +482,90 @@ struct Planner {
     release(mk);
   }
 
+  // ------------------------------ HODLR approximation of a dense device matrix (Sec. 2.1.1)
+  // Leaves are copied.  Every off-diagonal block B (m x q) is sampled by a randomized range
+  // finder (Halko, Martinsson and Tropp, SIAM Review 2011, Alg. 4.1): Y = B Omega with
+  // p = min(kc + 16, m, q) Gaussian columns, Q = orth(Y) by Householder QR, Z = B^T Q, and
+  // T_eps(Q Z^T) gives the stored factors and the rank (device rank table).  The kept rank is at
+  // most kc (else HODLR_ERANK), so at least 16 columns of oversampling remain and the range error
+  // stays at the level of sigma_{k+1} (when p = q the sample spans B exactly).
+  void compress_dense(const double* A, int lda, double thr, unsigned long long seed) {
+    const int kc = M->kc;
+    std::vector<CopyDesc> cps;
+    for (int j = 0; j < M->nleaf; ++j) {
+      const int v = M->nleaf - 1 + j, lo = M->lo[v], w = size(v);
+      CopyDesc cp = {};
+      cp.src = A + lo + (size_t)lo * lda; cp.lds = lda;
+      cp.dst = M->D + (size_t)j * M->ldl * M->ldl; cp.ldd = M->ldl;
+      cp.rows = w; cp.rows_src = w; cp.rows_src_ref = -1; cp.cols = w; cp.colsref = -1; cp.alpha = 1.0;
+      cps.push_back(cp);
+    }
+    rec(R_COPY, (int)cps.size(), put(cps));
+    for (int l = 0; l < M->levels; ++l) {
+      size_t mk = mark();
+      std::vector<QRDesc> qds;
+      std::vector<GemmDesc> gY, gP2, gP3, gQ, gZ;
+      std::vector<Trunc> ts;
+      std::vector<Rec> pre;
+      for (int v = (1 << l) - 1; v < (2 << l) - 1; ++v) {
+        for (int which = 0; which < 2; ++which) {
+          const int rlo = M->lo[which == 0 ? 2 * v + 1 : 2 * v + 2];
+          const int clo = M->lo[which == 0 ? 2 * v + 2 : 2 * v + 1];
+          const int m = which == 0 ? m1(v) : m2(v);
+          const int q = which == 0 ? m2(v) : m1(v);
+          const int p = std::min(std::min(kc + 16, m), q);
+          const double* B = A + rlo + (size_t)clo * lda;
+          double* Om = alloc<double>((size_t)q * p);
+          double* Y = alloc<double>((size_t)m * p);
+          double* tau = alloc<double>(p);
+          double* T = alloc<double>((size_t)p * p);
+          double* G = alloc<double>((size_t)p * p);
+          double* Q = alloc<double>((size_t)m * p);
+          double* P2 = alloc<double>((size_t)p * p);
+          double* P3 = alloc<double>((size_t)p * p);
+          double* Z = alloc<double>((size_t)q * p);
+          const unsigned long long stream = seed * (unsigned long long)(2 * M->nn + 2) + 2 * v + which;
+          Rec g = {};
+          g.type = R_GAUSS; g.p0 = Om; g.cnt = (size_t)q * p;
+          g.i0 = (int)(unsigned)(stream & 0xffffffffull); g.i1 = (int)(unsigned)(stream >> 32);
+          pre.push_back(g);
+          Rec ri = {};
+          ri.type = R_IDENT; ri.p0 = Q; ri.i0 = m; ri.i1 = m; ri.i2 = p;
+          pre.push_back(ri);
+          gY.push_back(gd(B, lda, 0, 0, Om, q, 0, 0, Y, m, m, -1, p, -1, q, -1, 1.0, 0.0, kStepNone, -1));
+          QRDesc qd = {};
+          qd.A = Y; qd.lda = m; qd.h = m; qd.w = p; qd.href = -1; qd.wref = -1; qd.tau = tau; qd.T = T;
+          qd.ldt = p; qd.G = G; qd.ldg = p; qd.step = kStepNone; qd.fmode = 1;
+          qds.push_back(qd);
+          // Q = (I - Y T Y^T) [I; 0]
+          gP2.push_back(gd(Y, m, 1, kMaskUnitLower, Q, m, 0, 0, P2, p, p, -1, p, -1, p, -1, 1.0, 0.0, kStepNone, -1));
+          gP3.push_back(gd(T, p, 0, kMaskUpper, P2, p, 0, 0, P3, p, p, -1, p, -1, p, -1, 1.0, 0.0, kStepNone, -1));
+          gQ.push_back(gd(Y, m, 0, kMaskUnitLower, P3, p, 0, 0, Q, m, m, -1, p, -1, p, -1, -1.0, 1.0, kStepNone, -1));
+          gZ.push_back(gd(B, lda, 1, 0, Q, m, 0, 0, Z, q, q, -1, p, -1, m, -1, 1.0, 0.0, kStepNone, -1));
+          Trunc t;
+          t.nL = m; t.nR = q;
+          t.L.push_back(seg(Q, m, p, -1, 1.0));
+          t.R.push_back(seg(Z, q, p, -1, 1.0));
+          t.thr = thr; t.thr_ref = nullptr;
+          t.Uout = which == 0 ? M->U12[v] : M->U21[v]; t.ldu = m;
+          t.Vout = which == 0 ? M->V12[v] : M->V21[v]; t.ldv = q;
+          t.kout_ref = which == 0 ? r12(v) : r21(v);
+          t.step = kStepNone;
+          ts.push_back(t);
+        }
+      }
+      for (auto& r : pre) push(r);
+      gemm(gY);
+      rec(R_QR, (int)qds.size(), put(qds));
+      gemm(gP2);
+      gemm(gP3);
+      gemm(gQ);
+      gemm(gZ);
+      truncate(ts);
+      release(mk);
+    }
+  }
+
   // --------------------------------------------------------- left-orthogonal form (Sec. 2.1)
   void left_orth(int p) {
     size_t mk = mark();
@@ -752,7 +836,7 @@ static int rec_kind(int t) {
     case R_SELECT: return 4;
     case R_CONCAT: case R_GATHER: case R_SCATTER: case R_COPY: case R_IDENT: case R_FILL: return 5;
     case R_NORM: return 6;
-    case R_TRSM: return 7;
+    case R_TRSM: case R_GAUSS: return 7;
     default: return -1;
   }
 }
@@ -803,6 +887,9 @@ static int run_plan_on(hodlr_ctx* ctx, hodlr_mat* M, Plan& P, Profiler* prof, cu
       case R_SELECT: e = launch_select((const SelectDesc*)hb, r.n, (SelectDesc*)dp, M->devints, flops, s); break;
       case R_COPY: e = launch_copy((const CopyDesc*)hb, r.n, (CopyDesc*)dp, M->devints, s); break;
       case R_FILL: e = launch_fill(r.p0, r.cnt, r.v, s); break;
+      case R_GAUSS:
+        e = launch_gauss(r.p0, r.cnt, ((unsigned long long)(unsigned)r.i1 << 32) | (unsigned)r.i0, s);
+        break;
       case R_IDENT: e = launch_set_diag_identity(r.p0, r.i0, r.i1, r.i2, s); break;
       case R_NORM: e = launch_norm_scale(r.p0, r.i0, reinterpret_cast<double*>(r.ip), r.i1, s); break;
       case R_MEMSET_INT: e = cudaMemsetAsync(r.ip, 0, r.cnt, s); break;
@@ -1074,14 +1161,13 @@ void hodlr_free(hodlr_mat* M) {
   delete M;
 }
 
-int hodlr_build(hodlr_ctx* ctx, int n, int nleaf, const int* leaf_sizes, const double* const* leaves,
-                const double* const* U12, const double* const* V12, const int* r12,
-                const double* const* U21, const double* const* V21, const int* r21, int rank_cap,
-                hodlr_mat** out) {
+}  // extern "C"
+
+// Allocate a matrix of the given partition with all values and ranks zero.
+static int alloc_mat(hodlr_ctx* ctx, int n, int nleaf, const int* leaf_sizes, int rank_cap, hodlr_mat** out) {
   if (!ctx || !out || !leaf_sizes || n <= 0 || nleaf <= 0 || (nleaf & (nleaf - 1)) || rank_cap < 1 ||
       rank_cap > 256)
     return HODLR_EINVAL;
-  if (nleaf > 1 && (!r12 || !r21)) return HODLR_EINVAL;
   long sum = 0;
   int maxw = 0;
   for (int j = 0; j < nleaf; ++j) {
@@ -1157,8 +1243,23 @@ int hodlr_build(hodlr_ctx* ctx, int n, int nleaf, const int* leaf_sizes, const d
   cudaMemsetAsync(M->devints, 0, sizeof(int) * M->n_devints, ctx->s);
   cudaMemsetAsync(M->dscal, 0, sizeof(double) * 32, ctx->s);
   cudaMemsetAsync(M->dstatus, 0, sizeof(int) * 4, ctx->s);
+  *out = M;
+  return HODLR_OK;
+}
+
+extern "C" {
+
+int hodlr_build(hodlr_ctx* ctx, int n, int nleaf, const int* leaf_sizes, const double* const* leaves,
+                const double* const* U12, const double* const* V12, const int* r12,
+                const double* const* U21, const double* const* V21, const int* r21, int rank_cap,
+                hodlr_mat** out) {
+  if (nleaf > 1 && (!r12 || !r21)) return HODLR_EINVAL;
+  if (!leaves) return HODLR_EINVAL;
+  hodlr_mat* M = nullptr;
+  int rc = alloc_mat(ctx, n, nleaf, leaf_sizes, rank_cap, &M);
+  if (rc) return rc;
   std::vector<int> z12(std::max(1, M->nn), 0), z21(std::max(1, M->nn), 0);
-  int rc = upload_values(ctx, M, leaves, U12, V12, r12 ? r12 : z12.data(), U21, V21, r21 ? r21 : z21.data());
+  rc = upload_values(ctx, M, leaves, U12, V12, r12 ? r12 : z12.data(), U21, V21, r21 ? r21 : z21.data());
   if (rc != HODLR_OK) {
     hodlr_free(M);
     return rc;
@@ -1728,6 +1829,47 @@ int hodlr_truncate(hodlr_ctx* ctx, int nL, int nR, int K, const double* L, const
   if (M.arena2) cudaFree(M.arena2);
   M.devints = nullptr; M.dstatus = nullptr; M.dscal = nullptr; M.arena = nullptr; M.arena2 = nullptr;
   return rc;
+}
+
+
+int hodlr_build_dense(hodlr_ctx* ctx, int n, int nleaf, const int* leaf_sizes, const double* A_dev, int lda,
+                      double tol, int rank_cap, unsigned long long seed, hodlr_mat** out) {
+  if (!ctx || !out || !A_dev || lda < n || !(tol >= 0)) return HODLR_EINVAL;
+  hodlr_mat* M = nullptr;
+  int rc = alloc_mat(ctx, n, nleaf, leaf_sizes, rank_cap, &M);
+  if (rc) return rc;
+  rc = temp_plan(ctx, M, [&](Planner& pl) { pl.compress_dense(A_dev, lda, tol, seed); });
+  int st = 0;
+  if (!rc) {
+    if (cudaMemcpy(&st, M->dstatus, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = HODLR_ECUDA;
+    else if (st == HODLR_ERANK) rc = HODLR_ERANK;
+  }
+  if (rc) {
+    hodlr_free(M);
+    return rc;
+  }
+  *out = M;
+  return HODLR_OK;
+}
+
+int hodlr_stats(hodlr_ctx* ctx, const hodlr_mat* A, int* max_rank_Y, int* max_rank_T, int* max_rank_R,
+                size_t* bytes) {
+  if (!ctx || !A) return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  HQ_CUDA_OK(cudaStreamSynchronize(ctx->s));
+  std::vector<int> h(std::max(1, 3 * A->nn), 0);
+  if (A->nn) HQ_CUDA_OK(cudaMemcpy(h.data(), A->devints, sizeof(int) * 3 * A->nn, cudaMemcpyDeviceToHost));
+  int mr = 0, my = 0, mt = 0;
+  for (int v = 0; v < A->nn; ++v) {
+    mr = std::max(mr, h[v]);
+    my = std::max(my, h[A->nn + v]);
+    mt = std::max(mt, h[2 * A->nn + v]);
+  }
+  if (max_rank_R) *max_rank_R = mr;
+  if (max_rank_Y) *max_rank_Y = my;
+  if (max_rank_T) *max_rank_T = mt;
+  if (bytes) *bytes = A->store_doubles * sizeof(double) + sizeof(int) * 3 * A->nn;
+  return HODLR_OK;
 }
 
 }  // extern "C"

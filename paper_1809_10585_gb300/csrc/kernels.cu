@@ -298,16 +298,29 @@ __global__ void select_kernel(const SelectDesc* __restrict__ descs, int* di, dou
   extern __shared__ int sh[];
   int* order = sh;           // q2 entries: output slot of column j, or -1
   __shared__ int kcount;
-  if (threadIdx.x == 0) kcount = 0;
+  __shared__ unsigned long long nmax_bits;
+  if (threadIdx.x == 0) {
+    kcount = 0;
+    nmax_bits = 0ull;
+  }
   __syncthreads();
+  // largest squared column norm (non-negative doubles order like their bit patterns)
+  for (int j = threadIdx.x; j < q2; j += blockDim.x)
+    atomicMax(&nmax_bits, (unsigned long long)__double_as_longlong(fmax(d.nrm[j], 0.0)));
+  __syncthreads();
+  // Columns below 4.4e-16 sqrt(q1) sigma_1 are numerically zero: their directions are rounding
+  // noise (a rank-deficient core drives them even to denormal size), so they are dropped even
+  // when thr is smaller; this changes the block by at most that much per column.
+  const double floor_ = 4.4e-16 * sqrt((double)max(q1, 1)) * sqrt(__longlong_as_double((long long)nmax_bits));
+  const double keep = fmax(thr, floor_);
   for (int j = threadIdx.x; j < q2; j += blockDim.x) {
     double nj = d.nrm[j];
     int slot = -1;
-    if (sqrt(nj) > thr) {
+    if (sqrt(nj) > keep) {
       int rank = 0;
       for (int l = 0; l < q2; ++l) {
         double nl = d.nrm[l];
-        if (sqrt(nl) > thr && (nl > nj || (nl == nj && l < j))) ++rank;
+        if (sqrt(nl) > keep && (nl > nj || (nl == nj && l < j))) ++rank;
       }
       slot = rank;
       atomicAdd(&kcount, 1);
@@ -389,6 +402,32 @@ cudaError_t launch_fill(double* p, size_t n, double v, cudaStream_t s) {
   size_t gb = (n + 255) / 256;
   int g = (int)(gb < 1024 ? gb : 1024);
   fill_kernel<<<g, 256, 0, s>>>(p, n, v);
+  return cudaGetLastError();
+}
+
+// Standard normal samples for a randomized range finder.  Element i of stream `seed` hashes the
+// counter seed * 2^32 + i with SplitMix64 (Steele, Lea and Flood, OOPSLA 2014); two 24-bit
+// uniforms of the hash give one normal by the Box-Muller transform, evaluated in FP32 (a sketch
+// needs independent Gaussian-like entries, not FP64 accuracy).
+__device__ inline unsigned long long splitmix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__global__ void gauss_kernel(double* p, size_t n, unsigned long long seed) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const unsigned long long z = splitmix64((seed << 32) + i);
+    const float u1 = ((float)(z >> 40) + 1.0f) * 0x1p-24f;              // (0, 1]
+    const float u2 = (float)((z >> 16) & 0xFFFFFFull) * 0x1p-24f;        // [0, 1)
+    p[i] = (double)(sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2));
+  }
+}
+cudaError_t launch_gauss(double* p, size_t n, unsigned long long seed, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  size_t gb = (n + 255) / 256;
+  int g = (int)(gb < 2048 ? gb : 2048);
+  gauss_kernel<<<g, 256, 0, s>>>(p, n, seed);
   return cudaGetLastError();
 }
 

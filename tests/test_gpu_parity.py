@@ -300,3 +300,28 @@ def test_truncate_without_threshold_keeps_an_orthonormal_basis(nL, nR, K):
     M = L @ Rt.T
     np.testing.assert_allclose(Lg @ Rg.T, M, atol=1e-12 * np.abs(M).max())
     np.testing.assert_allclose(Lg.T @ Lg, np.eye(k), atol=1e-12)
+
+
+@pytest.mark.parametrize("nL,nR,K", [(300, 200, 27), (128, 512, 40), (1024, 1024, 60)])
+def test_truncate_is_repeatable_and_accurate(nL, nR, K):
+    """Repeated runs of T_eps on the same input are bit-identical (the cluster kernels have no
+    timing-dependent reads) and accurate; two QR descriptors of different heights share one
+    launch here, the case where a missing barrier once showed up."""
+    rng = np.random.default_rng(nL + nR + K)
+    L = rng.standard_normal((nL, K)) * (10.0 ** -rng.uniform(0, 8, K))[None, :]
+    Rt = rng.standard_normal((nR, K))
+    from paper_1809_10585_gb300 import binding as B
+    outs = []
+    for _ in range(3):
+        tl, pl, _ = U.dev(L)
+        tr, pr, _ = U.dev(Rt)
+        to, po, _ = U.empty(nL, 128)
+        tq, pq, _ = U.empty(nR, 128)
+        rc, k = B.truncate(U.ctx(), nL, nR, K, pl, pr, 1e-12, 128, po, pq)
+        assert rc == 0
+        outs.append((k, U.host(to, nL, k), U.host(tq, nR, k)))
+    for k, Lg, Rg in outs[1:]:
+        assert k == outs[0][0] and np.array_equal(Lg, outs[0][1]) and np.array_equal(Rg, outs[0][2])
+    k, Lg, Rg = outs[0]
+    M = L @ Rt.T
+    assert np.linalg.norm(M - Lg @ Rg.T, 2) <= 1e-12 * 1.01 + 1e-13 * np.linalg.norm(M, 2)

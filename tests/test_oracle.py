@@ -346,3 +346,50 @@ def test_planted_missing_transpose_is_caught(monkeypatch):
     res = O.hqr(H, 0.0)
     V, T, R = dgeqrt_full(Ad)
     assert not np.allclose(res.R_dense(), R, atol=1e-8)
+
+
+def test_truncate_falls_back_to_dgesvd_when_dgesdd_fails(monkeypatch):
+    """Sec. 2.1.1: the truncation is defined by the SVD, whichever LAPACK driver computes it."""
+    rng = np.random.default_rng(11)
+    L = rng.standard_normal((60, 14)) * (10.0 ** -np.arange(14))[None, :]
+    Rt = rng.standard_normal((50, 14))
+    ref_L, ref_R = O.truncate(L, Rt, 1e-9)
+
+    def failing_svd(*a, **k):
+        raise np.linalg.LinAlgError("SVD did not converge")
+    monkeypatch.setattr(np.linalg, "svd", failing_svd)
+    got_L, got_R = O.truncate(L, Rt, 1e-9)
+    assert got_L.shape == ref_L.shape
+    s = scipy.linalg.svd(L @ Rt.T, compute_uv=False, lapack_driver="gesvd")
+    assert got_L.shape[1] == int(np.sum(s > 1e-9))
+    np.testing.assert_allclose(got_L @ got_R.T, ref_L @ ref_R.T, atol=1e-12)
+
+
+def test_compress_recovers_exact_hodlr_and_bounds_every_block():
+    """Sec. 2.1.1 construction: an exactly rank-k HODLR matrix is recovered with rank k in every
+    block; on a matrix of full-rank blocks each block keeps #{sigma > thr} terms and its error in
+    the 2-norm is below thr."""
+    inp = W.random_hodlr(300, 40, 5, seed=8)
+    A = W.to_dense(inp)
+    H = O.compress(A, inp.leaf_sizes, 1e-10 * np.linalg.norm(A, 2))
+    assert O.max_offdiag_rank(H) == 5
+    np.testing.assert_allclose(O.to_dense(H), A, atol=1e-12 * np.linalg.norm(A, 2))
+    # graded full-rank blocks: entries decay away from the diagonal
+    rng = np.random.default_rng(9)
+    n = 256
+    i = np.arange(n)
+    B = rng.standard_normal((n, n)) * np.exp(-np.abs(i[:, None] - i[None, :]) / 6.0)
+    sizes = W.balanced_leaf_sizes(n, 32)
+    thr = 1e-6
+    H = O.compress(B, sizes, thr)
+    D = O.to_dense(H)
+    ranges = W.node_ranges(sizes)
+    for v in range(len(sizes) - 1):
+        (lo1, hi1), (lo2, hi2) = ranges[2 * v + 1], ranges[2 * v + 2]
+        for (r0, r1, c0, c1) in ((lo1, hi1, lo2, hi2), (lo2, hi2, lo1, hi1)):
+            blk = B[r0:r1, c0:c1]
+            err = np.linalg.norm(blk - D[r0:r1, c0:c1], 2)
+            s = np.linalg.svd(blk, compute_uv=False)
+            k = int(np.sum(s > thr))
+            assert err <= thr * (1 + 1e-9) and (k == len(s) or abs(err - s[k]) <= 1e-9 * s[0])
+    np.testing.assert_array_equal(np.diag(D), np.diag(B))

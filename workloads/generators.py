@@ -207,6 +207,114 @@ def dense_to_hodlr_input(A, nmin, eps, leaf_sizes=None, name="") -> HodlrInput:
     return HodlrInput(n, sizes, leaves, U12, V12, U21, V21, name=name)
 
 
+def kernel_hodlr(n, nmin, eps=1e-12, seed=0, shift=None, samples=64, device="cpu", name="") -> HodlrInput:
+    """Kernel-generated nonsymmetric workload: A_ij = 1/(x_i - y_j) with the points of
+    ``kernel_points``, ``shift`` (default n) added to the diagonal, every off-diagonal block
+    replaced by its singular triplets with sigma > eps * sigma_1(block).
+
+    Blocks are never held whole: each is sampled by a randomized range finder (Halko, Martinsson
+    and Tropp, SIAM Review 2011, Alg. 4.1) from row panels generated on the fly, and the SVD of
+    the projected block gives the truncation; the sample count doubles until the smallest
+    captured singular value falls below eps * sigma_1.  The arithmetic runs in torch float64 on
+    ``device`` (input preparation only; the QR method never calls this)."""
+    import torch
+    dev = torch.device(device)
+    x_np, y_np = kernel_points(n, seed)
+    x = torch.from_numpy(x_np).to(dev)
+    y = torch.from_numpy(y_np).to(dev)
+    shift = float(n) if shift is None else float(shift)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1000003 * seed + 7)
+    sizes = balanced_leaf_sizes(n, nmin)
+    ranges = node_ranges(sizes)
+    nleaf = len(sizes)
+    leaves = []
+    for j in range(nleaf):
+        lo, hi = ranges[nleaf - 1 + j]
+        D = 1.0 / (x[lo:hi, None] - y[None, lo:hi])
+        D += shift * torch.eye(hi - lo, dtype=torch.float64, device=dev)
+        leaves.append(np.asfortranarray(D.cpu().numpy()))
+
+    def panel_rows(m2):
+        return max(1, min(1 << 14, (1 << 25) // max(m2, 1)))
+
+    def compress(rlo, rhi, clo, chi):
+        m1, m2 = rhi - rlo, chi - clo
+        xs, ys = x[rlo:rhi], y[clo:chi]
+        p = min(samples, m1, m2)
+        while True:
+            Om = torch.randn(m2, p, dtype=torch.float64, device=dev, generator=gen)
+            Y = torch.empty(m1, p, dtype=torch.float64, device=dev)
+            step = panel_rows(m2)
+            for a in range(0, m1, step):
+                Y[a:a + step] = (1.0 / (xs[a:a + step, None] - ys[None, :])) @ Om
+            Q, _ = torch.linalg.qr(Y)
+            Bt = torch.zeros(p, m2, dtype=torch.float64, device=dev)      # Q^T B
+            for a in range(0, m1, step):
+                Bt += Q[a:a + step].T @ (1.0 / (xs[a:a + step, None] - ys[None, :]))
+            Ub, sv, Vh = torch.linalg.svd(Bt, full_matrices=False)
+            if sv[-1] <= eps * sv[0] or p >= min(m1, m2):
+                break
+            p = min(2 * p, m1, m2)
+        k = int((sv > eps * sv[0]).sum().item())
+        U = (Q @ Ub[:, :k]).cpu().numpy()
+        V = (Vh[:k].T * sv[:k][None, :]).cpu().numpy()
+        return np.asfortranarray(U), np.asfortranarray(V)
+
+    U12, V12, U21, V21 = [], [], [], []
+    for v in range(nleaf - 1):
+        lo1, hi1 = ranges[2 * v + 1]
+        lo2, hi2 = ranges[2 * v + 2]
+        u, w = compress(lo1, hi1, lo2, hi2)
+        U12.append(u); V12.append(w)
+        u, w = compress(lo2, hi2, lo1, hi1)
+        U21.append(u); V21.append(w)
+    return HodlrInput(n, sizes, leaves, U12, V12, U21, V21, name=name or f"kernel_n{n}_nmin{nmin}")
+
+
+def banded_hodlr(n, b=8, nmin=256, seed=0, name="") -> HodlrInput:
+    """Symmetric banded matrix: entries N(0,1) for 0 < |i - j| <= b (mirrored), N(0,1) + 2b on
+    the diagonal.  An off-diagonal block of the HODLR partition is nonzero only in the b x b
+    corner next to the diagonal, so it is stored exactly with rank b: a selection of b rows
+    times those rows of the block."""
+    if b < 0 or nmin <= b:
+        raise ValueError("need 0 <= b < nmin")
+    rng = np.random.default_rng(seed)
+    diag = rng.standard_normal(n) + 2.0 * b
+    off = rng.standard_normal((b, n))            # off[k-1, i] = A[i, i+k] = A[i+k, i]
+
+    def entry_block(r0, r1, c0, c1):
+        B = np.zeros((r1 - r0, c1 - c0))
+        for i in range(r0, r1):
+            for j in range(max(c0, i - b), min(c1, i + b + 1)):
+                if i == j:
+                    B[i - r0, j - c0] = diag[i]
+                else:
+                    lo = min(i, j)
+                    B[i - r0, j - c0] = off[abs(i - j) - 1, lo]
+        return B
+
+    sizes = balanced_leaf_sizes(n, nmin)
+    ranges = node_ranges(sizes)
+    nleaf = len(sizes)
+    leaves = []
+    for j in range(nleaf):
+        lo, hi = ranges[nleaf - 1 + j]
+        leaves.append(np.asfortranarray(entry_block(lo, hi, lo, hi)))
+    U12, V12, U21, V21 = [], [], [], []
+    for v in range(nleaf - 1):
+        lo1, hi1 = ranges[2 * v + 1]
+        lo2, hi2 = ranges[2 * v + 2]
+        m1, m2 = hi1 - lo1, hi2 - lo2
+        # A12: rows hi1-b..hi1-1 of the first child against the columns of the second
+        S = np.zeros((m1, b)); S[m1 - b:, :] = np.eye(b)
+        C = entry_block(hi1 - b, hi1, lo2, hi2)                    # b x m2
+        U12.append(np.asfortranarray(S)); V12.append(np.asfortranarray(C.T))
+        # A21 = A12^T
+        U21.append(np.asfortranarray(C.T.copy())); V21.append(np.asfortranarray(S.copy()))
+    return HodlrInput(n, sizes, leaves, U12, V12, U21, V21, name=name or f"banded_n{n}_b{b}")
+
+
 def batched_family(count=256, seed0=0, nmin_choices=(128, 256), n_lo=2048, n_hi=32768):
     """Cross-matrix batch: n log-uniform in [n_lo, n_hi] rounded to nmin * 2^l, nmin from
     nmin_choices, ranks uniform in [5, 20], every second matrix column-scaled to kappa ~ 1e10."""
