@@ -932,6 +932,17 @@ __device__ __forceinline__ void jacobi_dsmem_impl(const JacobiDesc* __restrict__
   cl.sync();   // no CTA may exit while others still access its shared memory
 }
 
+// Cluster barrier and distributed-shared-memory mapping, or their one-CTA forms.
+template <bool SOLO>
+__device__ __forceinline__ void csync(cg::cluster_group& cl) {
+  if (SOLO) __syncthreads();
+  else cl.sync();
+}
+template <bool SOLO, class T>
+__device__ __forceinline__ T* rmt(cg::cluster_group& cl, T* p, int rank) {
+  return SOLO ? p : cl.map_shared_rank(p, rank);
+}
+
 // One-sided Jacobi, owner-computes form.  Column j lives in the shared memory of CTA j % C, in
 // two buffers: round r reads buffer r & 1 and writes buffer (r + 1) & 1.  For every pair (a, b)
 // of a round, the CTA owning a and the CTA owning b both form the same rotation from the same
@@ -941,13 +952,13 @@ __device__ __forceinline__ void jacobi_dsmem_impl(const JacobiDesc* __restrict__
 // round's reads and the round's reads before the buffer is written again.  A column without a
 // partner in a round is copied to the other buffer.  Lane groups, thresholds, deflation and the
 // exact-norm rule as in jacobi_dsmem_impl.
-template <int LG>
+template <int LG, bool SOLO>
 __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__ descs, const int* __restrict__ di,
                                                   double* flops, int q1cap, int q2cap) {
   constexpr int PPW = 32 / LG;                            // pair tasks per warp and step
   cg::cluster_group cl = cg::this_cluster();
-  const int C = (int)cl.num_blocks();
-  const int crank = (int)cl.block_rank();
+  const int C = SOLO ? 1 : (int)cl.num_blocks();
+  const int crank = SOLO ? 0 : (int)cl.block_rank();
   const JacobiDesc& d = descs[blockIdx.y];
   const int q1 = min(dimv(d.q1, d.q1ref, di), q1cap), q2 = min(dimv(d.q2, d.q2ref, di), q2cap);
   if (crank == 0 && threadIdx.x == 0 && flops && q1 > 0 && q2 > 0) {
@@ -955,13 +966,15 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
     atomicAdd(&flops[kKindSlot + 3], 4.0 * p * p * q + 8.0 * p * q * q + 9.0 * q * q * q);
   }
   extern __shared__ double jsm[];
-  const int nloc = (q2cap + C - 1) / C;
-  const int ldc = q1cap;
+  // SOLO: the whole core in this CTA's shared memory, laid out by its actual size
+  const int nloc = SOLO ? q2 : (q2cap + C - 1) / C;
+  const int ldc = SOLO ? max(q1, 1) : q1cap;
+  const int q2n = SOLO ? q2 : q2cap;
   double* cols0 = jsm;                                   // [2][nloc][ldc], slot s = column crank + s*C
   double* cn0 = cols0 + 2 * (size_t)nloc * ldc;          // [2][nloc] tracked squared norms
   double* nall = cn0 + 2 * nloc;                         // squared norms of all columns (sweep start)
-  int* act = reinterpret_cast<int*>(nall + q2cap);       // active columns of the sweep
-  int* own = act + q2cap;                                // positions (in act) of own active columns
+  int* act = reinterpret_cast<int*>(nall + q2n);         // active columns of the sweep
+  int* own = act + q2n;                                // positions (in act) of own active columns
   __shared__ int nact, nown;
   double* M = d.M;
   const size_t ldm = d.ldm;
@@ -985,7 +998,7 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
     for (int i = threadIdx.x; i < q1; i += QT) cols0[(size_t)sl * ldc + i] = M[i + (size_t)j * ldm];
   }
   // every CTA of the cluster must be running before any distributed shared memory access
-  cl.sync();
+  csync<SOLO>(cl);
 
   const int nreg = (q1 + LG - 1) / LG;
   const bool inreg = nreg <= kJacobiRegs;
@@ -1003,20 +1016,23 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
         v = fma(x, x, v);
       }
       v = warp_sum2(v);
-      if (lane < C) cl.map_shared_rank(nall, lane)[j] = v;
+      if (lane < C) rmt<SOLO>(cl, nall, lane)[j] = v;
       if (lane == 0) {
         cn[sl] = v;
         d.nrm[j] = v;
       }
     }
-    cl.sync();
+    csync<SOLO>(cl);
     if (sweep == kMaxSweeps || q2 < 2 || q1 == 0) break;
     if (threadIdx.x == 0) {
+      // act[x] packs (slot << 5) | owner CTA of the x-th active column, so the round loop needs
+      // no integer division by the cluster size
       int c = 0, o = 0;
       for (int j = 0; j < q2; ++j)
         if (nall[j] > dfl) {
-          if (j % C == crank) own[o++] = c;
-          act[c++] = j;
+          const int ow = j % C;
+          if (ow == crank) own[o++] = c;
+          act[c++] = ((j / C) << 5) | ow;
         }
       nact = c;
       nown = o;
@@ -1032,19 +1048,23 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
         const int t = tb + sub;
         const bool task = t < No;
         const int x = task ? own[t] : 0;
-        // partner of player x in round r of the circle schedule on P players
-        const int y = (x == m) ? r : (x == r ? m : ((2 * r - x) % m + m) % m);
+        // partner of player x in round r of the circle schedule on P players: 2r - x mod m
+        int y = 2 * r - x;
+        y += (y < 0) ? m : 0;
+        y -= (y >= m) ? m : 0;
+        y = (x == m) ? r : (x == r ? m : y);
         const bool valid = task && y < Ka;
         const int lo = min(x, y), hi = max(x, y);
-        const int a = valid ? act[lo] : 0, b = valid ? act[hi] : 0;
+        const int pa = valid ? act[lo] : 0, pb = valid ? act[hi] : 0;
+        const int ao = pa & 31, as = pa >> 5, bo = pb & 31, bs = pb >> 5;
         const bool mine_a = x == lo;                     // this task writes column a (else b)
-        const int me = task ? act[x] : 0;
-        const double* xa = cl.map_shared_rank(cols0, a % C) + rb * bufstride + (size_t)(a / C) * ldc;
-        const double* yb = cl.map_shared_rank(cols0, b % C) + rb * bufstride + (size_t)(b / C) * ldc;
-        const double al = valid ? cl.map_shared_rank(cn0, a % C)[rb * nloc + a / C] : 0.0;
-        const double be = valid ? cl.map_shared_rank(cn0, b % C)[rb * nloc + b / C] : 0.0;
-        double* dst = cols0 + wb * bufstride + (size_t)(me / C) * ldc;
-        const double* src = cols0 + rb * bufstride + (size_t)(me / C) * ldc;
+        const int ms = task ? (act[x] >> 5) : 0;         // own slot
+        const double* xa = rmt<SOLO>(cl, cols0, ao) + rb * bufstride + (size_t)as * ldc;
+        const double* yb = rmt<SOLO>(cl, cols0, bo) + rb * bufstride + (size_t)bs * ldc;
+        const double al = valid ? rmt<SOLO>(cl, cn0, ao)[rb * nloc + as] : 0.0;
+        const double be = valid ? rmt<SOLO>(cl, cn0, bo)[rb * nloc + bs] : 0.0;
+        double* dst = cols0 + wb * bufstride + (size_t)ms * ldc;
+        const double* src = cols0 + rb * bufstride + (size_t)ms * ldc;
         double xr[kJacobiRegs], yr[kJacobiRegs];
         double g0 = 0.0, g1 = 0.0;
         if (inreg) {
@@ -1109,13 +1129,13 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
           for (int o = LG / 2; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
         }
         if (task && gl == 0) {
-          const int sl = me / C;
+          const int sl = ms;
           const double nw = doit ? (mine_a ? fma(-tt, g, al) : fma(tt, g, be)) : cn0[rb * nloc + sl];
           cn0[wb * nloc + sl] = exact ? ss : nw;
           if (doit && mine_a) ++local;
         }
       }
-      cl.sync();
+      csync<SOLO>(cl);
       cur ^= 1;
     }
     if (local) atomicAdd(&d.rot[sweep], local);
@@ -1127,7 +1147,7 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
         for (int i = threadIdx.x; i < q1; i += QT) cols0[cur * bufstride + (size_t)sl * ldc + i] =
                                                       cols0[(cur ^ 1) * bufstride + (size_t)sl * ldc + i];
     }
-    cl.sync();
+    csync<SOLO>(cl);
     if (*(volatile int*)&d.rot[sweep] == 0) sweep = kMaxSweeps - 1;   // converged: final norms next pass
   }
   // write the rotated columns back (the rank selection reads them from global memory)
@@ -1136,8 +1156,16 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
     if (j >= q2) break;
     for (int i = threadIdx.x; i < q1; i += QT) M[i + (size_t)j * ldm] = cols0[cur * bufstride + (size_t)sl * ldc + i];
   }
-  cl.sync();   // no CTA may exit while others still access its shared memory
+  csync<SOLO>(cl);   // no CTA may exit while others still access its shared memory
 }
+
+// Shared memory of the owner-computes Jacobi for a core of at most q1cap x q2cap on `cluster` CTAs.
+__host__ __device__ inline size_t jacobi_owner_bytes(int q1cap, int q2cap, int cluster) {
+  const size_t nloc = (q2cap + cluster - 1) / cluster;
+  return 2 * nloc * (q1cap + 1) * sizeof(double) + (size_t)q2cap * sizeof(double) +
+         ((size_t)q2cap + nloc) * sizeof(int) + 64;
+}
+constexpr int kJacobiSoloCols = 32;   // cores up to this many columns run on one CTA
 
 // Lane-group width from the actual column length of this cluster's core (ranks are known only
 // on the device; every CTA of the cluster reads the same descriptor, so the choice is uniform).
@@ -1147,9 +1175,20 @@ __global__ void __launch_bounds__(QT) jacobi_dsmem_kernel(const JacobiDesc* __re
   const JacobiDesc& d = descs[blockIdx.y];
   const int q1 = min(dimv(d.q1, d.q1ref, di), q1cap);
   if (owner_form) {
-    if (q1 <= 8 * kJacobiRegs) jacobi_owner_impl<8>(descs, di, flops, q1cap, q2cap);
-    else if (q1 <= 16 * kJacobiRegs) jacobi_owner_impl<16>(descs, di, flops, q1cap, q2cap);
-    else jacobi_owner_impl<32>(descs, di, flops, q1cap, q2cap);
+    // Small cores run on one CTA (shared-memory barriers, no remote loads) when their actual
+    // size fits in the shared memory this launch reserved per CTA; the other CTAs leave.
+    const int q2 = min(dimv(d.q2, d.q2ref, di), q2cap);
+    const int C = (int)cg::this_cluster().num_blocks();
+    if (q2 <= kJacobiSoloCols && jacobi_owner_bytes(q1, q2, 1) <= jacobi_owner_bytes(q1cap, q2cap, C)) {
+      if (cg::this_cluster().block_rank() != 0) return;
+      if (q1 <= 8 * kJacobiRegs) jacobi_owner_impl<8, true>(descs, di, flops, q1cap, q2cap);
+      else if (q1 <= 16 * kJacobiRegs) jacobi_owner_impl<16, true>(descs, di, flops, q1cap, q2cap);
+      else jacobi_owner_impl<32, true>(descs, di, flops, q1cap, q2cap);
+      return;
+    }
+    if (q1 <= 8 * kJacobiRegs) jacobi_owner_impl<8, false>(descs, di, flops, q1cap, q2cap);
+    else if (q1 <= 16 * kJacobiRegs) jacobi_owner_impl<16, false>(descs, di, flops, q1cap, q2cap);
+    else jacobi_owner_impl<32, false>(descs, di, flops, q1cap, q2cap);
   } else {
     if (q1 <= 8 * kJacobiRegs) jacobi_dsmem_impl<8>(descs, di, flops, q1cap, q2cap);
     else if (q1 <= 16 * kJacobiRegs) jacobi_dsmem_impl<16>(descs, di, flops, q1cap, q2cap);
@@ -1162,11 +1201,7 @@ size_t jacobi_dsmem_bytes(int q1cap, int q2cap, int cluster) {
   return nloc * (q1cap + 1) * sizeof(double) + (size_t)q2cap * sizeof(double) + (size_t)q2cap * sizeof(int) + 64;
 }
 
-size_t jacobi_owner_bytes(int q1cap, int q2cap, int cluster) {
-  const size_t nloc = (q2cap + cluster - 1) / cluster;
-  return 2 * nloc * (q1cap + 1) * sizeof(double) + (size_t)q2cap * sizeof(double) +
-         ((size_t)q2cap + nloc) * sizeof(int) + 64;
-}
+
 
 cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, const int* devints, double* flops,
                           int cluster, cudaStream_t s) {
