@@ -409,7 +409,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batch", type=int, default=32,
+    ap.add_argument("--batch", type=int, default=64,
                     help="matrices of the workload factored concurrently per step (cross-matrix batching)")
     ap.add_argument("--no-served", action="store_true",
                     help="skip the served request stream (p50/p99 latency)")

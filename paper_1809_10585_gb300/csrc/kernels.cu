@@ -71,7 +71,15 @@ __global__ void __launch_bounds__(GT) gemm_kernel(const GemmDesc* __restrict__ d
 
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  // Thread layout by the actual width of this tile (ranks are known only on the device, and
+  // most products here multiply by a block of at most 8 columns): 16 x 16 threads with 2 x 2
+  // outputs each, 16 columns x 16 row pairs with 2 x 1, or 8 columns x 32 rows with 1 x 1, so
+  // that the FP64 pipe does not spend its issue slots on padding columns.
+  const int wcols = n - col0;
+  const int mode = wcols <= 8 ? 2 : (wcols <= 16 ? 1 : 0);
+  const int tx = mode == 0 ? threadIdx.x % 16 : (mode == 1 ? threadIdx.x % 16 : threadIdx.x % 8);
+  const int ty = mode == 0 ? threadIdx.x / 16 : (mode == 1 ? threadIdx.x / 16 : threadIdx.x / 8);
+  const int bcols = mode == 0 ? BN : (mode == 1 ? 16 : 8);
   double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
   for (int kk = k0; kk < k1; kk += BK) {
     for (int e = threadIdx.x; e < BM * BK; e += GT) {
@@ -83,7 +91,7 @@ __global__ void __launch_bounds__(GT) gemm_kernel(const GemmDesc* __restrict__ d
       }
       As[l][i] = v;
     }
-    for (int e = threadIdx.x; e < BN * BK; e += GT) {
+    for (int e = threadIdx.x; e < bcols * BK; e += GT) {
       int l = e % BK, j = e / BK;
       int gl = kk + l, gj = col0 + j;
       double v = 0.0;
@@ -93,17 +101,37 @@ __global__ void __launch_bounds__(GT) gemm_kernel(const GemmDesc* __restrict__ d
       Bs[l][j] = v;
     }
     __syncthreads();
+    if (mode == 0) {
 #pragma unroll
-    for (int l = 0; l < BK; ++l) {
-      double a0 = As[l][ty], a1 = As[l][ty + 16];
-      double b0 = Bs[l][tx], b1 = Bs[l][tx + 16];
-      acc[0][0] = fma(a0, b0, acc[0][0]);
-      acc[0][1] = fma(a0, b1, acc[0][1]);
-      acc[1][0] = fma(a1, b0, acc[1][0]);
-      acc[1][1] = fma(a1, b1, acc[1][1]);
+      for (int l = 0; l < BK; ++l) {
+        double a0 = As[l][ty], a1 = As[l][ty + 16];
+        double b0 = Bs[l][tx], b1 = Bs[l][tx + 16];
+        acc[0][0] = fma(a0, b0, acc[0][0]);
+        acc[0][1] = fma(a0, b1, acc[0][1]);
+        acc[1][0] = fma(a1, b0, acc[1][0]);
+        acc[1][1] = fma(a1, b1, acc[1][1]);
+      }
+    } else if (mode == 1) {
+#pragma unroll
+      for (int l = 0; l < BK; ++l) {
+        const double b0 = Bs[l][tx];
+        acc[0][0] = fma(As[l][ty], b0, acc[0][0]);
+        acc[1][0] = fma(As[l][ty + 16], b0, acc[1][0]);
+      }
+    } else {
+#pragma unroll
+      for (int l = 0; l < BK; l += 2) {                 // two chains
+        acc[0][0] = fma(As[l][ty], Bs[l][tx], acc[0][0]);
+        acc[1][1] = fma(As[l + 1][ty], Bs[l + 1][tx], acc[1][1]);
+      }
     }
     __syncthreads();
   }
+  if (mode == 2) {
+    acc[0][0] += acc[1][1];
+    acc[1][1] = 0.0;
+  }
+  const int na = mode == 2 ? 1 : 2, nb = mode == 0 ? 2 : 1;
   double alpha = d.alpha;
   if (d.alpha_ref) alpha *= *d.alpha_ref;
 #pragma unroll
@@ -111,7 +139,7 @@ __global__ void __launch_bounds__(GT) gemm_kernel(const GemmDesc* __restrict__ d
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
       int gi = row0 + ty + 16 * a, gj = col0 + tx + 16 * b;
-      if (gi < m && gj < n) {
+      if (a < na && b < nb && gi < m && gj < n) {
         if (to_part) {
           d.part[(size_t)split * d.m * d.n + gi + (size_t)gj * d.m] = acc[a][b];
         } else {
@@ -144,7 +172,7 @@ __global__ void __launch_bounds__(GT) gemm_kernel(const GemmDesc* __restrict__ d
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
       int gi = row0 + ty + 16 * a, gj = col0 + tx + 16 * b;
-      if (gi < m && gj < n) {
+      if (a < na && b < nb && gi < m && gj < n) {
         double sacc = 0.0;
         for (int sp = 0; sp < nsp; ++sp) sacc += __ldcg(&d.part[(size_t)sp * d.m * d.n + gi + (size_t)gj * d.m]);
         double* c = d.C + gi + (size_t)gj * d.ldc;
