@@ -235,7 +235,7 @@ def gpu_arm(args):
     cmax = ctx.cluster
     ccl = args.cluster if args.cluster > 0 else (cmax if nb == 1 else min(cmax, BATCH_CLUSTER))
     ctx.cluster = ccl
-    mats = [B.Matrix(ctx, x, rank_cap=RANK_CAP) for x in inps]
+    mats = [B.Matrix(ctx, x, rank_cap=args.rank_cap) for x in inps]
     M = mats[0]
     for m in mats:
         m.snapshot()
@@ -378,7 +378,7 @@ def gpu_arm(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N, "nmin": NMIN, "rank": K, "col_scale_decades": DECADES,
-                       "tol": TOL, "rank_cap": RANK_CAP, "batch": nb, "cluster": ccl,
+                       "tol": TOL, "rank_cap": args.rank_cap, "batch": nb, "cluster": ccl,
                        "batching": "independent seeded matrices of the workload factored concurrently, one CUDA graph per step",
                        "l2": "flushed (256 MiB write) between timed steps",
                        "parallelism": f"replicas x{ws}", "anorm": anorm},
@@ -411,6 +411,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=64,
                     help="matrices of the workload factored concurrently per step (cross-matrix batching)")
+    ap.add_argument("--rank-cap", type=int, default=RANK_CAP,
+                    help="rank capacity of the stored factors (a factorization that needs more fails)")
     ap.add_argument("--no-served", action="store_true",
                     help="skip the served request stream (p50/p99 latency)")
     ap.add_argument("--cluster", type=int, default=0,

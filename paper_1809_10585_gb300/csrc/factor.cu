@@ -1159,6 +1159,11 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
   csync<SOLO>(cl);   // no CTA may exit while others still access its shared memory
 }
 
+// Shared memory of the remote-store Jacobi (jacobi_dsmem_impl) for a core of at most q1cap x q2cap.
+__host__ __device__ inline size_t jacobi_dsmem_bytes(int q1cap, int q2cap, int cluster) {
+  const size_t nloc = (q2cap + cluster - 1) / cluster;
+  return nloc * (q1cap + 1) * sizeof(double) + (size_t)q2cap * sizeof(double) + (size_t)q2cap * sizeof(int) + 64;
+}
 // Shared memory of the owner-computes Jacobi for a core of at most q1cap x q2cap on `cluster` CTAs.
 __host__ __device__ inline size_t jacobi_owner_bytes(int q1cap, int q2cap, int cluster) {
   const size_t nloc = (q2cap + cluster - 1) / cluster;
@@ -1190,16 +1195,22 @@ __global__ void __launch_bounds__(QT) jacobi_dsmem_kernel(const JacobiDesc* __re
     else if (q1 <= 16 * kJacobiRegs) jacobi_owner_impl<16, false>(descs, di, flops, q1cap, q2cap);
     else jacobi_owner_impl<32, false>(descs, di, flops, q1cap, q2cap);
   } else {
+    // the same one-CTA path when the reserved shared memory of the remote-store form suffices
+    const int q2 = min(dimv(d.q2, d.q2ref, di), q2cap);
+    const int C = (int)cg::this_cluster().num_blocks();
+    if (q2 <= kJacobiSoloCols && jacobi_owner_bytes(q1, q2, 1) <= jacobi_dsmem_bytes(q1cap, q2cap, C)) {
+      if (cg::this_cluster().block_rank() != 0) return;
+      if (q1 <= 8 * kJacobiRegs) jacobi_owner_impl<8, true>(descs, di, flops, q1cap, q2cap);
+      else if (q1 <= 16 * kJacobiRegs) jacobi_owner_impl<16, true>(descs, di, flops, q1cap, q2cap);
+      else jacobi_owner_impl<32, true>(descs, di, flops, q1cap, q2cap);
+      return;
+    }
     if (q1 <= 8 * kJacobiRegs) jacobi_dsmem_impl<8>(descs, di, flops, q1cap, q2cap);
     else if (q1 <= 16 * kJacobiRegs) jacobi_dsmem_impl<16>(descs, di, flops, q1cap, q2cap);
     else jacobi_dsmem_impl<32>(descs, di, flops, q1cap, q2cap);
   }
 }
 
-size_t jacobi_dsmem_bytes(int q1cap, int q2cap, int cluster) {
-  const size_t nloc = (q2cap + cluster - 1) / cluster;
-  return nloc * (q1cap + 1) * sizeof(double) + (size_t)q2cap * sizeof(double) + (size_t)q2cap * sizeof(int) + 64;
-}
 
 
 
