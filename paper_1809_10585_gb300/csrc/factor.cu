@@ -63,6 +63,10 @@ __device__ double block_sum(double v, double* red) {
 __device__ void qr_build_T(const QRDesc& d, const double* A, const size_t lda, const int h, const int kmax,
                            const int C, const int crank, cg::cluster_group& cl) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // staging area: 16 x 16 blocks of G per warp for the diagonal blocks, then the two 16 x 32
+  // operand tiles of the merges
+  __shared__ double gsm[QW][TNB][TNB + 1];
+  static_assert(QW * TNB * (TNB + 1) >= 2 * 16 * 33, "merge tiles must fit in the staging area");
   if (d.T == nullptr || kmax == 0) return;
 
   // ---- T from G = Y^T Y (strictly upper part), Y unit lower trapezoidal
@@ -144,63 +148,131 @@ __device__ void qr_build_T(const QRDesc& d, const double* A, const size_t lda, c
   }
   cl.sync();
   {
+    // Diagonal 16 x 16 blocks, one warp per block: the block of G is staged in shared memory and
+    // lane l keeps row l of the block of T in registers, so the column recurrence runs without
+    // global memory in its dependent chain.
     const int gw = warp * C + crank, nw = C * QW;   // consecutive items on different SMs
     const int nblk = (kmax + TNB - 1) / TNB;
     for (int b = gw; b < nblk; b += nw) {
-      const int b0 = b * TNB, b1 = min(kmax, b0 + TNB);
-      for (int jj = b0; jj < b1; ++jj) {
-        const double tj = __ldcg(&d.tau[jj]);
-        // lane l computes T[b0 + l, jj] for b0 + l < jj
-        int i = b0 + lane;
-        double v = 0.0;
-        if (i < jj && lane < TNB) {
-          double s = 0.0;
-          for (int l = i; l < jj; ++l) s = fma(T[i + l * ldt], __ldcg(&G[l + jj * ldg]), s);
-          v = -tj * s;
-        }
-        __syncwarp();
-        if (i < jj && lane < TNB) T[i + jj * ldt] = v;
-        if (lane == 0) T[jj + jj * ldt] = tj;
-        __syncwarp();
+      const int b0 = b * TNB, nbk = min(kmax, b0 + TNB) - b0;
+      for (int e = lane; e < TNB * TNB; e += 32) {
+        const int r = e % TNB, c = e / TNB;
+        gsm[warp][r][c] = (r < c && c < nbk) ? __ldcg(&G[(b0 + r) + (size_t)(b0 + c) * ldg]) : 0.0;
       }
+      const double tl = lane < nbk ? __ldcg(&d.tau[b0 + lane]) : 0.0;
+      __syncwarp();
+      double trow[TNB];
+#pragma unroll
+      for (int c = 0; c < TNB; ++c) trow[c] = 0.0;
+#pragma unroll
+      for (int c = 0; c < TNB; ++c) {
+        // T(l, c) = -tau_c sum_{l <= q < c} T(l, q) G(q, c), T(c, c) = tau_c
+        const double tc = __shfl_sync(0xffffffffu, tl, c);
+        double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+        for (int q = 0; q < c; ++q) {
+          if (q & 1) s1 = fma(trow[q], gsm[warp][q][c], s1);
+          else s0 = fma(trow[q], gsm[warp][q][c], s0);
+        }
+        trow[c] = lane < c ? -tc * (s0 + s1) : (lane == c ? tc : 0.0);
+      }
+      if (lane < nbk) {
+#pragma unroll
+        for (int c = 0; c < TNB; ++c)
+          if (c < nbk && c >= lane) T[(b0 + lane) + (size_t)(b0 + c) * ldt] = trow[c];
+      }
+      __syncwarp();
     }
   }
-  // ---- merges: T12 = -T1 G12 T2 for adjacent blocks of size s
+  // ---- merges: T12 = -T1 G12 T2 for adjacent blocks of size s, as two triangular products in
+  // 32 x 32 output tiles (one CTA per tile, operands staged through shared memory in chunks of
+  // 16; 2 x 2 outputs per thread): X = T1 G12 is kept transposed in G's strictly lower part,
+  // then T12 = -X T2.
+  double (*As)[33] = reinterpret_cast<double (*)[33]>(&gsm[0][0][0]);          // [16][33]
+  double (*Bs)[33] = reinterpret_cast<double (*)[33]>(&gsm[0][0][0] + 16 * 33);  // [16][33]
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   for (int s = TNB; s < kmax; s *= 2) {
-    cl.sync();
-    const long tid = (long)crank * QT + threadIdx.x, nt = (long)C * QT;
     const int npair = (kmax + 2 * s - 1) / (2 * s);
-    // X = T1 G12 stored transposed in G's strictly lower part: G[b + jj, a + i]
-    for (long e = tid; e < (long)npair * s * s; e += nt) {
-      int q = (int)(e / ((long)s * s));
-      int rem = (int)(e % ((long)s * s));
-      int i = rem % s, jj = rem / s;
-      int a = 2 * q * s, b = a + s;
-      if (b + jj >= kmax) continue;
-      double acc = 0.0, acc1 = 0.0;                       // two chains
-      int l = i;
-      for (; l + 1 < s; l += 2) {
-        acc = fma(__ldcg(&T[(a + i) + (size_t)(a + l) * ldt]), __ldcg(&G[(a + l) + (size_t)(b + jj) * ldg]), acc);
-        acc1 = fma(__ldcg(&T[(a + i) + (size_t)(a + l + 1) * ldt]), __ldcg(&G[(a + l + 1) + (size_t)(b + jj) * ldg]), acc1);
+    if (s < 32) {
+      // 16 x 16 blocks: one output per thread is cheaper than a padded 32 x 32 tile
+      const long tid = (long)crank * QT + threadIdx.x, nt = (long)C * QT;
+      cl.sync();
+      for (long e = tid; e < (long)npair * s * s; e += nt) {
+        const int q = (int)(e / ((long)s * s)), rem = (int)(e % ((long)s * s));
+        const int i = rem % s, jj = rem / s, a = 2 * q * s, b = a + s;
+        if (b + jj >= kmax) continue;
+        double acc = 0.0;
+        for (int l = i; l < s; ++l) acc = fma(__ldcg(&T[(a + i) + (size_t)(a + l) * ldt]), __ldcg(&G[(a + l) + (size_t)(b + jj) * ldg]), acc);
+        G[(b + jj) + (size_t)(a + i) * ldg] = acc;
       }
-      if (l < s) acc = fma(__ldcg(&T[(a + i) + (size_t)(a + l) * ldt]), __ldcg(&G[(a + l) + (size_t)(b + jj) * ldg]), acc);
-      G[(b + jj) + (size_t)(a + i) * ldg] = acc + acc1;
+      cl.sync();
+      for (long e = tid; e < (long)npair * s * s; e += nt) {
+        const int q = (int)(e / ((long)s * s)), rem = (int)(e % ((long)s * s));
+        const int i = rem % s, jj = rem / s, a = 2 * q * s, b = a + s;
+        if (b + jj >= kmax) continue;
+        double acc = 0.0;
+        for (int l = 0; l <= jj; ++l) acc = fma(__ldcg(&G[(b + l) + (size_t)(a + i) * ldg]), __ldcg(&T[(b + l) + (size_t)(b + jj) * ldt]), acc);
+        T[(a + i) + (size_t)(b + jj) * ldt] = -acc;
+      }
+      continue;
     }
-    cl.sync();
-    for (long e = tid; e < (long)npair * s * s; e += nt) {
-      int q = (int)(e / ((long)s * s));
-      int rem = (int)(e % ((long)s * s));
-      int i = rem % s, jj = rem / s;
-      int a = 2 * q * s, b = a + s;
-      if (b + jj >= kmax) continue;
-      double acc = 0.0, acc1 = 0.0;                       // two chains
-      int l = 0;
-      for (; l + 1 <= jj; l += 2) {
-        acc = fma(__ldcg(&G[(b + l) + (size_t)(a + i) * ldg]), __ldcg(&T[(b + l) + (size_t)(b + jj) * ldt]), acc);
-        acc1 = fma(__ldcg(&G[(b + l + 1) + (size_t)(a + i) * ldg]), __ldcg(&T[(b + l + 1) + (size_t)(b + jj) * ldt]), acc1);
+    const int tpd = (s + 31) / 32;                        // tiles per dimension of one pair
+    for (int pass = 0; pass < 2; ++pass) {
+      cl.sync();
+      for (int tile = crank; tile < npair * tpd * tpd; tile += C) {
+        const int q = tile / (tpd * tpd), rem = tile % (tpd * tpd);
+        const int i0 = 32 * (rem % tpd), j0 = 32 * (rem / tpd);
+        const int a = 2 * q * s, b = a + s;
+        const int bs = min(s, kmax - b);                  // width of the second block
+        if (bs <= 0 || j0 >= bs) continue;                // uniform over the CTA
+        double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+        // pass 0: X(i, jj) = sum_{l >= i} T1(i, l) G12(l, jj);  pass 1: T12(i, jj) = -sum_{l <= jj} X(i, l) T2(l, jj)
+        const int lbeg = pass == 0 ? i0 : 0;
+        const int lend = pass == 0 ? s : min(bs, j0 + 32);
+        for (int l0 = lbeg; l0 < lend; l0 += 16) {
+          for (int e = threadIdx.x; e < 32 * 16; e += QT) {
+            const int ii = e % 32, ll = e / 32;
+            const int i = i0 + ii, l = l0 + ll;
+            double va = 0.0;
+            if (i < s && l < lend) {
+              if (pass == 0) va = (l >= i) ? __ldcg(&T[(a + i) + (size_t)(a + l) * ldt]) : 0.0;
+              else va = __ldcg(&G[(b + l) + (size_t)(a + i) * ldg]);
+            }
+            As[ll][ii] = va;
+          }
+          for (int e = threadIdx.x; e < 16 * 32; e += QT) {
+            const int ll = e % 16, jj2 = e / 16;
+            const int l = l0 + ll, jj = j0 + jj2;
+            double vb = 0.0;
+            if (jj < bs && l < lend) {
+              if (pass == 0) vb = __ldcg(&G[(a + l) + (size_t)(b + jj) * ldg]);
+              else vb = (l <= jj) ? __ldcg(&T[(b + l) + (size_t)(b + jj) * ldt]) : 0.0;
+            }
+            Bs[ll][jj2] = vb;
+          }
+          __syncthreads();
+#pragma unroll
+          for (int ll = 0; ll < 16; ++ll) {
+            const double a0 = As[ll][ty], a1 = As[ll][ty + 16];
+            const double b0 = Bs[ll][tx], b1 = Bs[ll][tx + 16];
+            acc[0][0] = fma(a0, b0, acc[0][0]);
+            acc[0][1] = fma(a0, b1, acc[0][1]);
+            acc[1][0] = fma(a1, b0, acc[1][0]);
+            acc[1][1] = fma(a1, b1, acc[1][1]);
+          }
+          __syncthreads();
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int v = 0; v < 2; ++v) {
+            const int i = i0 + ty + 16 * u, jj = j0 + tx + 16 * v;
+            if (i < s && jj < bs) {
+              if (pass == 0) G[(b + jj) + (size_t)(a + i) * ldg] = acc[u][v];
+              else T[(a + i) + (size_t)(b + jj) * ldt] = -acc[u][v];
+            }
+          }
       }
-      if (l <= jj) acc = fma(__ldcg(&G[(b + l) + (size_t)(a + i) * ldg]), __ldcg(&T[(b + l) + (size_t)(b + jj) * ldt]), acc);
-      T[(a + i) + (size_t)(b + jj) * ldt] = -(acc + acc1);
     }
   }
 }
