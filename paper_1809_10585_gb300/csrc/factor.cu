@@ -431,9 +431,9 @@ __global__ void __launch_bounds__(QT) qr_cluster_kernel(const QRDesc* __restrict
 __global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __restrict__ descs,
                                                             const int* __restrict__ di, double* flops);
 
-__global__ void __launch_bounds__(QT) jacobi_dsmem_kernel(const JacobiDesc* __restrict__ descs,
+__global__ void __launch_bounds__(QT, 2) jacobi_dsmem_kernel(const JacobiDesc* __restrict__ descs,
                                                           const int* __restrict__ di, double* flops,
-                                                          int q1cap, int q2cap, int owner_form);
+                                                          int q1cap, int q2cap, int smem_bytes);
 constexpr size_t kJacobiSmemMax = 200 * 1024;
 
 
@@ -738,8 +738,8 @@ __device__ inline void rr_pair(int r, int i, int P, int& a, int& b) {
   }
 }
 
-__global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __restrict__ descs,
-                                                            const int* __restrict__ di, double* flops) {
+__device__ __forceinline__ void jacobi_global_impl(const JacobiDesc* __restrict__ descs,
+                                                   const int* __restrict__ di, double* flops) {
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int crank = (int)cl.block_rank();
@@ -865,6 +865,11 @@ __global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __
   }
 }
 
+__global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __restrict__ descs,
+                                                            const int* __restrict__ di, double* flops) {
+  jacobi_global_impl(descs, di, flops);
+}
+
 // One-sided Jacobi with the core held in distributed shared memory: column j lives in the
 // shared memory of CTA j % C.  Each warp rotates 32 / LG column pairs at once, one pair per
 // group of LG lanes (LG = 8, 16 or 32, the smallest with q1 <= LG * kJacobiRegs): the FP64
@@ -889,12 +894,12 @@ __device__ __forceinline__ void jacobi_dsmem_impl(const JacobiDesc* __restrict__
     atomicAdd(&flops[kKindSlot + 3], 4.0 * p * p * q + 8.0 * p * q * q + 9.0 * q * q * q);
   }
   extern __shared__ double jsm[];
-  const int nloc = (q2cap + C - 1) / C;
-  const int ldc = q1cap;
+  const int nloc = (q2 + C - 1) / C;                     // laid out by the actual core size
+  const int ldc = max(q1, 1);
   double* cols = jsm;                                    // nloc x ldc, slot s = column crank + s*C
   double* cn = cols + (size_t)nloc * ldc;                // current squared norms of own columns
   double* nall = cn + nloc;                              // squared norms of all columns (sweep start)
-  int* act = reinterpret_cast<int*>(nall + q2cap);       // active columns of the sweep
+  int* act = reinterpret_cast<int*>(nall + q2);          // active columns of the sweep
   __shared__ int nact;
   double* M = d.M;
   const size_t ldm = d.ldm;
@@ -1097,10 +1102,11 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
     atomicAdd(&flops[kKindSlot + 3], 4.0 * p * p * q + 8.0 * p * q * q + 9.0 * q * q * q);
   }
   extern __shared__ double jsm[];
-  // SOLO: the whole core in this CTA's shared memory, laid out by its actual size
-  const int nloc = SOLO ? q2 : (q2cap + C - 1) / C;
-  const int ldc = SOLO ? max(q1, 1) : q1cap;
-  const int q2n = SOLO ? q2 : q2cap;
+  // laid out by the core's actual size (ranks are known only here), which the caller checked
+  // against the shared memory of the launch
+  const int nloc = (q2 + C - 1) / C;
+  const int ldc = max(q1, 1);
+  const int q2n = q2;
   double* cols0 = jsm;                                   // [2][nloc][ldc], slot s = column crank + s*C
   double* cn0 = cols0 + 2 * (size_t)nloc * ldc;          // [2][nloc] tracked squared norms
   double* nall = cn0 + 2 * nloc;                         // squared norms of all columns (sweep start)
@@ -1305,40 +1311,40 @@ constexpr int kJacobiSoloCols = 32;   // cores up to this many columns run on on
 
 // Lane-group width from the actual column length of this cluster's core (ranks are known only
 // on the device; every CTA of the cluster reads the same descriptor, so the choice is uniform).
-__global__ void __launch_bounds__(QT) jacobi_dsmem_kernel(const JacobiDesc* __restrict__ descs,
+__global__ void __launch_bounds__(QT, 2) jacobi_dsmem_kernel(const JacobiDesc* __restrict__ descs,
                                                           const int* __restrict__ di, double* flops,
-                                                          int q1cap, int q2cap, int owner_form) {
+                                                          int q1cap, int q2cap, int smem_bytes) {
+  // The form is chosen from the core's actual size (every CTA of the cluster reads the same
+  // descriptor): one CTA for small cores; on clusters of 8 or more CTAs owner-computes when its
+  // two column buffers fit in the shared memory of the launch; else remote-store when one buffer
+  // fits; global memory otherwise.
   const JacobiDesc& d = descs[blockIdx.y];
   const int q1 = min(dimv(d.q1, d.q1ref, di), q1cap);
-  if (owner_form) {
-    // Small cores run on one CTA (shared-memory barriers, no remote loads) when their actual
-    // size fits in the shared memory this launch reserved per CTA; the other CTAs leave.
-    const int q2 = min(dimv(d.q2, d.q2ref, di), q2cap);
-    const int C = (int)cg::this_cluster().num_blocks();
-    if (q2 <= kJacobiSoloCols && jacobi_owner_bytes(q1, q2, 1) <= jacobi_owner_bytes(q1cap, q2cap, C)) {
-      if (cg::this_cluster().block_rank() != 0) return;
-      if (q1 <= 8 * kJacobiRegs) jacobi_owner_impl<8, true>(descs, di, flops, q1cap, q2cap);
-      else if (q1 <= 16 * kJacobiRegs) jacobi_owner_impl<16, true>(descs, di, flops, q1cap, q2cap);
-      else jacobi_owner_impl<32, true>(descs, di, flops, q1cap, q2cap);
-      return;
-    }
+  const int q2 = min(dimv(d.q2, d.q2ref, di), q2cap);
+  const int C = (int)cg::this_cluster().num_blocks();
+  const size_t avail = (size_t)smem_bytes;
+  if (q2 <= kJacobiSoloCols && jacobi_owner_bytes(q1, q2, 1) <= avail) {
+    if (cg::this_cluster().block_rank() != 0) return;
+    if (q1 <= 8 * kJacobiRegs) jacobi_owner_impl<8, true>(descs, di, flops, q1cap, q2cap);
+    else if (q1 <= 16 * kJacobiRegs) jacobi_owner_impl<16, true>(descs, di, flops, q1cap, q2cap);
+    else jacobi_owner_impl<32, true>(descs, di, flops, q1cap, q2cap);
+  } else if (C >= 8 && jacobi_owner_bytes(q1, q2, C) <= avail) {
+    // owner-computes shortens the round (only loads cross SMs) but computes every pair on both
+    // owners: it pays off on large clusters, where a round is latency-bound, not on small ones,
+    // where the SM's FP64 issue rate is the limit
+    if (q1 <= 8 * kJacobiRegs) jacobi_owner_impl<8, false>(descs, di, flops, q1cap, q2cap);
+    else if (q1 <= 16 * kJacobiRegs) jacobi_owner_impl<16, false>(descs, di, flops, q1cap, q2cap);
+    else jacobi_owner_impl<32, false>(descs, di, flops, q1cap, q2cap);
+  } else if (jacobi_dsmem_bytes(q1, q2, C) <= avail) {
+    if (q1 <= 8 * kJacobiRegs) jacobi_dsmem_impl<8>(descs, di, flops, q1cap, q2cap);
+    else if (q1 <= 16 * kJacobiRegs) jacobi_dsmem_impl<16>(descs, di, flops, q1cap, q2cap);
+    else jacobi_dsmem_impl<32>(descs, di, flops, q1cap, q2cap);
+  } else if (jacobi_owner_bytes(q1, q2, C) <= avail) {
     if (q1 <= 8 * kJacobiRegs) jacobi_owner_impl<8, false>(descs, di, flops, q1cap, q2cap);
     else if (q1 <= 16 * kJacobiRegs) jacobi_owner_impl<16, false>(descs, di, flops, q1cap, q2cap);
     else jacobi_owner_impl<32, false>(descs, di, flops, q1cap, q2cap);
   } else {
-    // the same one-CTA path when the reserved shared memory of the remote-store form suffices
-    const int q2 = min(dimv(d.q2, d.q2ref, di), q2cap);
-    const int C = (int)cg::this_cluster().num_blocks();
-    if (q2 <= kJacobiSoloCols && jacobi_owner_bytes(q1, q2, 1) <= jacobi_dsmem_bytes(q1cap, q2cap, C)) {
-      if (cg::this_cluster().block_rank() != 0) return;
-      if (q1 <= 8 * kJacobiRegs) jacobi_owner_impl<8, true>(descs, di, flops, q1cap, q2cap);
-      else if (q1 <= 16 * kJacobiRegs) jacobi_owner_impl<16, true>(descs, di, flops, q1cap, q2cap);
-      else jacobi_owner_impl<32, true>(descs, di, flops, q1cap, q2cap);
-      return;
-    }
-    if (q1 <= 8 * kJacobiRegs) jacobi_dsmem_impl<8>(descs, di, flops, q1cap, q2cap);
-    else if (q1 <= 16 * kJacobiRegs) jacobi_dsmem_impl<16>(descs, di, flops, q1cap, q2cap);
-    else jacobi_dsmem_impl<32>(descs, di, flops, q1cap, q2cap);
+    jacobi_global_impl(descs, di, flops);
   }
 }
 
@@ -1375,14 +1381,13 @@ cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, const int* 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const size_t smem2 = jacobi_owner_bytes(q1cap, q2cap, cluster);
-  if (smem2 <= kJacobiSmemMax && q2cap <= kJacobiMaxCols) {
+  // shared memory for the owner-computes form at the capacities, at most the per-CTA limit; the
+  // kernel picks its form from the actual core size, which is usually far below the capacities
+  const size_t smem2 = std::min(jacobi_owner_bytes(q1cap, q2cap, cluster), kJacobiSmemMax);
+  if (q2cap <= kJacobiMaxCols) {
     cfg.dynamicSmemBytes = smem2;
-    return cudaLaunchKernelEx(&cfg, jacobi_dsmem_kernel, (const JacobiDesc*)d, devints, flops, q1cap, q2cap, 1);
-  }
-  if (smem <= kJacobiSmemMax && q2cap <= kJacobiMaxCols) {
-    cfg.dynamicSmemBytes = smem;
-    return cudaLaunchKernelEx(&cfg, jacobi_dsmem_kernel, (const JacobiDesc*)d, devints, flops, q1cap, q2cap, 0);
+    return cudaLaunchKernelEx(&cfg, jacobi_dsmem_kernel, (const JacobiDesc*)d, devints, flops, q1cap, q2cap,
+                              (int)smem2);
   }
   return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel, (const JacobiDesc*)d, devints, flops);
 }
