@@ -60,6 +60,15 @@ int hodlr_ctx_set_stream(hodlr_ctx* ctx, void* stream);
  * below 1 or above the device's maximum. */
 int hodlr_ctx_set_cluster(hodlr_ctx* ctx, int cluster);
 int hodlr_ctx_get_cluster(hodlr_ctx* ctx, int* cluster);
+/* Number of factorizations the caller runs on the GPU at the same time through this and other
+ * contexts (default 1).  Above 1, the QR and Jacobi kernels reserve less shared memory per CTA
+ * (two CTAs per SM instead of one), so that CTAs of different factorizations share SMs;
+ * hodlr_qr_batched applies this by itself for the duration of a batch of two or more.  Results
+ * depend on the setting at the level of rounding only (a matrix whose columns no longer fit in
+ * the cluster's shared memory is factored in the global-memory form).  Graphs captured earlier
+ * are re-captured on their next call.  HODLR_EINVAL for a value below 1. */
+int hodlr_ctx_set_concurrency(hodlr_ctx* ctx, int factorizations);
+int hodlr_ctx_get_concurrency(hodlr_ctx* ctx, int* factorizations);
 /* Block until all queued work on the context's stream is done. */
 int hodlr_sync(hodlr_ctx* ctx);
 

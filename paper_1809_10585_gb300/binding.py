@@ -37,6 +37,8 @@ _SIGS = {
     "hodlr_ctx_set_stream": (C.c_int, [_VP, _VP]),
     "hodlr_ctx_set_cluster": (C.c_int, [_VP, C.c_int]),
     "hodlr_ctx_get_cluster": (C.c_int, [_VP, _PI]),
+    "hodlr_ctx_set_concurrency": (C.c_int, [_VP, C.c_int]),
+    "hodlr_ctx_get_concurrency": (C.c_int, [_VP, _PI]),
     "hodlr_sync": (C.c_int, [_VP]),
     "hodlr_build": (C.c_int, [_VP, C.c_int, C.c_int, _PI, _PPD, _PPD, _PPD, _PI, _PPD, _PPD, _PI, C.c_int, C.POINTER(_VP)]),
     "hodlr_build_dense": (C.c_int, [_VP, C.c_int, C.c_int, _PI, _VP, C.c_int, C.c_double, C.c_int, C.c_ulonglong,
@@ -129,6 +131,16 @@ class Context:
     @cluster.setter
     def cluster(self, size: int):
         check(lib().hodlr_ctx_set_cluster(self.h, int(size)), "hodlr_ctx_set_cluster")
+
+    @property
+    def concurrency(self) -> int:
+        v = C.c_int()
+        check(lib().hodlr_ctx_get_concurrency(self.h, C.byref(v)), "hodlr_ctx_get_concurrency")
+        return v.value
+
+    @concurrency.setter
+    def concurrency(self, factorizations: int):
+        check(lib().hodlr_ctx_set_concurrency(self.h, int(factorizations)), "hodlr_ctx_set_concurrency")
 
     def sync(self):
         check(lib().hodlr_sync(self.h), "hodlr_sync")

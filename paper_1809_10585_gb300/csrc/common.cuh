@@ -157,10 +157,16 @@ cudaError_t launch_gemm(GemmDesc* h_descs, int n, GemmDesc* d_descs, const int* 
 cudaError_t launch_concat(const ConcatDesc* h, int n, ConcatDesc* d, int* devints, cudaStream_t s);
 cudaError_t launch_panel_gather(const PanelDesc* h, int n, PanelDesc* d, int* devints, cudaStream_t s);
 cudaError_t launch_panel_scatter(const PanelDesc* h, int n, PanelDesc* d, const int* devints, cudaStream_t s);
+// The cluster kernels reserve shared memory for the capacities of their launch, at most
+// `smem_cap` bytes (the per-CTA limit when larger), and pick their form from the actual sizes.
+// kClusterSmemShared is the cap while several factorizations run concurrently: two CTAs per SM
+// (their register use, ~126 per thread at 256 threads, allows no more), each with up to 18 KB
+// of static shared memory, out of the SM's 228 KB.
+constexpr size_t kClusterSmemShared = 92 * 1024;
 cudaError_t launch_qr(const QRDesc* h, int n, QRDesc* d, const int* devints, double* flops,
-                      int cluster, cudaStream_t s);
+                      int cluster, size_t smem_cap, cudaStream_t s);
 cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, const int* devints,
-                          double* flops, int cluster, cudaStream_t s);
+                          double* flops, int cluster, size_t smem_cap, cudaStream_t s);
 cudaError_t launch_select(const SelectDesc* h, int n, SelectDesc* d, int* devints, double* flops,
                           cudaStream_t s);
 cudaError_t launch_copy(const CopyDesc* h, int n, CopyDesc* d, const int* devints, cudaStream_t s);

@@ -1,6 +1,6 @@
 // Cluster-cooperative FP64 factorizations of the hQR hot path:
 //
-//  * qr_cluster_kernel — Householder QR in compact WY form (Alg. 1 semantics: one
+//  * qr_dsmem_kernel — Householder QR in compact WY form (Alg. 1 semantics: one
 //    reflector per column, LAPACK dlarfg sign convention) of one dense h x w matrix per
 //    thread-block cluster.  Columns are dealt cyclically to the CTAs of the cluster; for
 //    column j its owner builds the reflector, one cluster barrier publishes it, and every CTA
@@ -10,15 +10,17 @@
 //    Used for the compressed leaf columns (Alg. 2, lowest level), the left-orthogonalization
 //    (Sec. 2.1) and the two QRs inside T_eps (Sec. 2.1.1).
 //
-//  * jacobi_cluster_kernel — one-sided (Hestenes) Jacobi on the columns of the K x K core of
+//  * jacobi_dsmem_kernel — one-sided (Hestenes) Jacobi on the columns of the K x K core of
 //    T_eps, round-robin pair ordering, pairs spread over all warps of the cluster, one
 //    cluster barrier per round.
 //
 // On GB300 a single SM retires about 2 FP64 FMA per clock, so a K^3 factorization on one SM
 // takes milliseconds for K ~ 100; a cluster of up to 16 CTAs (one per SM) multiplies the FP64
-// rate at the cost of one hardware cluster barrier per step.  Data stay in global memory
-// (L2-resident at these sizes) and are read with ld.global.cg so that values published by
-// other CTAs of the cluster after a barrier are never served stale from L1.
+// rate at the cost of one hardware cluster barrier per step.  Both kernels pick their form
+// from the actual (device-side) sizes: columns in the shared memory of the cluster's CTAs,
+// exchanged through distributed shared memory, when they fit; otherwise in global memory
+// (L2-resident at these sizes), read with ld.global.cg so that values published by other CTAs
+// of the cluster after a barrier are never served stale from L1.
 #include <cooperative_groups.h>
 
 #include <cstdio>
@@ -34,7 +36,6 @@ constexpr int QW = QT / 32;        // warps per CTA
 constexpr int TNB = 16;            // diagonal block size of the T build
 constexpr int kJacobiRegs = 8;     // column elements per lane held in registers (q1 <= 256)
 constexpr int kQRRegs = 16;        // QR: column elements per lane in registers (h <= 512)
-constexpr int kQRStageRows = 4096; // QR: reflector staged in shared memory up to this height
 constexpr int kJacobiMaxCols = 4096;
 
 __device__ inline double warp_sum2(double v) {
@@ -277,8 +278,10 @@ __device__ void qr_build_T(const QRDesc& d, const double* A, const size_t lda, c
   }
 }
 
-__global__ void __launch_bounds__(QT) qr_cluster_kernel(const QRDesc* __restrict__ descs,
-                                                        const int* __restrict__ di, double* flops) {
+// Global-memory form of the cluster QR: the columns stay in global memory (L2-resident),
+// the reflector is staged in `ysm` (shared memory of `stage_rows` doubles) when it fits.
+__device__ __forceinline__ void qr_global_impl(const QRDesc* __restrict__ descs, const int* __restrict__ di,
+                                               double* flops, double* ysm, int stage_rows) {
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int crank = (int)cl.block_rank();
@@ -314,7 +317,6 @@ __global__ void __launch_bounds__(QT) qr_cluster_kernel(const QRDesc* __restrict
   // every CTA has used it; its owner scales it after the next cluster barrier.  scal_j is kept
   // on G's diagonal (the T build uses only G's off-diagonal parts).  The norm of the next
   // pivot column is produced by the warp that applies the current reflector to it.
-  __shared__ double ysm[kQRStageRows];
   __shared__ double xn_next;
   double* G0 = d.G;
   const size_t ldg0 = d.ldg;
@@ -328,7 +330,7 @@ __global__ void __launch_bounds__(QT) qr_cluster_kernel(const QRDesc* __restrict
     if (threadIdx.x == 0) xn_next = s;
   }
   __syncthreads();
-  const bool staged = h <= kQRStageRows;
+  const bool staged = h <= stage_rows;
   const bool in_regs = h <= 32 * kQRRegs;
   for (int j = 0; j < kmax; ++j) {
     if ((j % C) == crank && threadIdx.x == 0) {
@@ -442,23 +444,22 @@ constexpr size_t kJacobiSmemMax = 200 * 1024;
 // reflector in place, one cluster barrier publishes it, and every CTA copies it once through
 // DSMEM into a local buffer before updating its own columns (one warp per column, the warp
 // that updates the next pivot also returns that column's norm).  The factored columns are
-// written back to global memory and T is built as in qr_cluster_kernel.
-__global__ void __launch_bounds__(QT) qr_dsmem_kernel(const QRDesc* __restrict__ descs,
-                                                      const int* __restrict__ di, double* flops,
-                                                      int hcap, int wcap) {
+// written back to global memory and T is built as in the global-memory form.  The layout
+// follows the actual size h x w: `nloc` slots of h doubles and a reflector buffer of h.
+__device__ __forceinline__ void qr_dsmem_impl(const QRDesc* __restrict__ descs, const int* __restrict__ di,
+                                              double* flops, int h, int w, double* qsm) {
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int crank = (int)cl.block_rank();
   const QRDesc& d = descs[blockIdx.y];
-  const int h = min(dimv(d.h, d.href, di), hcap), w = min(dimv(d.w, d.wref, di), wcap);
   const int kmax = min(h, w);
   double* A = d.A;
   const size_t lda = d.lda;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  extern __shared__ double qsm[];
-  const int nloc = (wcap + C - 1) / C;
-  double* cols = qsm;                                   // nloc x hcap
-  double* ybuf = cols + (size_t)nloc * hcap;            // hcap
+  const int nloc = (w + C - 1) / C;
+  const size_t ldc = h;
+  double* cols = qsm;                                   // nloc x h
+  double* ybuf = cols + (size_t)nloc * ldc;             // h
   __shared__ double red[QW + 1];
   __shared__ double sh_tau, xn_next;
 
@@ -482,7 +483,7 @@ __global__ void __launch_bounds__(QT) qr_dsmem_kernel(const QRDesc* __restrict__
   for (int sl = 0; sl < nloc; ++sl) {
     const int c = crank + sl * C;
     if (c >= w) break;
-    for (int i = threadIdx.x; i < h; i += QT) cols[(size_t)sl * hcap + i] = A[i + (size_t)c * lda];
+    for (int i = threadIdx.x; i < h; i += QT) cols[(size_t)sl * ldc + i] = A[i + (size_t)c * lda];
   }
   cl.sync();                                             // all CTAs running before any DSMEM access
   if (crank == 0 && kmax > 0) {
@@ -496,7 +497,7 @@ __global__ void __launch_bounds__(QT) qr_dsmem_kernel(const QRDesc* __restrict__
   for (int j = 0; j < kmax; ++j) {
     const int owner = j % C;
     if (owner == crank) {
-      double* cj = cols + (size_t)(j / C) * hcap;
+      double* cj = cols + (size_t)(j / C) * ldc;
       if (threadIdx.x == 0) {
         const double s = xn_next;
         const double alpha = cj[j];
@@ -521,14 +522,14 @@ __global__ void __launch_bounds__(QT) qr_dsmem_kernel(const QRDesc* __restrict__
     cl.sync();
     const double tau = *cl.map_shared_rank(&sh_tau, owner);
     if (tau != 0.0) {
-      const double* yj = cl.map_shared_rank(cols, owner) + (size_t)(j / C) * hcap;
+      const double* yj = cl.map_shared_rank(cols, owner) + (size_t)(j / C) * ldc;
       for (int i = j + 1 + threadIdx.x; i < h; i += QT) ybuf[i] = yj[i];
       __syncthreads();
     }
     const int first = j + 1;
     const int c0 = first + ((crank - first % C) + C) % C;
     for (int c = c0 + warp * C; c < w; c += QW * C) {
-      double* a = cols + (size_t)(c / C) * hcap;
+      double* a = cols + (size_t)(c / C) * ldc;
       double nn = 0.0;
       if (tau != 0.0) {
         if (in_regs) {
@@ -596,15 +597,31 @@ __global__ void __launch_bounds__(QT) qr_dsmem_kernel(const QRDesc* __restrict__
   for (int sl = 0; sl < nloc; ++sl) {
     const int c = crank + sl * C;
     if (c >= w) break;
-    for (int i = threadIdx.x; i < h; i += QT) A[i + (size_t)c * lda] = cols[(size_t)sl * hcap + i];
+    for (int i = threadIdx.x; i < h; i += QT) A[i + (size_t)c * lda] = cols[(size_t)sl * ldc + i];
   }
   qr_build_T(d, A, lda, h, kmax, C, crank, cl);   // starts with a cluster barrier
 }
 
-size_t qr_dsmem_bytes(int hcap, int wcap, int cluster) {
-  const size_t nloc = (wcap + cluster - 1) / cluster;
-  return (nloc + 1) * (size_t)hcap * sizeof(double) + 64;
+// Bytes of shared memory of the distributed form for an h x w matrix on C CTAs.
+__host__ __device__ inline size_t qr_dsmem_bytes(int h, int w, int cluster) {
+  const size_t nloc = (w + cluster - 1) / cluster;
+  return (nloc + 1) * (size_t)h * sizeof(double) + 64;
 }
+
+// The form is chosen from the matrix's actual size (every CTA of the cluster reads the same
+// descriptor): distributed shared memory when its columns fit in the launch's shared memory,
+// the global-memory form otherwise (reflector staged in the same shared memory).
+__global__ void __launch_bounds__(QT) qr_dsmem_kernel(const QRDesc* __restrict__ descs,
+                                                      const int* __restrict__ di, double* flops,
+                                                      int hcap, int wcap, int smem_bytes) {
+  const QRDesc& d = descs[blockIdx.y];
+  const int h = min(dimv(d.h, d.href, di), hcap), w = min(dimv(d.w, d.wref, di), wcap);
+  const int C = (int)cg::this_cluster().num_blocks();
+  extern __shared__ double qsm[];
+  if (qr_dsmem_bytes(h, w, C) <= (size_t)smem_bytes) qr_dsmem_impl(descs, di, flops, h, w, qsm);
+  else qr_global_impl(descs, di, flops, qsm, smem_bytes / (int)sizeof(double));
+}
+
 constexpr size_t kQRSmemMax = 200 * 1024;
 
 // Largest cluster size both cluster kernels can be launched with (16 needs the non-portable
@@ -614,7 +631,8 @@ int qr_max_cluster() {
   static int cached = -1;
   if (cached > 0) return cached;
   int v = 8;
-  bool ok = cudaFuncSetAttribute(qr_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+  bool ok = cudaFuncSetAttribute(qr_dsmem_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+            cudaFuncSetAttribute(qr_dsmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQRSmemMax) == cudaSuccess &&
             cudaFuncSetAttribute(jacobi_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
   if (ok) {
     cudaLaunchConfig_t cfg = {};
@@ -628,7 +646,9 @@ int qr_max_cluster() {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, qr_cluster_kernel, &cfg) == cudaSuccess && nclusters > 0) {
+    cfg.dynamicSmemBytes = kQRSmemMax;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, qr_dsmem_kernel, &cfg) == cudaSuccess && nclusters > 0) {
+      cfg.dynamicSmemBytes = 0;
       int nj = 0;
       if (cudaOccupancyMaxActiveClusters(&nj, jacobi_cluster_kernel, &cfg) == cudaSuccess && nj > 0) v = 16;
     }
@@ -636,15 +656,13 @@ int qr_max_cluster() {
   cudaGetLastError();
   cudaFuncSetAttribute(jacobi_dsmem_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaFuncSetAttribute(jacobi_dsmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kJacobiSmemMax);
-  cudaFuncSetAttribute(qr_dsmem_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  cudaFuncSetAttribute(qr_dsmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQRSmemMax);
   cudaGetLastError();
   cached = v;
   return v;
 }
 
 cudaError_t launch_qr(const QRDesc* h, int n, QRDesc* d, const int* devints, double* flops,
-                      int cluster, cudaStream_t s) {
+                      int cluster, size_t smem_cap, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cluster, n, 1);
@@ -663,12 +681,11 @@ cudaError_t launch_qr(const QRDesc* h, int n, QRDesc* d, const int* devints, dou
     hcap = max(hcap, h[i].h);
     wcap = max(wcap, h[i].w);
   }
-  const size_t smem = qr_dsmem_bytes(hcap, wcap, cluster);
-  if (smem <= kQRSmemMax) {
-    cfg.dynamicSmemBytes = smem;
-    return cudaLaunchKernelEx(&cfg, qr_dsmem_kernel, (const QRDesc*)d, devints, flops, hcap, wcap);
-  }
-  return cudaLaunchKernelEx(&cfg, qr_cluster_kernel, (const QRDesc*)d, devints, flops);
+  // shared memory for the capacities, up to the per-CTA limit; the kernel picks its form from
+  // the actual sizes
+  const size_t smem = std::min(qr_dsmem_bytes(hcap, wcap, cluster), std::min(kQRSmemMax, smem_cap));
+  cfg.dynamicSmemBytes = smem;
+  return cudaLaunchKernelEx(&cfg, qr_dsmem_kernel, (const QRDesc*)d, devints, flops, hcap, wcap, (int)smem);
 }
 
 // --------------------------------------------------------------------------------- Jacobi
@@ -1352,7 +1369,7 @@ __global__ void __launch_bounds__(QT, 2) jacobi_dsmem_kernel(const JacobiDesc* _
 
 
 cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, const int* devints, double* flops,
-                          int cluster, cudaStream_t s) {
+                          int cluster, size_t smem_cap, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int cluster_max = cluster;
   int q1cap = 0, q2cap = 0;
@@ -1383,7 +1400,7 @@ cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, const int* 
   cfg.numAttrs = 1;
   // shared memory for the owner-computes form at the capacities, at most the per-CTA limit; the
   // kernel picks its form from the actual core size, which is usually far below the capacities
-  const size_t smem2 = std::min(jacobi_owner_bytes(q1cap, q2cap, cluster), kJacobiSmemMax);
+  const size_t smem2 = std::min(jacobi_owner_bytes(q1cap, q2cap, cluster), std::min(kJacobiSmemMax, smem_cap));
   if (q2cap <= kJacobiMaxCols) {
     cfg.dynamicSmemBytes = smem2;
     return cudaLaunchKernelEx(&cfg, jacobi_dsmem_kernel, (const JacobiDesc*)d, devints, flops, q1cap, q2cap,
@@ -1438,7 +1455,7 @@ extern "C" int hodlr_dense_qr_noalloc(hodlr_ctx* ctx, int h, int w, double* A, i
   QRDesc* dq = reinterpret_cast<QRDesc*>(base);
   // every entry of tau and G is written by the kernel before it is read: nothing to clear
   cudaError_t e = cudaMemcpyAsync(dq, &q, sizeof(QRDesc), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = launch_qr(&q, 1, dq, nullptr, nullptr, ctx_cluster(ctx), s);
+  if (e == cudaSuccess) e = launch_qr(&q, 1, dq, nullptr, nullptr, ctx_cluster(ctx), (size_t)-1, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, __FILE__, __LINE__);
   return 0;

@@ -43,7 +43,16 @@ struct hodlr_ctx {
   std::vector<hodlr_mat*> bmats;
   double btol = -1, banorm = -2;
   int bcluster = 0;
+  int concurrency = 1;           // factorizations in flight, as set by the caller
+  int concurrent = 1;            // factorizations in flight on the pool's streams (batch size)
+  int bconc = 0;
 };
+
+// Shared memory a cluster kernel may reserve per CTA: the per-CTA limit for one factorization at
+// a time; with several in flight, a cap that lets CTAs of other factorizations share the SM.
+static size_t smem_cap(const hodlr_ctx* ctx) {
+  return std::max(ctx->concurrent, ctx->concurrency) > 1 ? kClusterSmemShared : (size_t)-1;
+}
 
 enum RecType { R_GEMM, R_REDUCE, R_CONCAT, R_GATHER, R_SCATTER, R_QR, R_JACOBI, R_SELECT, R_COPY,
                R_FILL, R_IDENT, R_NORM, R_MEMSET_INT, R_TRSM, R_EVREC, R_EVWAIT, R_GAUSS };
@@ -118,6 +127,7 @@ struct hodlr_mat {
   cudaGraphExec_t gexec = nullptr;
   double g_tol = -1, g_anorm = -2;
   int g_cluster = 0;
+  int g_conc = 0;
   bool factored = false;
 };
 
@@ -882,8 +892,13 @@ static int run_plan_on(hodlr_ctx* ctx, hodlr_mat* M, Plan& P, Profiler* prof, cu
       case R_CONCAT: e = launch_concat((const ConcatDesc*)hb, r.n, (ConcatDesc*)dp, M->devints, s); break;
       case R_GATHER: e = launch_panel_gather((const PanelDesc*)hb, r.n, (PanelDesc*)dp, M->devints, s); break;
       case R_SCATTER: e = launch_panel_scatter((const PanelDesc*)hb, r.n, (PanelDesc*)dp, M->devints, s); break;
-      case R_QR: e = launch_qr((const QRDesc*)hb, r.n, (QRDesc*)dp, M->devints, flops, ctx->cluster, s); break;
-      case R_JACOBI: e = launch_jacobi((const JacobiDesc*)hb, r.n, (JacobiDesc*)dp, M->devints, flops, ctx->cluster, s); break;
+      case R_QR:
+        e = launch_qr((const QRDesc*)hb, r.n, (QRDesc*)dp, M->devints, flops, ctx->cluster, smem_cap(ctx), s);
+        break;
+      case R_JACOBI:
+        e = launch_jacobi((const JacobiDesc*)hb, r.n, (JacobiDesc*)dp, M->devints, flops, ctx->cluster,
+                          smem_cap(ctx), s);
+        break;
       case R_SELECT: e = launch_select((const SelectDesc*)hb, r.n, (SelectDesc*)dp, M->devints, flops, s); break;
       case R_COPY: e = launch_copy((const CopyDesc*)hb, r.n, (CopyDesc*)dp, M->devints, s); break;
       case R_FILL: e = launch_fill(r.p0, r.cnt, r.v, s); break;
@@ -1090,6 +1105,18 @@ int hodlr_ctx_set_cluster(hodlr_ctx* ctx, int cluster) {
 int hodlr_ctx_get_cluster(hodlr_ctx* ctx, int* cluster) {
   if (!ctx || !cluster) return HODLR_EINVAL;
   *cluster = ctx->cluster;
+  return HODLR_OK;
+}
+
+int hodlr_ctx_set_concurrency(hodlr_ctx* ctx, int factorizations) {
+  if (!ctx || factorizations < 1) return HODLR_EINVAL;
+  ctx->concurrency = factorizations;
+  return HODLR_OK;
+}
+
+int hodlr_ctx_get_concurrency(hodlr_ctx* ctx, int* factorizations) {
+  if (!ctx || !factorizations) return HODLR_EINVAL;
+  *factorizations = ctx->concurrency;
   return HODLR_OK;
 }
 
@@ -1357,7 +1384,8 @@ int hodlr_qr_graph(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm) {
   HQ_CUDA_OK(cudaSetDevice(ctx->dev));
   int rc = ensure_plan(ctx, A, tol, anorm);
   if (rc) return rc;
-  if (!A->gexec || A->g_tol != tol || A->g_anorm != anorm || A->g_cluster != ctx->cluster) {
+  if (!A->gexec || A->g_tol != tol || A->g_anorm != anorm || A->g_cluster != ctx->cluster ||
+      A->g_conc != ctx->concurrency) {
     if (A->gexec) cudaGraphExecDestroy(A->gexec);
     A->gexec = nullptr;
     cudaGraph_t g;
@@ -1373,6 +1401,7 @@ int hodlr_qr_graph(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm) {
     A->g_tol = tol;
     A->g_anorm = anorm;
     A->g_cluster = ctx->cluster;
+    A->g_conc = ctx->concurrency;
   }
   HQ_CUDA_OK(cudaGraphLaunch(A->gexec, ctx->s));
   A->factored = true;
@@ -1434,6 +1463,7 @@ static int batch_launch(hodlr_ctx* ctx, int count, hodlr_mat* const* A, double t
   HQ_CUDA_OK(cudaEventRecord(fork, ctx->s));
   std::vector<cudaEvent_t> joins(count, nullptr);
   int rc = HODLR_OK;
+  ctx->concurrent = count;
   for (int i = 0; i < count && !rc; ++i) {
     cudaStream_t m = ctx->pool[i].first, sd = ctx->pool[i].second;
     if (cudaStreamWaitEvent(m, fork, 0) != cudaSuccess) rc = HODLR_ECUDA;
@@ -1447,6 +1477,7 @@ static int batch_launch(hodlr_ctx* ctx, int count, hodlr_mat* const* A, double t
                 cudaEventRecord(joins[i], m) != cudaSuccess || cudaStreamWaitEvent(ctx->s, joins[i], 0) != cudaSuccess))
       rc = HODLR_ECUDA;
   }
+  ctx->concurrent = 1;
   cudaEventDestroy(fork);
   for (auto e : joins)
     if (e) cudaEventDestroy(e);
@@ -1489,7 +1520,7 @@ int hodlr_qr_batched_graph(hodlr_ctx* ctx, int count, hodlr_mat* const* A, doubl
   if (rc) return rc;
   std::vector<hodlr_mat*> key(A, A + count);
   if (!ctx->bgraph || replan || key != ctx->bmats || ctx->btol != tol || ctx->banorm != anorm ||
-      ctx->bcluster != ctx->cluster) {
+      ctx->bcluster != ctx->cluster || ctx->bconc != ctx->concurrency) {
     if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
     ctx->bgraph = nullptr;
     cudaGraph_t g;
@@ -1505,6 +1536,7 @@ int hodlr_qr_batched_graph(hodlr_ctx* ctx, int count, hodlr_mat* const* A, doubl
     ctx->btol = tol;
     ctx->banorm = anorm;
     ctx->bcluster = ctx->cluster;
+    ctx->bconc = ctx->concurrency;
   }
   HQ_CUDA_OK(cudaGraphLaunch(ctx->bgraph, ctx->s));
   for (int i = 0; i < count; ++i) A[i]->factored = true;
@@ -1770,7 +1802,7 @@ int hodlr_dense_qr(hodlr_ctx* ctx, int h, int w, double* A, int lda, double* T, 
   q.A = A; q.lda = lda; q.h = h; q.w = w; q.href = -1; q.wref = -1; q.tau = tau; q.T = T; q.ldt = ldt;
   q.G = G; q.ldg = k; q.step = kStepNone; q.fmode = 0;
   cudaError_t e = cudaMemcpyAsync(dq, &q, sizeof(QRDesc), cudaMemcpyHostToDevice, ctx->s);
-  if (e == cudaSuccess) e = launch_qr(&q, 1, dq, nullptr, nullptr, ctx->cluster, ctx->s);
+  if (e == cudaSuccess) e = launch_qr(&q, 1, dq, nullptr, nullptr, ctx->cluster, (size_t)-1, ctx->s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->s);
   cudaFree(tau);
   cudaFree(G);

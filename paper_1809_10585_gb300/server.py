@@ -70,6 +70,8 @@ class Server:
         self.device = device
         self.dev = f"cuda:{device}"      # where right-hand sides are staged
         self.slots = [B.Context(device) for _ in range(slots)]
+        for c in self.slots:             # several factorizations share the SMs
+            c.concurrency = slots
         self.free = deque(range(slots))
         self.budget = float(hbm_budget)
         self.used = 0.0

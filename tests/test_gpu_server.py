@@ -32,7 +32,7 @@ def test_results_alone_equal_results_in_the_mix():
     lat = mix.latencies()
     mix.close()
     assert lat["count"] == len(got) and lat["p99_s"] >= lat["p50_s"] > 0
-    alone = S.Server(0, slots=1, hbm_budget=60e9)
+    alone = S.Server(0, slots=6, hbm_budget=60e9)     # same slots, one request at a time
     ref = []
     for r in _requests():
         r.arrival = 0.0

@@ -6,8 +6,9 @@
   products) and the leading diagonal block of R is compared with a dense QR of the leading
   block column;
 * a sample of the cross-matrix batch family (n log-uniform, nmin in {128, 256}, ranks 5-20,
-  every second matrix column-scaled), factored in one batched CUDA graph: each matrix equals
-  its factorization alone bit for bit and meets the error bounds against a dense reference;
+  every second matrix column-scaled), factored in one batched CUDA graph: each matrix agrees
+  with its factorization alone to rounding (with several factorizations in flight the cluster
+  kernels may run in another form) and meets the error bounds against a dense reference;
 * symmetric banded matrices (b = 8) as HODLR matrices with exact rank-b off-diagonal blocks."""
 import numpy as np
 import pytest
@@ -96,7 +97,7 @@ def test_batched_family_sample():
             assert M.status()[0] == 0
             got = [U.dense_of(M, w).cpu().numpy() for w in (1, 2, 3)]
             for a, b in zip(got, ref):
-                assert np.array_equal(a, b), inp.name
+                assert np.max(np.abs(a - b)) <= 1e-9 * max(1.0, np.max(np.abs(b))), inp.name
             Y, R, T = (torch.from_numpy(np.ascontiguousarray(x.T)).cuda() for x in got)
             A = torch.from_numpy(W.to_dense(inp)).cuda()
             an = U.norm2(A)
