@@ -382,6 +382,7 @@ __device__ __forceinline__ void qr_global_impl(const QRDesc* __restrict__ descs,
           t = warp_sum2(t);
           const double wv = tau * fma(scal, t, __ldcg(&a[j]));
           const double ws = wv * scal;
+          const bool pivot = c == j + 1;          // next pivot: its norm below row j + 1 too
 #pragma unroll
           for (int q = 0; q < kQRRegs; ++q) {
             if (q < nq) {
@@ -389,7 +390,7 @@ __device__ __forceinline__ void qr_global_impl(const QRDesc* __restrict__ descs,
               if (i < h) {
                 const double v = fma(-ws, staged ? ysm[i] : __ldcg(&y[i]), r[q]);
                 a[i] = v;
-                if (i > j + 1) nn = fma(v, v, nn);
+                if (pivot && i > j + 1) nn = fma(v, v, nn);
               }
             }
           }
@@ -400,10 +401,11 @@ __device__ __forceinline__ void qr_global_impl(const QRDesc* __restrict__ descs,
           t = warp_sum2(t);
           const double wv = tau * fma(scal, t, __ldcg(&a[j]));
           const double ws = wv * scal;
+          const bool pivot = c == j + 1;
           for (int i = j + 1 + lane; i < h; i += 32) {
             const double v = fma(-ws, staged ? ysm[i] : __ldcg(&y[i]), __ldcg(&a[i]));
             a[i] = v;
-            if (i > j + 1) nn = fma(v, v, nn);
+            if (pivot && i > j + 1) nn = fma(v, v, nn);
           }
           if (lane == 0) a[j] = __ldcg(&a[j]) - wv;
         }
@@ -549,22 +551,32 @@ __device__ __forceinline__ void qr_dsmem_impl(const QRDesc* __restrict__ descs, 
           }
           double t = warp_sum2(t0 + t1);
           const double wv = tau * (t + a[j]);
-          double nn1 = 0.0;
+          if (c == j + 1) {                       // next pivot: its norm below row j + 1 too
+            double nn1 = 0.0;
 #pragma unroll
-          for (int q = 0; q < kQRRegs; ++q) {
-            if (q < nq) {
-              const int i = j + 1 + lane + 32 * q;
-              if (i < h) {
-                const double v = fma(-wv, ybuf[i], r[q]);
-                a[i] = v;
-                if (i > j + 1) {
-                  if (q & 1) nn1 = fma(v, v, nn1);
-                  else nn = fma(v, v, nn);
+            for (int q = 0; q < kQRRegs; ++q) {
+              if (q < nq) {
+                const int i = j + 1 + lane + 32 * q;
+                if (i < h) {
+                  const double v = fma(-wv, ybuf[i], r[q]);
+                  a[i] = v;
+                  if (i > j + 1) {
+                    if (q & 1) nn1 = fma(v, v, nn1);
+                    else nn = fma(v, v, nn);
+                  }
                 }
               }
             }
+            nn += nn1;
+          } else {
+#pragma unroll
+            for (int q = 0; q < kQRRegs; ++q) {
+              if (q < nq) {
+                const int i = j + 1 + lane + 32 * q;
+                if (i < h) a[i] = fma(-wv, ybuf[i], r[q]);
+              }
+            }
           }
-          nn += nn1;
           __syncwarp();
           if (lane == 0) a[j] -= wv;
         } else {
@@ -572,10 +584,14 @@ __device__ __forceinline__ void qr_dsmem_impl(const QRDesc* __restrict__ descs, 
           for (int i = j + 1 + lane; i < h; i += 32) t = fma(ybuf[i], a[i], t);
           t = warp_sum2(t);
           const double wv = tau * (t + a[j]);
-          for (int i = j + 1 + lane; i < h; i += 32) {
-            const double v = fma(-wv, ybuf[i], a[i]);
-            a[i] = v;
-            if (i > j + 1) nn = fma(v, v, nn);
+          if (c == j + 1) {
+            for (int i = j + 1 + lane; i < h; i += 32) {
+              const double v = fma(-wv, ybuf[i], a[i]);
+              a[i] = v;
+              if (i > j + 1) nn = fma(v, v, nn);
+            }
+          } else {
+            for (int i = j + 1 + lane; i < h; i += 32) a[i] = fma(-wv, ybuf[i], a[i]);
           }
           __syncwarp();
           if (lane == 0) a[j] -= wv;
@@ -1028,8 +1044,9 @@ __device__ __forceinline__ void jacobi_dsmem_impl(const JacobiDesc* __restrict__
         const bool a_shrinks = tg > 0.0;
         const bool exact = doit && (a_shrinks ? (tg > 0.5 * al) : (-tg > 0.5 * be));
         const bool any_exact = __any_sync(0xffffffffu, exact);
+        const bool any_doit = __any_sync(0xffffffffu, doit);   // else the warp's pairs are final
         double s0 = 0.0, s1 = 0.0;
-        if (inreg) {
+        if (inreg && any_doit) {
 #pragma unroll
           for (int t = 0; t < kJacobiRegs; ++t) {
             if (t < nreg) {
@@ -1256,8 +1273,9 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
         const bool a_shrinks = tg > 0.0;
         const bool exact = doit && (mine_a == a_shrinks) && (a_shrinks ? (tg > 0.5 * al) : (-tg > 0.5 * be));
         const bool any_exact = __any_sync(0xffffffffu, exact);
+        const bool any_doit = __any_sync(0xffffffffu, doit);
         double s0 = 0.0, s1 = 0.0;
-        if (inreg) {
+        if (inreg && any_doit) {
 #pragma unroll
           for (int u = 0; u < kJacobiRegs; ++u) {
             if (u < nreg) {
@@ -1268,6 +1286,15 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
                 if (u & 1) s1 = fma(v, v, s1);
                 else s0 = fma(v, v, s0);
               }
+            }
+          }
+        } else if (inreg) {
+          // no pair of the warp rotates: carry the own columns over (no arithmetic)
+#pragma unroll
+          for (int u = 0; u < kJacobiRegs; ++u) {
+            if (u < nreg) {
+              const int i = gl + LG * u;
+              if (task && i < q1) dst[i] = src[i];
             }
           }
         } else if (task) {

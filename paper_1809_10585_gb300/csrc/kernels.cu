@@ -71,85 +71,86 @@ __global__ void __launch_bounds__(GT) gemm_kernel(const GemmDesc* __restrict__ d
 
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
-  // Thread layout by the actual width of this tile (ranks are known only on the device, and
-  // most products here multiply by a block of at most 8 columns): 16 x 16 threads with 2 x 2
-  // outputs each, 16 columns x 16 row pairs with 2 x 1, or 8 columns x 32 rows with 1 x 1, so
-  // that the FP64 pipe does not spend its issue slots on padding columns.
-  const int wcols = n - col0;
-  const int mode = wcols <= 8 ? 2 : (wcols <= 16 ? 1 : 0);
-  const int tx = mode == 0 ? threadIdx.x % 16 : (mode == 1 ? threadIdx.x % 16 : threadIdx.x % 8);
-  const int ty = mode == 0 ? threadIdx.x / 16 : (mode == 1 ? threadIdx.x / 16 : threadIdx.x / 8);
-  const int bcols = mode == 0 ? BN : (mode == 1 ? 16 : 8);
-  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  // The outputs of this tile that exist (ma x na: sizes are known only on the device, and most
+  // products here multiply by a block of a few columns) are dealt to the threads in
+  // column-major order, one per thread per pass, up to four passes for a full 32 x 32 tile.
+  // A warp whose outputs all lie beyond ma x na issues nothing, so the FP64 pipe, the limit
+  // of this kernel, spends no instruction on padding rows or columns except in the last warp
+  // of a pass (its idle lanes repeat the last output and do not store).  Two FMA chains per
+  // output (even and odd k) halve the dependent latency.
+  const int ma = min(BM, m - row0), na = min(BN, n - col0);
+  const int nout = ma * na;
+  const int wbase = threadIdx.x & ~31;
+  int oi[4], oj[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int o = min((int)threadIdx.x + GT * u, nout - 1);
+    oj[u] = o / ma;
+    oi[u] = o - oj[u] * ma;
+  }
+  double acc[4][2];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) acc[u][0] = acc[u][1] = 0.0;
   for (int kk = k0; kk < k1; kk += BK) {
+    const int kl = min(BK, k1 - kk);
     for (int e = threadIdx.x; e < BM * BK; e += GT) {
       int i = e % BM, l = e / BM;
       int gi = row0 + i, gl = kk + l;
       double v = 0.0;
-      if (gi < m && gl < k1) {
+      if (i < ma && l < kl) {
         v = d.ta ? masked(d.A, d.lda, gl, gi, d.mska) : masked(d.A, d.lda, gi, gl, d.mska);
       }
       As[l][i] = v;
     }
-    for (int e = threadIdx.x; e < bcols * BK; e += GT) {
+    for (int e = threadIdx.x; e < na * BK; e += GT) {
       int l = e % BK, j = e / BK;
       int gl = kk + l, gj = col0 + j;
       double v = 0.0;
-      if (gj < n && gl < k1) {
+      if (l < kl) {
         v = d.tb ? masked(d.B, d.ldb, gj, gl, d.mskb) : masked(d.B, d.ldb, gl, gj, d.mskb);
       }
       Bs[l][j] = v;
     }
     __syncthreads();
-    if (mode == 0) {
 #pragma unroll
-      for (int l = 0; l < BK; ++l) {
-        double a0 = As[l][ty], a1 = As[l][ty + 16];
-        double b0 = Bs[l][tx], b1 = Bs[l][tx + 16];
-        acc[0][0] = fma(a0, b0, acc[0][0]);
-        acc[0][1] = fma(a0, b1, acc[0][1]);
-        acc[1][0] = fma(a1, b0, acc[1][0]);
-        acc[1][1] = fma(a1, b1, acc[1][1]);
-      }
-    } else if (mode == 1) {
+    for (int u = 0; u < 4; ++u) {
+      if (wbase + GT * u < nout) {                      // warp-uniform
+        const int i = oi[u], j = oj[u];
+        if (kl == BK) {
 #pragma unroll
-      for (int l = 0; l < BK; ++l) {
-        const double b0 = Bs[l][tx];
-        acc[0][0] = fma(As[l][ty], b0, acc[0][0]);
-        acc[1][0] = fma(As[l][ty + 16], b0, acc[1][0]);
-      }
-    } else {
-#pragma unroll
-      for (int l = 0; l < BK; l += 2) {                 // two chains
-        acc[0][0] = fma(As[l][ty], Bs[l][tx], acc[0][0]);
-        acc[1][1] = fma(As[l + 1][ty], Bs[l + 1][tx], acc[1][1]);
+          for (int l = 0; l < BK; l += 2) {
+            acc[u][0] = fma(As[l][i], Bs[l][j], acc[u][0]);
+            acc[u][1] = fma(As[l + 1][i], Bs[l + 1][j], acc[u][1]);
+          }
+        } else {
+          int l = 0;
+          for (; l + 1 < kl; l += 2) {
+            acc[u][0] = fma(As[l][i], Bs[l][j], acc[u][0]);
+            acc[u][1] = fma(As[l + 1][i], Bs[l + 1][j], acc[u][1]);
+          }
+          if (l < kl) acc[u][0] = fma(As[l][i], Bs[l][j], acc[u][0]);
+        }
       }
     }
     __syncthreads();
   }
-  if (mode == 2) {
-    acc[0][0] += acc[1][1];
-    acc[1][1] = 0.0;
-  }
-  const int na = mode == 2 ? 1 : 2, nb = mode == 0 ? 2 : 1;
   double alpha = d.alpha;
   if (d.alpha_ref) alpha *= *d.alpha_ref;
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      int gi = row0 + ty + 16 * a, gj = col0 + tx + 16 * b;
-      if (a < na && b < nb && gi < m && gj < n) {
-        if (to_part) {
-          d.part[(size_t)split * d.m * d.n + gi + (size_t)gj * d.m] = acc[a][b];
-        } else {
-          double* c = d.C + gi + (size_t)gj * d.ldc;
-          double v = alpha * acc[a][b];
-          if (d.beta != 0.0) v = fma(d.beta, *c, v);
-          *c = v;
-        }
+  for (int u = 0; u < 4; ++u) {
+    if ((int)threadIdx.x + GT * u < nout) {
+      const int gi = row0 + oi[u], gj = col0 + oj[u];
+      const double sacc = acc[u][0] + acc[u][1];
+      if (to_part) {
+        d.part[(size_t)split * d.m * d.n + gi + (size_t)gj * d.m] = sacc;
+      } else {
+        double* c = d.C + gi + (size_t)gj * d.ldc;
+        double v = alpha * sacc;
+        if (d.beta != 0.0) v = fma(d.beta, *c, v);
+        *c = v;
       }
     }
+  }
   if (!to_part || d.tile_count == nullptr) return;
   // split-K: the last split to finish this tile sums the partials in split order (the result
   // does not depend on arrival order) and resets the counter for the next use
@@ -168,19 +169,17 @@ __global__ void __launch_bounds__(GT) gemm_kernel(const GemmDesc* __restrict__ d
   for (int sp = 0; sp < d.ksplit; ++sp)
     if (sp * kchunk < k) nsp = sp + 1;
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      int gi = row0 + ty + 16 * a, gj = col0 + tx + 16 * b;
-      if (a < na && b < nb && gi < m && gj < n) {
-        double sacc = 0.0;
-        for (int sp = 0; sp < nsp; ++sp) sacc += __ldcg(&d.part[(size_t)sp * d.m * d.n + gi + (size_t)gj * d.m]);
-        double* c = d.C + gi + (size_t)gj * d.ldc;
-        double v = alpha * sacc;
-        if (d.beta != 0.0) v = fma(d.beta, *c, v);
-        *c = v;
-      }
+  for (int u = 0; u < 4; ++u) {
+    if ((int)threadIdx.x + GT * u < nout) {
+      const int gi = row0 + oi[u], gj = col0 + oj[u];
+      double sacc = 0.0;
+      for (int sp = 0; sp < nsp; ++sp) sacc += __ldcg(&d.part[(size_t)sp * d.m * d.n + gi + (size_t)gj * d.m]);
+      double* c = d.C + gi + (size_t)gj * d.ldc;
+      double v = alpha * sacc;
+      if (d.beta != 0.0) v = fma(d.beta, *c, v);
+      *c = v;
     }
+  }
 }
 
 // Sum split-K partials: C = alpha * sum_s part_s + beta * C.  One block per 256 outputs.
