@@ -370,6 +370,7 @@ def gpu_arm(args):
                 "flops_per_launch": p["flops"] / max(1, p["launches"]),
                 "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (per-SM DFMA rate measured)",
                 "kind_ms": {k: round(v["ms"], 4) for k, v in prof.items()},
+                "kind_gflop": {k: round(v["flops"] / 1e9, 4) for k, v in prof.items()},
                 "kind_share": {k: round(v["ms"] / max(1e-9, sum(x["ms"] for x in prof.values())), 4)
                                for k, v in prof.items()}}
     gpu_launches = sum(v["launches"] for v in prof.values()) * args.steps * nb

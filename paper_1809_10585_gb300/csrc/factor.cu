@@ -905,11 +905,11 @@ __global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __
 
 // One-sided Jacobi with the core held in distributed shared memory: column j lives in the
 // shared memory of CTA j % C.  Each warp rotates 32 / LG column pairs at once, one pair per
-// group of LG lanes (LG = 8, 16 or 32, the smallest with q1 <= LG * kJacobiRegs): the FP64
+// group of LG lanes (LG = 4, 8, 16 or 32, the smallest with q1 <= LG * kJacobiRegs): the FP64
 // instructions that form the rotation (the scarce resource, see jacobi_rotation) are then
 // shared by several pairs, and the dot product needs only log2(LG) shuffle levels.  Control
 // flow stays warp-uniform: a group whose pair is converged, deflated or absent applies the
-// identity and stores nothing.  Pair (a, b) reads and writes both columns through DSMEM; per
+// identity and stores nothing; a warp none of whose pairs rotates skips the application.  Pair (a, b) reads and writes both columns through DSMEM; per
 // round that is one remote load, one remote store and one cluster barrier.  Same pair schedule,
 // thresholds and deflation as jacobi_cluster_kernel.  Columns longer than LG * kJacobiRegs
 // (q1 > 256 for LG = 32) are streamed from shared memory twice instead of held in registers.
@@ -1369,22 +1369,26 @@ __global__ void __launch_bounds__(QT, 2) jacobi_dsmem_kernel(const JacobiDesc* _
   const size_t avail = (size_t)smem_bytes;
   if (q2 <= kJacobiSoloCols && jacobi_owner_bytes(q1, q2, 1) <= avail) {
     if (cg::this_cluster().block_rank() != 0) return;
-    if (q1 <= 8 * kJacobiRegs) jacobi_owner_impl<8, true>(descs, di, flops, q1cap, q2cap);
+    if (q1 <= 4 * kJacobiRegs) jacobi_owner_impl<4, true>(descs, di, flops, q1cap, q2cap);
+    else if (q1 <= 8 * kJacobiRegs) jacobi_owner_impl<8, true>(descs, di, flops, q1cap, q2cap);
     else if (q1 <= 16 * kJacobiRegs) jacobi_owner_impl<16, true>(descs, di, flops, q1cap, q2cap);
     else jacobi_owner_impl<32, true>(descs, di, flops, q1cap, q2cap);
   } else if (C >= 8 && jacobi_owner_bytes(q1, q2, C) <= avail) {
     // owner-computes shortens the round (only loads cross SMs) but computes every pair on both
     // owners: it pays off on large clusters, where a round is latency-bound, not on small ones,
     // where the SM's FP64 issue rate is the limit
-    if (q1 <= 8 * kJacobiRegs) jacobi_owner_impl<8, false>(descs, di, flops, q1cap, q2cap);
+    if (q1 <= 4 * kJacobiRegs) jacobi_owner_impl<4, false>(descs, di, flops, q1cap, q2cap);
+    else if (q1 <= 8 * kJacobiRegs) jacobi_owner_impl<8, false>(descs, di, flops, q1cap, q2cap);
     else if (q1 <= 16 * kJacobiRegs) jacobi_owner_impl<16, false>(descs, di, flops, q1cap, q2cap);
     else jacobi_owner_impl<32, false>(descs, di, flops, q1cap, q2cap);
   } else if (jacobi_dsmem_bytes(q1, q2, C) <= avail) {
-    if (q1 <= 8 * kJacobiRegs) jacobi_dsmem_impl<8>(descs, di, flops, q1cap, q2cap);
+    if (q1 <= 4 * kJacobiRegs) jacobi_dsmem_impl<4>(descs, di, flops, q1cap, q2cap);
+    else if (q1 <= 8 * kJacobiRegs) jacobi_dsmem_impl<8>(descs, di, flops, q1cap, q2cap);
     else if (q1 <= 16 * kJacobiRegs) jacobi_dsmem_impl<16>(descs, di, flops, q1cap, q2cap);
     else jacobi_dsmem_impl<32>(descs, di, flops, q1cap, q2cap);
   } else if (jacobi_owner_bytes(q1, q2, C) <= avail) {
-    if (q1 <= 8 * kJacobiRegs) jacobi_owner_impl<8, false>(descs, di, flops, q1cap, q2cap);
+    if (q1 <= 4 * kJacobiRegs) jacobi_owner_impl<4, false>(descs, di, flops, q1cap, q2cap);
+    else if (q1 <= 8 * kJacobiRegs) jacobi_owner_impl<8, false>(descs, di, flops, q1cap, q2cap);
     else if (q1 <= 16 * kJacobiRegs) jacobi_owner_impl<16, false>(descs, di, flops, q1cap, q2cap);
     else jacobi_owner_impl<32, false>(descs, di, flops, q1cap, q2cap);
   } else {
@@ -1409,7 +1413,7 @@ cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, const int* 
   // Cluster size for this launch: enough CTAs that each has about two warps of pair groups per
   // round (more CTAs only add barrier cost: a round is one dependent chain per pair), at most
   // the context's size, and enough that the columns fit in shared memory.
-  const int ppw = q1cap <= 8 * kJacobiRegs ? 4 : (q1cap <= 16 * kJacobiRegs ? 2 : 1);   // from the caps
+  const int ppw = q1cap <= 4 * kJacobiRegs ? 8 : (q1cap <= 8 * kJacobiRegs ? 4 : (q1cap <= 16 * kJacobiRegs ? 2 : 1));
   const int pairs = (q2cap + 1) / 2;
   cluster = max(1, min(cluster, (pairs + 2 * ppw - 1) / (2 * ppw)));
   while (cluster < cluster_max && jacobi_dsmem_bytes(q1cap, q2cap, cluster) > kJacobiSmemMax) ++cluster;

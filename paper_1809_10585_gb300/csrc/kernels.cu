@@ -35,7 +35,7 @@ __device__ inline double masked(const double* M, int ld, int r, int c, int mask)
   return r == c ? 1.0 : 0.0;
 }
 
-__global__ void __launch_bounds__(GT) gemm_kernel(const GemmDesc* __restrict__ descs, int ndesc,
+__global__ void __launch_bounds__(GT, 4) gemm_kernel(const GemmDesc* __restrict__ descs, int ndesc,
                                                   const int* __restrict__ di, double* flops) {
   // locate descriptor: work items are contiguous per descriptor
   int item = blockIdx.x;
@@ -91,27 +91,40 @@ __global__ void __launch_bounds__(GT) gemm_kernel(const GemmDesc* __restrict__ d
   double acc[4][2];
 #pragma unroll
   for (int u = 0; u < 4; ++u) acc[u][0] = acc[u][1] = 0.0;
+  // Operand tiles pass through registers: the loads of chunk kk + BK are in flight while chunk
+  // kk is multiplied.  Element e = threadIdx.x + GT p (p = 0, 1) of each tile is mapped so that
+  // consecutive threads read consecutive addresses of the stored (possibly transposed) operand.
+  double pa[2], pb[2];
+  auto fetch = [&](int kk) {
+    const int kl = min(BK, k1 - kk);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int e = threadIdx.x + GT * p;
+      const int i = d.ta ? e / BK : e % BM, l = d.ta ? e % BK : e / BM;
+      double v = 0.0;
+      if (i < ma && l < kl)
+        v = d.ta ? masked(d.A, d.lda, kk + l, row0 + i, d.mska) : masked(d.A, d.lda, row0 + i, kk + l, d.mska);
+      pa[p] = v;
+      const int j = d.tb ? e % BN : e / BK, lb = d.tb ? e / BN : e % BK;
+      double w = 0.0;
+      if (j < na && lb < kl)
+        w = d.tb ? masked(d.B, d.ldb, col0 + j, kk + lb, d.mskb) : masked(d.B, d.ldb, kk + lb, col0 + j, d.mskb);
+      pb[p] = w;
+    }
+  };
+  fetch(k0);
   for (int kk = k0; kk < k1; kk += BK) {
     const int kl = min(BK, k1 - kk);
-    for (int e = threadIdx.x; e < BM * BK; e += GT) {
-      int i = e % BM, l = e / BM;
-      int gi = row0 + i, gl = kk + l;
-      double v = 0.0;
-      if (i < ma && l < kl) {
-        v = d.ta ? masked(d.A, d.lda, gl, gi, d.mska) : masked(d.A, d.lda, gi, gl, d.mska);
-      }
-      As[l][i] = v;
-    }
-    for (int e = threadIdx.x; e < na * BK; e += GT) {
-      int l = e % BK, j = e / BK;
-      int gl = kk + l, gj = col0 + j;
-      double v = 0.0;
-      if (l < kl) {
-        v = d.tb ? masked(d.B, d.ldb, gj, gl, d.mskb) : masked(d.B, d.ldb, gl, gj, d.mskb);
-      }
-      Bs[l][j] = v;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int e = threadIdx.x + GT * p;
+      const int i = d.ta ? e / BK : e % BM, l = d.ta ? e % BK : e / BM;
+      As[l][i] = pa[p];
+      const int j = d.tb ? e % BN : e / BK, lb = d.tb ? e / BN : e % BK;
+      if (j < na) Bs[lb][j] = pb[p];
     }
     __syncthreads();
+    if (kk + BK < k1) fetch(kk + BK);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       if (wbase + GT * u < nout) {                      // warp-uniform
