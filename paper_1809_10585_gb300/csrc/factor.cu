@@ -292,7 +292,6 @@ __device__ __forceinline__ void qr_global_impl(const QRDesc* __restrict__ descs,
   const size_t lda = d.lda;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ double red[QW + 1];
-  __shared__ double bc[2];
 
   if (crank == 0 && threadIdx.x == 0 && flops && kmax > 0) {
     if (d.step >= 0) {
@@ -530,7 +529,72 @@ __device__ __forceinline__ void qr_dsmem_impl(const QRDesc* __restrict__ descs, 
     }
     const int first = j + 1;
     const int c0 = first + ((crank - first % C) + C) % C;
-    for (int c = c0 + warp * C; c < w; c += QW * C) {
+    // A warp updates two columns at once, c and c + QW C: one load of the reflector serves both
+    // dot products, and the two warp reductions share their first level (lanes 0-15 finish the
+    // sum of c, lanes 16-31 that of c + QW C), which saves FP64 instructions on short columns.
+    for (int c = c0 + warp * C; c < w; c += 2 * QW * C) {
+      const int c2 = c + QW * C;
+      if (tau != 0.0 && c2 < w) {
+        double* aA = cols + (size_t)(c / C) * ldc;
+        double* aB = cols + (size_t)(c2 / C) * ldc;
+        const int nq = (h - j - 1 + 31) >> 5;     // warp-uniform row slots
+        double tA0 = 0.0, tA1 = 0.0, tB0 = 0.0, tB1 = 0.0;
+        int q = 0;
+        for (; q + 1 < nq; q += 2) {
+          const int i0 = j + 1 + lane + 32 * q, i1 = i0 + 32;   // i0 < h here
+          const double y0 = ybuf[i0];
+          tA0 = fma(y0, aA[i0], tA0);
+          tB0 = fma(y0, aB[i0], tB0);
+          if (i1 < h) {
+            const double y1 = ybuf[i1];
+            tA1 = fma(y1, aA[i1], tA1);
+            tB1 = fma(y1, aB[i1], tB1);
+          }
+        }
+        if (q < nq) {
+          const int i0 = j + 1 + lane + 32 * q;
+          if (i0 < h) {
+            const double y0 = ybuf[i0];
+            tA0 = fma(y0, aA[i0], tA0);
+            tB0 = fma(y0, aB[i0], tB0);
+          }
+        }
+        const bool lo = lane < 16;
+        const double tA = tA0 + tA1, tB = tB0 + tB1;
+        double tm = (lo ? tA : tB) + __shfl_xor_sync(0xffffffffu, lo ? tB : tA, 16);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) tm += __shfl_xor_sync(0xffffffffu, tm, o);
+        double* ac = lo ? aA : aB;
+        const double wv = tau * (tm + ac[j]);
+        const double wA = __shfl_sync(0xffffffffu, wv, 0), wB = __shfl_sync(0xffffffffu, wv, 16);
+        if (c == j + 1) {                         // next pivot: its norm below row j + 1 too
+          double nn = 0.0;
+          for (int qq = 0; qq < nq; ++qq) {
+            const int i = j + 1 + lane + 32 * qq;
+            if (i < h) {
+              const double yv = ybuf[i];
+              const double v = fma(-wA, yv, aA[i]);
+              aA[i] = v;
+              aB[i] = fma(-wB, yv, aB[i]);
+              if (i > j + 1) nn = fma(v, v, nn);
+            }
+          }
+          nn = warp_sum2(nn);
+          if (lane == 0) xn_next = nn;
+        } else {
+          for (int qq = 0; qq < nq; ++qq) {
+            const int i = j + 1 + lane + 32 * qq;
+            if (i < h) {
+              const double yv = ybuf[i];
+              aA[i] = fma(-wA, yv, aA[i]);
+              aB[i] = fma(-wB, yv, aB[i]);
+            }
+          }
+        }
+        __syncwarp();
+        if ((lane & 15) == 0) ac[j] -= wv;       // lane 0: column c, lane 16: column c + QW C
+        continue;
+      }
       double* a = cols + (size_t)(c / C) * ldc;
       double nn = 0.0;
       if (tau != 0.0) {
@@ -603,6 +667,7 @@ __device__ __forceinline__ void qr_dsmem_impl(const QRDesc* __restrict__ descs, 
         nn = warp_sum2(nn);
         if (lane == 0) xn_next = nn;
       }
+      // (tau = 0: no reflector, the second column c + QW C is unchanged and is never the pivot)
     }
     // One cluster barrier per column suffices.  sh_tau of a CTA is rewritten only when it owns
     // a column again, C >= 2 columns later, after every CTA has arrived at the barrier of the
