@@ -24,6 +24,7 @@
 #include <cooperative_groups.h>
 
 #include <cstdio>
+#include <cstdlib>
 
 #include "common.cuh"
 
@@ -57,12 +58,25 @@ __device__ double block_sum(double v, double* red) {
   return red[QW];
 }
 
+// Cluster barrier and distributed-shared-memory mapping, or their one-CTA forms.
+template <bool SOLO>
+__device__ __forceinline__ void csync(cg::cluster_group& cl) {
+  if (SOLO) __syncthreads();
+  else cl.sync();
+}
+template <bool SOLO, class T>
+__device__ __forceinline__ T* rmt(cg::cluster_group& cl, T* p, int rank) {
+  return SOLO ? p : cl.map_shared_rank(p, rank);
+}
+
 // T of the compact WY form from the Householder vectors stored below the diagonal of A
 // (unit diagonal implied): G = Y^T Y (strictly upper part), 16 x 16 diagonal blocks by the
 // column recurrence T(0:i,i) = -tau_i T(0:i,0:i) G(0:i,i), then T12 = -T1 G12 T2 (Sec. 3, Eq. (10))
 // for blocks of doubling size.  A and tau must be final and visible to every CTA of the cluster.
+// `solo`: one CTA alone (block barriers instead of cluster barriers).  Not a template, so that
+// both forms share the one static staging area.
 __device__ void qr_build_T(const QRDesc& d, const double* A, const size_t lda, const int h, const int kmax,
-                           const int C, const int crank, cg::cluster_group& cl) {
+                           const int C, const int crank, cg::cluster_group& cl, const bool solo) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // staging area: 16 x 16 blocks of G per warp for the diagonal blocks, then the two 16 x 32
   // operand tiles of the merges
@@ -75,7 +89,7 @@ __device__ void qr_build_T(const QRDesc& d, const double* A, const size_t lda, c
   const size_t ldg = d.ldg;
   double* T = d.T;
   const size_t ldt = d.ldt;
-  cl.sync();   // all columns final
+  if (solo) __syncthreads(); else cl.sync();   // all columns final
   {
     // G in 4 x 4 tiles of (i, jj) column blocks, one warp per tile: every lane walks its share of
     // the rows once for 16 dot products (16 FMA per 8 loads instead of 1 per 2), then the 16 sums
@@ -147,7 +161,7 @@ __device__ void qr_build_T(const QRDesc& d, const double* A, const size_t lda, c
       if (i > jj) T[i + jj * ldt] = 0.0;
     }
   }
-  cl.sync();
+  if (solo) __syncthreads(); else cl.sync();
   {
     // Diagonal 16 x 16 blocks, one warp per block: the block of G is staged in shared memory and
     // lane l keeps row l of the block of T in registers, so the column recurrence runs without
@@ -197,7 +211,7 @@ __device__ void qr_build_T(const QRDesc& d, const double* A, const size_t lda, c
     if (s < 32) {
       // 16 x 16 blocks: one output per thread is cheaper than a padded 32 x 32 tile
       const long tid = (long)crank * QT + threadIdx.x, nt = (long)C * QT;
-      cl.sync();
+      if (solo) __syncthreads(); else cl.sync();
       for (long e = tid; e < (long)npair * s * s; e += nt) {
         const int q = (int)(e / ((long)s * s)), rem = (int)(e % ((long)s * s));
         const int i = rem % s, jj = rem / s, a = 2 * q * s, b = a + s;
@@ -206,7 +220,7 @@ __device__ void qr_build_T(const QRDesc& d, const double* A, const size_t lda, c
         for (int l = i; l < s; ++l) acc = fma(__ldcg(&T[(a + i) + (size_t)(a + l) * ldt]), __ldcg(&G[(a + l) + (size_t)(b + jj) * ldg]), acc);
         G[(b + jj) + (size_t)(a + i) * ldg] = acc;
       }
-      cl.sync();
+      if (solo) __syncthreads(); else cl.sync();
       for (long e = tid; e < (long)npair * s * s; e += nt) {
         const int q = (int)(e / ((long)s * s)), rem = (int)(e % ((long)s * s));
         const int i = rem % s, jj = rem / s, a = 2 * q * s, b = a + s;
@@ -219,7 +233,7 @@ __device__ void qr_build_T(const QRDesc& d, const double* A, const size_t lda, c
     }
     const int tpd = (s + 31) / 32;                        // tiles per dimension of one pair
     for (int pass = 0; pass < 2; ++pass) {
-      cl.sync();
+      if (solo) __syncthreads(); else cl.sync();
       for (int tile = crank; tile < npair * tpd * tpd; tile += C) {
         const int q = tile / (tpd * tpd), rem = tile % (tpd * tpd);
         const int i0 = 32 * (rem % tpd), j0 = 32 * (rem / tpd);
@@ -428,7 +442,7 @@ __device__ __forceinline__ void qr_global_impl(const QRDesc* __restrict__ descs,
     if (sp != 0.0)
       for (int i = kmax + threadIdx.x; i < h; i += QT) A[i + (kmax - 1) * lda] = __ldcg(&A[i + (kmax - 1) * lda]) * sp;
   }
-  qr_build_T(d, A, lda, h, kmax, C, crank, cl);
+  qr_build_T(d, A, lda, h, kmax, C, crank, cl, false);
 }
 
 __global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __restrict__ descs,
@@ -436,7 +450,7 @@ __global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __
 
 __global__ void __launch_bounds__(QT, 2) jacobi_dsmem_kernel(const JacobiDesc* __restrict__ descs,
                                                           const int* __restrict__ di, double* flops,
-                                                          int q1cap, int q2cap, int smem_bytes);
+                                                          int q1cap, int q2cap, int smem_bytes, int solo_cols);
 constexpr size_t kJacobiSmemMax = 200 * 1024;
 
 
@@ -447,11 +461,12 @@ constexpr size_t kJacobiSmemMax = 200 * 1024;
 // that updates the next pivot also returns that column's norm).  The factored columns are
 // written back to global memory and T is built as in the global-memory form.  The layout
 // follows the actual size h x w: `nloc` slots of h doubles and a reflector buffer of h.
+template <bool SOLO>
 __device__ __forceinline__ void qr_dsmem_impl(const QRDesc* __restrict__ descs, const int* __restrict__ di,
                                               double* flops, int h, int w, double* qsm) {
   cg::cluster_group cl = cg::this_cluster();
-  const int C = (int)cl.num_blocks();
-  const int crank = (int)cl.block_rank();
+  const int C = SOLO ? 1 : (int)cl.num_blocks();
+  const int crank = SOLO ? 0 : (int)cl.block_rank();
   const QRDesc& d = descs[blockIdx.y];
   const int kmax = min(h, w);
   double* A = d.A;
@@ -486,7 +501,7 @@ __device__ __forceinline__ void qr_dsmem_impl(const QRDesc* __restrict__ descs, 
     if (c >= w) break;
     for (int i = threadIdx.x; i < h; i += QT) cols[(size_t)sl * ldc + i] = A[i + (size_t)c * lda];
   }
-  cl.sync();                                             // all CTAs running before any DSMEM access
+  csync<SOLO>(cl);                                       // all CTAs running before any DSMEM access
   if (crank == 0 && kmax > 0) {
     double s = 0.0;
     for (int i = 1 + threadIdx.x; i < h; i += QT) s = fma(cols[i], cols[i], s);
@@ -520,9 +535,12 @@ __device__ __forceinline__ void qr_dsmem_impl(const QRDesc* __restrict__ descs, 
       if (scal != 0.0)
         for (int i = j + 1 + threadIdx.x; i < h; i += QT) cj[i] *= scal;
     }
-    cl.sync();
-    const double tau = *cl.map_shared_rank(&sh_tau, owner);
-    if (tau != 0.0) {
+    csync<SOLO>(cl);
+    const double tau = *rmt<SOLO>(cl, &sh_tau, owner);
+    const double* yref = ybuf;                         // the reflector of column j
+    if (SOLO) {
+      yref = cols + (size_t)j * ldc;                   // local, and only read until the next step
+    } else if (tau != 0.0) {
       const double* yj = cl.map_shared_rank(cols, owner) + (size_t)(j / C) * ldc;
       for (int i = j + 1 + threadIdx.x; i < h; i += QT) ybuf[i] = yj[i];
       __syncthreads();
@@ -542,11 +560,11 @@ __device__ __forceinline__ void qr_dsmem_impl(const QRDesc* __restrict__ descs, 
         int q = 0;
         for (; q + 1 < nq; q += 2) {
           const int i0 = j + 1 + lane + 32 * q, i1 = i0 + 32;   // i0 < h here
-          const double y0 = ybuf[i0];
+          const double y0 = yref[i0];
           tA0 = fma(y0, aA[i0], tA0);
           tB0 = fma(y0, aB[i0], tB0);
           if (i1 < h) {
-            const double y1 = ybuf[i1];
+            const double y1 = yref[i1];
             tA1 = fma(y1, aA[i1], tA1);
             tB1 = fma(y1, aB[i1], tB1);
           }
@@ -554,7 +572,7 @@ __device__ __forceinline__ void qr_dsmem_impl(const QRDesc* __restrict__ descs, 
         if (q < nq) {
           const int i0 = j + 1 + lane + 32 * q;
           if (i0 < h) {
-            const double y0 = ybuf[i0];
+            const double y0 = yref[i0];
             tA0 = fma(y0, aA[i0], tA0);
             tB0 = fma(y0, aB[i0], tB0);
           }
@@ -572,7 +590,7 @@ __device__ __forceinline__ void qr_dsmem_impl(const QRDesc* __restrict__ descs, 
           for (int qq = 0; qq < nq; ++qq) {
             const int i = j + 1 + lane + 32 * qq;
             if (i < h) {
-              const double yv = ybuf[i];
+              const double yv = yref[i];
               const double v = fma(-wA, yv, aA[i]);
               aA[i] = v;
               aB[i] = fma(-wB, yv, aB[i]);
@@ -585,7 +603,7 @@ __device__ __forceinline__ void qr_dsmem_impl(const QRDesc* __restrict__ descs, 
           for (int qq = 0; qq < nq; ++qq) {
             const int i = j + 1 + lane + 32 * qq;
             if (i < h) {
-              const double yv = ybuf[i];
+              const double yv = yref[i];
               aA[i] = fma(-wA, yv, aA[i]);
               aB[i] = fma(-wB, yv, aB[i]);
             }
@@ -608,8 +626,8 @@ __device__ __forceinline__ void qr_dsmem_impl(const QRDesc* __restrict__ descs, 
               const int i = j + 1 + lane + 32 * q;
               r[q] = i < h ? a[i] : 0.0;
               if (i < h) {
-                if (q & 1) t1 = fma(ybuf[i], r[q], t1);
-                else t0 = fma(ybuf[i], r[q], t0);
+                if (q & 1) t1 = fma(yref[i], r[q], t1);
+                else t0 = fma(yref[i], r[q], t0);
               }
             }
           }
@@ -622,7 +640,7 @@ __device__ __forceinline__ void qr_dsmem_impl(const QRDesc* __restrict__ descs, 
               if (q < nq) {
                 const int i = j + 1 + lane + 32 * q;
                 if (i < h) {
-                  const double v = fma(-wv, ybuf[i], r[q]);
+                  const double v = fma(-wv, yref[i], r[q]);
                   a[i] = v;
                   if (i > j + 1) {
                     if (q & 1) nn1 = fma(v, v, nn1);
@@ -637,7 +655,7 @@ __device__ __forceinline__ void qr_dsmem_impl(const QRDesc* __restrict__ descs, 
             for (int q = 0; q < kQRRegs; ++q) {
               if (q < nq) {
                 const int i = j + 1 + lane + 32 * q;
-                if (i < h) a[i] = fma(-wv, ybuf[i], r[q]);
+                if (i < h) a[i] = fma(-wv, yref[i], r[q]);
               }
             }
           }
@@ -645,17 +663,17 @@ __device__ __forceinline__ void qr_dsmem_impl(const QRDesc* __restrict__ descs, 
           if (lane == 0) a[j] -= wv;
         } else {
           double t = 0.0;
-          for (int i = j + 1 + lane; i < h; i += 32) t = fma(ybuf[i], a[i], t);
+          for (int i = j + 1 + lane; i < h; i += 32) t = fma(yref[i], a[i], t);
           t = warp_sum2(t);
           const double wv = tau * (t + a[j]);
           if (c == j + 1) {
             for (int i = j + 1 + lane; i < h; i += 32) {
-              const double v = fma(-wv, ybuf[i], a[i]);
+              const double v = fma(-wv, yref[i], a[i]);
               a[i] = v;
               if (i > j + 1) nn = fma(v, v, nn);
             }
           } else {
-            for (int i = j + 1 + lane; i < h; i += 32) a[i] = fma(-wv, ybuf[i], a[i]);
+            for (int i = j + 1 + lane; i < h; i += 32) a[i] = fma(-wv, yref[i], a[i]);
           }
           __syncwarp();
           if (lane == 0) a[j] -= wv;
@@ -680,7 +698,7 @@ __device__ __forceinline__ void qr_dsmem_impl(const QRDesc* __restrict__ descs, 
     if (c >= w) break;
     for (int i = threadIdx.x; i < h; i += QT) A[i + (size_t)c * lda] = cols[(size_t)sl * ldc + i];
   }
-  qr_build_T(d, A, lda, h, kmax, C, crank, cl);   // starts with a cluster barrier
+  qr_build_T(d, A, lda, h, kmax, C, crank, cl, SOLO);   // starts with a barrier
 }
 
 // Bytes of shared memory of the distributed form for an h x w matrix on C CTAs.
@@ -694,16 +712,23 @@ __host__ __device__ inline size_t qr_dsmem_bytes(int h, int w, int cluster) {
 // the global-memory form otherwise (reflector staged in the same shared memory).
 __global__ void __launch_bounds__(QT) qr_dsmem_kernel(const QRDesc* __restrict__ descs,
                                                       const int* __restrict__ di, double* flops,
-                                                      int hcap, int wcap, int smem_bytes) {
+                                                      int hcap, int wcap, int smem_bytes, int solo_cols) {
   const QRDesc& d = descs[blockIdx.y];
   const int h = min(dimv(d.h, d.href, di), hcap), w = min(dimv(d.w, d.wref, di), wcap);
   const int C = (int)cg::this_cluster().num_blocks();
   extern __shared__ double qsm[];
-  if (qr_dsmem_bytes(h, w, C) <= (size_t)smem_bytes) qr_dsmem_impl(descs, di, flops, h, w, qsm);
-  else qr_global_impl(descs, di, flops, qsm, smem_bytes / (int)sizeof(double));
+  if (w <= solo_cols && qr_dsmem_bytes(h, w, 1) <= (size_t)smem_bytes) {
+    if (cg::this_cluster().block_rank() != 0) return;   // one CTA; no cluster barrier follows
+    qr_dsmem_impl<true>(descs, di, flops, h, w, qsm);
+  } else if (qr_dsmem_bytes(h, w, C) <= (size_t)smem_bytes) {
+    qr_dsmem_impl<false>(descs, di, flops, h, w, qsm);
+  } else {
+    qr_global_impl(descs, di, flops, qsm, smem_bytes / (int)sizeof(double));
+  }
 }
 
 constexpr size_t kQRSmemMax = 200 * 1024;
+constexpr int kQRSoloCols = 32;
 
 // Largest cluster size both cluster kernels can be launched with (16 needs the non-portable
 // attribute and enough SMs per GPC), probed once per process; attributes are set here, never
@@ -766,7 +791,11 @@ cudaError_t launch_qr(const QRDesc* h, int n, QRDesc* d, const int* devints, dou
   // the actual sizes
   const size_t smem = std::min(qr_dsmem_bytes(hcap, wcap, cluster), std::min(kQRSmemMax, smem_cap));
   cfg.dynamicSmemBytes = smem;
-  return cudaLaunchKernelEx(&cfg, qr_dsmem_kernel, (const QRDesc*)d, devints, flops, hcap, wcap, (int)smem);
+  // matrices of at most this many columns are factored by one CTA of the cluster (the others
+  // exit at once): no cluster barrier per column; more of them while other factorizations
+  // share the SMs
+  const int solo = smem_cap < kQRSmemMax ? 2 * kQRSoloCols : kQRSoloCols;
+  return cudaLaunchKernelEx(&cfg, qr_dsmem_kernel, (const QRDesc*)d, devints, flops, hcap, wcap, (int)smem, solo);
 }
 
 // --------------------------------------------------------------------------------- Jacobi
@@ -1167,17 +1196,6 @@ __device__ __forceinline__ void jacobi_dsmem_impl(const JacobiDesc* __restrict__
   cl.sync();   // no CTA may exit while others still access its shared memory
 }
 
-// Cluster barrier and distributed-shared-memory mapping, or their one-CTA forms.
-template <bool SOLO>
-__device__ __forceinline__ void csync(cg::cluster_group& cl) {
-  if (SOLO) __syncthreads();
-  else cl.sync();
-}
-template <bool SOLO, class T>
-__device__ __forceinline__ T* rmt(cg::cluster_group& cl, T* p, int rank) {
-  return SOLO ? p : cl.map_shared_rank(p, rank);
-}
-
 // One-sided Jacobi, owner-computes form.  Column j lives in the shared memory of CTA j % C, in
 // two buffers: round r reads buffer r & 1 and writes buffer (r + 1) & 1.  For every pair (a, b)
 // of a round, the CTA owning a and the CTA owning b both form the same rotation from the same
@@ -1422,7 +1440,7 @@ constexpr int kJacobiSoloCols = 32;   // cores up to this many columns run on on
 // on the device; every CTA of the cluster reads the same descriptor, so the choice is uniform).
 __global__ void __launch_bounds__(QT, 2) jacobi_dsmem_kernel(const JacobiDesc* __restrict__ descs,
                                                           const int* __restrict__ di, double* flops,
-                                                          int q1cap, int q2cap, int smem_bytes) {
+                                                          int q1cap, int q2cap, int smem_bytes, int solo_cols) {
   // The form is chosen from the core's actual size (every CTA of the cluster reads the same
   // descriptor): one CTA for small cores; on clusters of 8 or more CTAs owner-computes when its
   // two column buffers fit in the shared memory of the launch; else remote-store when one buffer
@@ -1432,7 +1450,7 @@ __global__ void __launch_bounds__(QT, 2) jacobi_dsmem_kernel(const JacobiDesc* _
   const int q2 = min(dimv(d.q2, d.q2ref, di), q2cap);
   const int C = (int)cg::this_cluster().num_blocks();
   const size_t avail = (size_t)smem_bytes;
-  if (q2 <= kJacobiSoloCols && jacobi_owner_bytes(q1, q2, 1) <= avail) {
+  if (q2 <= solo_cols && jacobi_owner_bytes(q1, q2, 1) <= avail) {
     if (cg::this_cluster().block_rank() != 0) return;
     if (q1 <= 4 * kJacobiRegs) jacobi_owner_impl<4, true>(descs, di, flops, q1cap, q2cap);
     else if (q1 <= 8 * kJacobiRegs) jacobi_owner_impl<8, true>(descs, di, flops, q1cap, q2cap);
@@ -1499,8 +1517,11 @@ cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, const int* 
   const size_t smem2 = std::min(jacobi_owner_bytes(q1cap, q2cap, cluster), std::min(kJacobiSmemMax, smem_cap));
   if (q2cap <= kJacobiMaxCols) {
     cfg.dynamicSmemBytes = smem2;
+    // cores of at most this many columns run on one CTA; more of them while other factorizations
+    // share the SMs (throughput over latency)
+    const int solo = smem_cap < kJacobiSmemMax ? 2 * kJacobiSoloCols : kJacobiSoloCols;
     return cudaLaunchKernelEx(&cfg, jacobi_dsmem_kernel, (const JacobiDesc*)d, devints, flops, q1cap, q2cap,
-                              (int)smem2);
+                              (int)smem2, solo);
   }
   return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel, (const JacobiDesc*)d, devints, flops);
 }
