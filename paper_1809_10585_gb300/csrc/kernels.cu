@@ -37,12 +37,28 @@ __device__ inline double masked(const double* M, int ld, int r, int c, int mask)
 
 __global__ void __launch_bounds__(GT, 4) gemm_kernel(const GemmDesc* __restrict__ descs, int ndesc,
                                                   const int* __restrict__ di, double* flops) {
-  // locate descriptor: work items are contiguous per descriptor
-  int item = blockIdx.x;
-  int lo = 0, hi = ndesc - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (descs[mid].work0 <= item) lo = mid; else hi = mid - 1;
+  // Locate the descriptor (work items are contiguous per descriptor, work0 strictly increasing):
+  // each warp samples 32 first items at stride s = ceil(ndesc / 32) in one load and votes, then
+  // scans the chosen stretch of s descriptors 32 at a time, so a CTA waits for two dependent
+  // loads instead of log2(ndesc) of a binary search (most CTAs here live only a few us).
+  const int item = blockIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int stride = (ndesc + 31) >> 5;
+  int lo;
+  {
+    const int idx = lane * stride;
+    const bool le = idx < ndesc && __ldg(&descs[idx].work0) <= item;
+    lo = (31 - __clz(__ballot_sync(0xffffffffu, le))) * stride;   // lane 0 always votes yes
+  }
+  if (stride > 1) {
+    const int end = min(lo + stride, ndesc);
+    for (int b = lo; b < end; b += 32) {
+      const int idx = b + lane;
+      const bool le = idx < end && __ldg(&descs[idx].work0) <= item;
+      const unsigned m = __ballot_sync(0xffffffffu, le);
+      lo = b + 31 - __clz(m);                         // bit 0 is set: descs[b].work0 <= item
+      if (m != 0xffffffffu) break;
+    }
   }
   const GemmDesc& d = descs[lo];
   int local = item - d.work0;
