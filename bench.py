@@ -59,6 +59,29 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_seeds(rank, nb):
+    """Seeds of the matrices one rank factors per step: replicas only, every rank its own
+    disjoint set of nb matrices, no data shared between ranks."""
+    return [rank * nb + i for i in range(nb)]
+
+
+def max_over_ranks(x, device="cpu"):
+    """The largest x over the ranks of the default process group (x itself without one): the
+    timed region of the slowest rank sets the whole job's time."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws, nb, steps, seconds):
+    """Factorizations per second of the whole job: every rank factors nb matrices per step."""
+    return ws * nb * steps / seconds
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
 
@@ -228,7 +251,7 @@ def gpu_arm(args):
     BUILD.build()
 
     nb = max(1, args.batch)
-    inps = [make_input(rank * nb + i) for i in range(nb)]
+    inps = [make_input(sd) for sd in rank_seeds(rank, nb)]
     inp = inps[0]
     ctx = B.Context(local)
     stream = torch.cuda.Stream()
@@ -300,17 +323,13 @@ def gpu_arm(args):
         sms = sum(a.elapsed_time(b) for a, b in sev) / args.steps
         single = {"value": 1e3 / sms, "unit": UNIT, "ms_per_step": sms, "cluster": cmax}
         ctx.cluster = ccl
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, "cuda")
     for m in mats:
         st, _ = m.status()
         if st != 0:
             raise RuntimeError(f"factorization status {st}")
     ms_per_step = ms_total / args.steps
-    value = ws * nb * args.steps / (ms_total / 1e3)
+    value = whole_job_rate(ws, nb, args.steps, ms_total / 1e3)
 
     # ---------------------------------------------------------------- end to end (host buffers)
     def pinned_like(a):
@@ -353,12 +372,8 @@ def gpu_arm(args):
             e2e_step()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": ws * nb * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+    e2e_s = max_over_ranks(e2e_s, "cuda")
+    e2e = {"value": whole_job_rate(ws, nb, e2e_steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(out_bytes), "steps": e2e_steps}
 
     # ---------------------------------------------------------------- roofline of the top kernel
