@@ -62,7 +62,8 @@ int hodlr_ctx_set_cluster(hodlr_ctx* ctx, int cluster);
 int hodlr_ctx_get_cluster(hodlr_ctx* ctx, int* cluster);
 /* Number of factorizations the caller runs on the GPU at the same time through this and other
  * contexts (default 1).  Above 1, the QR and Jacobi kernels reserve less shared memory per CTA
- * (two CTAs per SM instead of one), so that CTAs of different factorizations share SMs;
+ * (two CTAs per SM instead of one), so that CTAs of different factorizations share SMs, and run
+ * QRs of up to 64 columns and Jacobi cores of up to 64 columns on one CTA (32 otherwise);
  * hodlr_qr_batched applies this by itself for the duration of a batch of two or more.  Results
  * depend on the setting at the level of rounding only (a matrix whose columns no longer fit in
  * the cluster's shared memory is factored in the global-memory form).  Graphs captured earlier
@@ -134,8 +135,9 @@ int hodlr_qr_profile(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm, dou
 
 /*
  * hodlr_qr_batched — cross-matrix batching: factor `count` distinct matrices A[0..count-1]
- * (any partitions, ranks and sizes), each as hodlr_qr(tol, anorm) would, concurrently on the
- * device.  Each matrix runs on its own pair of streams owned by the context; the pairs are
+ * (any partitions, ranks and sizes), each as hodlr_qr(tol, anorm) would up to rounding (while
+ * the batch runs, the kernels take the forms of hodlr_ctx_set_concurrency(count)), concurrently
+ * on the device.  Each matrix runs on its own pair of streams owned by the context; the pairs are
  * forked from and joined back into the context's stream, so later work on that stream sees
  * all results.  Asynchronous.  HODLR_EINVAL if a pointer repeats.
  *

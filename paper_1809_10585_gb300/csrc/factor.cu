@@ -1434,7 +1434,8 @@ __host__ __device__ inline size_t jacobi_owner_bytes(int q1cap, int q2cap, int c
   return 2 * nloc * (q1cap + 1) * sizeof(double) + (size_t)q2cap * sizeof(double) +
          ((size_t)q2cap + nloc) * sizeof(int) + 64;
 }
-constexpr int kJacobiSoloCols = 32;   // cores up to this many columns run on one CTA
+constexpr int kJacobiSoloCols = 32;   // cores up to this many columns run on one CTA (twice as
+                                      // many while factorizations share the SMs)
 
 // Lane-group width from the actual column length of this cluster's core (ranks are known only
 // on the device; every CTA of the cluster reads the same descriptor, so the choice is uniform).
