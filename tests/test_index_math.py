@@ -1,0 +1,191 @@
+"""CPU checks of the index arithmetic and warp-exchange patterns of the CUDA kernels.
+
+Each check restates, in plain Python over a 32-lane warp, one mapping the kernels rely on and
+verifies its invariant on every size the kernels meet: that each output, operand element,
+column pair or partial sum is produced exactly once and lands where the kernel reads it.  These
+are the properties that make the kernels' accesses stay in bounds; the parity tests then check
+the numbers on the GPU."""
+import bisect
+import itertools
+
+import numpy as np
+
+GT, BM, BN, BK = 256, 32, 32, 16           # gemm_kernel: threads, tile rows, tile columns, k chunk
+
+
+def shfl_xor(vals, o):
+    return [vals[l ^ o] for l in range(32)]
+
+
+def test_gemm_outputs_dealt_densely():
+    """gemm_kernel: the ma x na outputs of a tile go to threads in column-major order, one per
+    thread per pass; only warps holding an output issue the FMA chain, only lanes holding one
+    store, and the wasted lanes of a pass are those of its last warp."""
+    for ma in range(1, BM + 1):
+        for na in range(1, BN + 1):
+            nout = ma * na
+            stored = []
+            for u in range(4):
+                busy = 0
+                for t in range(GT):
+                    o = min(t + GT * u, nout - 1)
+                    j = o // ma
+                    i = o - j * ma
+                    assert 0 <= i < ma and 0 <= j < na
+                    computes = (t & ~31) + GT * u < nout
+                    if computes:
+                        busy += 1
+                    if t + GT * u < nout:
+                        assert computes
+                        stored.append((i, j))
+                assert busy - max(0, min(GT, nout - GT * u)) < 32
+            assert sorted(stored) == [(i, j) for i in range(ma) for j in range(na)]
+
+
+def test_gemm_operand_tiles_covered_once_and_coalesced():
+    """gemm_kernel prefetch: element e = t + 256 p (p = 0, 1) of the 32 x 16 A tile and the
+    16 x 32 B tile; consecutive threads read consecutive addresses of the stored operand."""
+    for ta in (0, 1):
+        cells = []
+        for e in range(2 * GT):
+            i, l = (e // BK, e % BK) if ta else (e % BM, e // BM)
+            cells.append((i, l))
+        assert sorted(cells) == [(i, l) for i in range(BM) for l in range(BK)]
+        lda = 1000
+        for w in range(0, 2 * GT, 32):          # a warp's 32 consecutive elements
+            addr = [(l + i * lda) if ta else (i + l * lda) for i, l in cells[w:w + 32]]
+            runs = sum(1 for a, b in zip(addr, addr[1:]) if b != a + 1)
+            assert runs <= 1                     # at most two contiguous runs per warp
+    for tb in (0, 1):
+        cells = []
+        for e in range(2 * GT):
+            j, lb = (e % BN, e // BN) if tb else (e // BK, e % BK)
+            cells.append((j, lb))
+        assert sorted(cells) == [(j, l) for j in range(BN) for l in range(BK)]
+
+
+def _vote_search(work0, item):
+    """gemm_kernel descriptor lookup: a 32-lane vote at stride s, then a scan of s entries."""
+    nd = len(work0)
+    stride = (nd + 31) >> 5
+    m = 0
+    for lane in range(32):
+        idx = lane * stride
+        if idx < nd and work0[idx] <= item:
+            m |= 1 << lane
+    lo = (m.bit_length() - 1) * stride            # lane 0 always votes yes
+    if stride > 1:
+        end = min(lo + stride, nd)
+        b = lo
+        while b < end:
+            m = 0
+            for lane in range(32):
+                idx = b + lane
+                if idx < end and work0[idx] <= item:
+                    m |= 1 << lane
+            lo = b + m.bit_length() - 1           # m == 0 gives b - 1: the previous chunk's last
+            if m != 0xFFFFFFFF:
+                break
+            b += 32
+    return lo
+
+
+def test_gemm_descriptor_vote_equals_bisection():
+    rng = np.random.default_rng(3)
+    for nd in list(range(1, 70)) + [1023, 1024, 1025, 2000]:
+        work = rng.integers(1, 9, size=nd)
+        work0 = [0] + list(np.cumsum(work)[:-1])
+        total = int(np.sum(work))
+        items = range(total) if total < 600 else rng.integers(0, total, size=600)
+        for item in items:
+            assert _vote_search(work0, int(item)) == bisect.bisect_right(work0, int(item)) - 1
+
+
+def test_qr_two_column_reduction():
+    """qr_dsmem_kernel pair update: one exchange at offset 16 moves column A's partial sums to
+    lanes 0-15 and column B's to lanes 16-31, then four levels finish both sums at once."""
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        tA, tB = rng.standard_normal(32), rng.standard_normal(32)
+        lo = [l < 16 for l in range(32)]
+        send = [tB[l] if lo[l] else tA[l] for l in range(32)]
+        recv = shfl_xor(send, 16)
+        tm = [(tA[l] if lo[l] else tB[l]) + recv[l] for l in range(32)]
+        for o in (8, 4, 2, 1):
+            other = shfl_xor(tm, o)
+            tm = [tm[l] + other[l] for l in range(32)]
+        assert np.allclose(tm[:16], tA.sum(), rtol=1e-13) and np.allclose(tm[16:], tB.sum(), rtol=1e-13)
+
+
+def test_T_build_halving_exchange():
+    """qr_build_T: each lane holds 16 partial sums of a 4 x 4 block of G; after halving
+    exchanges at offsets 16, 8, 4, 2 and a final add at offset 1, lane l holds entry q(l)
+    summed over all lanes, q(l) = 8 b4 + 4 b3 + 2 b2 + b1 of l's bits."""
+    rng = np.random.default_rng(7)
+    acc = [list(rng.standard_normal(16)) for _ in range(32)]
+    total = np.sum(np.array(acc), axis=0)
+    for o, half in ((16, 8), (8, 4), (4, 2), (2, 1)):
+        new = []
+        for l in range(32):
+            hi = bool(l & o)
+            row = acc[l][:]
+            partner = acc[l ^ o]
+            for q in range(half):
+                send_p = partner[q] if (l ^ o) & o else partner[q + half]   # what the partner sends
+                keep = row[q + half] if hi else row[q]
+                row[q] = keep + send_p
+            new.append(row)
+        acc = new
+    final = [acc[l][0] + acc[l ^ 1][0] for l in range(32)]
+    for l in range(32):
+        q = ((l >> 4) & 1) * 8 + ((l >> 3) & 1) * 4 + ((l >> 2) & 1) * 2 + ((l >> 1) & 1)
+        assert np.isclose(final[l], total[q], rtol=1e-12)
+
+
+def _rr_pair(r, i, P):
+    if i == 0:
+        return P - 1, r
+    m = P - 1
+    a = r + i
+    a -= m if a >= m else 0
+    b = r - i
+    b += m if b < 0 else 0
+    return a, b
+
+
+def test_jacobi_round_robin_schedules():
+    """rr_pair (remote-store and global forms) and the owner form's partner y = 2r - x mod m:
+    every round pairs all P players, and the P - 1 rounds meet every pair exactly once."""
+    for P in range(2, 42, 2):
+        m = P - 1
+        seen = set()
+        for r in range(P - 1):
+            players = []
+            for i in range(P // 2):
+                a, b = _rr_pair(r, i, P)
+                assert 0 <= a < P and 0 <= b < P and a != b
+                players += [a, b]
+                seen.add((min(a, b), max(a, b)))
+            assert sorted(players) == list(range(P))
+            # owner form: each player finds its partner alone, consistently with rr_pair
+            partner = {}
+            for x in range(P):
+                y = 2 * r - x
+                y += m if y < 0 else 0
+                y -= m if y >= m else 0
+                y = r if x == m else (m if x == r else y)
+                partner[x] = y
+            for x in range(P):
+                assert partner[partner[x]] == x and partner[x] != x
+            pairs_owner = {(min(x, y), max(x, y)) for x, y in partner.items()}
+            pairs_rr = {(min(*_rr_pair(r, i, P)), max(*_rr_pair(r, i, P))) for i in range(P // 2)}
+            assert pairs_owner == pairs_rr
+        assert seen == set(itertools.combinations(range(P), 2))
+
+
+def test_jacobi_packed_active_columns():
+    """jacobi owner form: act[x] = (slot << 5) | owner CTA, with owner = j % C < 32."""
+    for C in (1, 2, 4, 8, 16):
+        for j in range(4096):
+            p = ((j // C) << 5) | (j % C)
+            assert (p & 31) == j % C and (p >> 5) == j // C and (p >> 5) * C + (p & 31) == j
