@@ -47,9 +47,25 @@ WORKLOAD = "hodlr_qr_n8192_nmin256_k10_colscaled1e-14_tol1e-12"
 N, NMIN, K, DECADES, TOL = 8192, 256, 10, 14.0, 1e-12
 RANK_CAP = 128
 BATCH_CLUSTER = 4          # default cluster size when several matrices are factored per step
-# FP64 ALU peak from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
-# (the DFMA rate of one SM, 2 per clock, was measured with an FMA throughput loop)
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 roofline denominator: the DFMA rate measured on this GPU model by hodlr_fp64_peak
+# (`python bench.py --peaks`), recorded with its command and clocks in this file
+PEAK_RECORD = os.path.join("profiles", "fp64_peak.md")
+
+
+def recorded_fp64_peak():
+    """(DFMA TFLOP/s, DMMA TFLOP/s) from the committed measurement record, or None."""
+    import re
+    path = os.path.join(ROOT, PEAK_RECORD)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        m = re.match(r"^\s*(dfma_tflops|dmma_tflops):\s*([0-9.eE+-]+)\s*$", line)
+        if m:
+            vals[m.group(1)] = float(m.group(2))
+    if "dfma_tflops" not in vals:
+        return None
+    return vals["dfma_tflops"], vals.get("dmma_tflops")
 
 
 def dist_env():
@@ -377,6 +393,14 @@ def gpu_arm(args):
            "d2h_bytes_per_step": int(out_bytes), "steps": e2e_steps}
 
     # ---------------------------------------------------------------- roofline of the top kernel
+    live = B.fp64_peak(local)
+    rec = recorded_fp64_peak()
+    if rec is not None:
+        peak = rec[0]
+        peak_source = f"{PEAK_RECORD}: DFMA throughput measured on GB300 by hodlr_fp64_peak (CUDA events)"
+    else:
+        peak = live["dfma"]
+        peak_source = "DFMA throughput measured in this run by hodlr_fp64_peak (CUDA events)"
     prof = M.qr_profile(TOL, 0.0)
     flops_total = M.flops()["total"]
     top = max((k for k in prof if prof[k]["flops"] > 0), key=lambda k: prof[k]["ms"])
@@ -386,14 +410,14 @@ def gpu_arm(args):
     # algorithmic flops over its event-timed duration
     step_achieved = nb * flops_total / (ms_per_step / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": f"batched hQR graph ({nb} factorizations per launch)",
-                "achieved": step_achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": step_achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "achieved": step_achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": step_achieved / peak, "traffic": None,
                 "flops_per_launch": nb * flops_total, "ms_per_launch": ms_per_step,
-                "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (per-SM DFMA rate measured)",
+                "peak_source": peak_source, "peak_live": live,
                 "per_kernel": {
                     "note": "one factorization alone, kernels serialised on two streams, "
                             f"{ctx.cluster}-CTA clusters; per-launch durations by CUDA events",
-                    "top": top, "top_achieved": top_achieved, "top_frac": top_achieved / FP64_PEAK_TFLOPS,
+                    "top": top, "top_achieved": top_achieved, "top_frac": top_achieved / peak,
                     "top_launches": p["launches"], "top_ms_per_launch": p["ms"] / max(1, p["launches"]),
                     "top_flops_per_launch": p["flops"] / max(1, p["launches"]),
                     "kind_ms": {k: round(v["ms"], 4) for k, v in prof.items()},
@@ -430,6 +454,30 @@ def gpu_arm(args):
     return 0
 
 
+def peaks_arm(args):
+    """FP64 DFMA and DMMA (mma.sync.m8n8k4) throughput of this GPU, with the SM clocks sampled
+    while the microbenchmark runs: the record behind the roofline denominator."""
+    import torch
+    from paper_1809_10585_gb300 import binding as B
+    from paper_1809_10585_gb300 import build as BUILD
+    BUILD.build()
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    B.fp64_peak(local, iters=200, reps=1)            # warm-up
+    clocks = ClockSampler(local)
+    clocks.start()
+    runs = [B.fp64_peak(local, iters=4000, reps=5) for _ in range(3)]
+    clk = clocks.stop()
+    best = {k: max(r[k] for r in runs) for k in ("dfma", "dmma")}
+    line = {"fp64_peak": True, "dfma_tflops": best["dfma"], "dmma_tflops": best["dmma"],
+            "runs": runs, "clocks": clk, "gpu": torch.cuda.get_device_name(local),
+            "sms": torch.cuda.get_device_properties(local).multi_processor_count,
+            "method": "hodlr_fp64_peak: 4 CTAs x 256 threads per SM, 8 independent chains per thread "
+                      "(DFMA) or per warp (mma.sync.m8n8k4.f64), best of 5 event-timed launches, 3 runs"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -443,11 +491,15 @@ def main():
                     help="rank capacity of the stored factors (a factorization that needs more fails)")
     ap.add_argument("--no-served", action="store_true",
                     help="skip the served request stream (p50/p99 latency)")
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure the FP64 DFMA / DMMA throughput of the GPU and exit")
     ap.add_argument("--cluster", type=int, default=0,
                     help="CTAs per thread-block cluster of the QR/Jacobi kernels (0: automatic)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.peaks:
+        return peaks_arm(args)
     return gpu_arm(args)
 
 

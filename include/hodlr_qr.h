@@ -35,7 +35,8 @@ extern "C" {
 #define HODLR_ENOMEM 2     /* device or host allocation failed                               */
 #define HODLR_ERANK 3      /* a truncated rank exceeded the rank capacity: result truncated  */
 #define HODLR_ESINGULAR 4  /* zero diagonal entry of R met in a triangular solve             */
-#define HODLR_ETIMEOUT 5   /* a device-side wait gave up                                     */
+#define HODLR_ETIMEOUT 5   /* reserved for a device-side wait that gave up; no entry point
+                              waits on the device today, so none returns it                  */
 #define HODLR_ECUDA 6      /* a CUDA runtime call failed                                     */
 #define HODLR_ESTATE 7     /* call not valid in the object's state (e.g. solve before qr)    */
 
@@ -150,12 +151,16 @@ int hodlr_qr_profile(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm, dou
 int hodlr_qr_batched(hodlr_ctx* ctx, int count, hodlr_mat* const* A, double tol, double anorm);
 int hodlr_qr_batched_graph(hodlr_ctx* ctx, int count, hodlr_mat* const* A, double tol, double anorm);
 
-/* Synchronize and return the status word of the last factorization (HODLR_OK, HODLR_ERANK,
- * HODLR_ETIMEOUT) in *status, and the ||A||_2 used in *anorm_used (either may be NULL). */
+/* Synchronize and return the status word of the last factorization in *status, and the
+ * ||A||_2 used for the thresholds eps ||A||_2 of Alg. 2 (S~ and the update of the second block
+ * column) in *anorm_used (either may be NULL).  The status is HODLR_OK, or HODLR_ERANK when a
+ * truncation T_eps (Sec. 2.1.1) kept more singular values than the rank capacity. */
 int hodlr_status(hodlr_ctx* ctx, hodlr_mat* A, int* status, double* anorm_used);
 
-/* Copy the current ranks to host arrays of nleaf-1 entries (any may be NULL):
- * r12/r21 of the A/Y/R storage and rT of T's upper blocks.  Synchronous. */
+/* Copy the current off-diagonal ranks (the k of Eq. (3), A_off = A_L A_R with A_L of k columns)
+ * to host arrays of nleaf-1 entries, heap order (any may be NULL): r12/r21 of the A/Y/R storage
+ * (before hodlr_qr the ranks of A; after it, r12 those of R and r21 those of Y) and rT of T's
+ * upper blocks; these are the quantities of Table 3.  Synchronous. */
 int hodlr_ranks(hodlr_ctx* ctx, const hodlr_mat* A, int* r12, int* r21, int* rT);
 
 /* Algorithmic FP64 flop counts of the last hodlr_qr, per step of the hot path, into
@@ -201,9 +206,12 @@ int hodlr_matvec(hodlr_ctx* ctx, const hodlr_mat* A, int which, int trans, int n
 int hodlr_apply_q(hodlr_ctx* ctx, const hodlr_mat* A, int nrhs, double* B_dev, int ldb);
 int hodlr_apply_qt(hodlr_ctx* ctx, const hodlr_mat* A, int nrhs, double* B_dev, int ldb);
 
-/* B_dev <- R^{-1} Q^T B: Q^T b followed by HODLR back-substitution with R
- * (x2 = R22^{-1} b2, x1 = R11^{-1} (b1 - R12 x2)).  Needs hodlr_qr.  A zero diagonal entry
- * of R makes the result non-finite; hodlr_solve then returns HODLR_ESINGULAR (synchronous). */
+/* B_dev <- R^{-1} Q^T B: the solution of A x = b by the QR decomposition (Sec. 1: x = R^{-1}
+ * Q^T b), i.e. Q^T b = b - Y T^T Y^T b followed by the HODLR back-substitution with the upper
+ * triangular R (Table 1, triangular solve: x2 = R22^{-1} b2, x1 = R11^{-1} (b1 - R12 x2),
+ * dense triangular solves at the leaves).  B is n x nrhs, leading dimension ldb >= n, owned by
+ * the caller and overwritten.  Needs hodlr_qr.  A zero diagonal entry of R makes the result
+ * non-finite; hodlr_solve then returns HODLR_ESINGULAR (synchronous). */
 int hodlr_solve(hodlr_ctx* ctx, const hodlr_mat* A, int nrhs, double* B_dev, int ldb);
 
 /*
@@ -258,16 +266,31 @@ int hodlr_truncate(hodlr_ctx* ctx, int nL, int nR, int K, const double* L_dev,
  *
  * It calls no cudaMalloc, cudaFree or allocating library routine.  Its scratch (the launch
  * descriptor, tau and the G = Y^T Y work area) lives in one static device array of about
- * 0.5 MiB that every GPU loading this library holds until the process exits.  Limit:
- * min(h, w) <= 256 (HODLR_EINVAL beyond it, with nothing written); other arguments as in
- * hodlr_dense_qr.  The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  All calls share the one
- * array and it keeps the last call's contents (every entry is written before it is read, so
- * nothing needs clearing); calls that overlap on the GPU, e.g. from two contexts or streams,
+ * 0.5 MiB that every GPU loading this library holds until the process exits.  Limits:
+ * min(h, w) <= 256 and, as for hodlr_dense_qr, w <= 1024 (HODLR_EINVAL beyond them, with
+ * nothing written); other arguments as in hodlr_dense_qr.  The call makes the context's device
+ * current (A_dev and T_dev must live there).  The first call on a device looks up the array's
+ * device address on that device; make that first call before any stream capture.  The address
+ * table is safe to fill from several host threads at once.  All calls share the one array and
+ * it keeps the last call's contents (every entry is written before it is read, so nothing needs
+ * clearing); calls that overlap on the GPU, e.g. from two contexts, streams or host threads,
  * race on it.  Synchronous.
  */
 int hodlr_dense_qr_noalloc(hodlr_ctx* ctx, int h, int w, double* A_dev, int lda, double* T_dev,
                            int ldt);
+
+/*
+ * hodlr_fp64_peak — measured FP64 throughput of device `device`, the roofline denominator for
+ * the kernels above (they are bound by FP64 arithmetic).  Not part of the paper's method: a
+ * measurement utility.  Two paths are timed with CUDA events, best of `reps` launches after one
+ * warm-up launch, on a grid of 4 CTAs of 256 threads per SM:
+ *   dfma_tflops : fused multiply-add (8 independent chains per thread, 2 flops each);
+ *   dmma_tflops : the FP64 tensor-core instruction mma.sync.m8n8k4.f64 (512 flops each);
+ *   sm_mhz      : SM clock during the best DFMA launch (cycles of one CTA over its time), or NULL.
+ * `iters` sets the launch length (128 iterations of 16 x 8 operations per thread each).
+ * Allocates a few bytes and a stream, synchronous.  HODLR_EINVAL on bad arguments.
+ */
+int hodlr_fp64_peak(int device, int iters, int reps, double* dfma_tflops, double* dmma_tflops, double* sm_mhz);
 
 #ifdef __cplusplus
 }

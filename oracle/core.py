@@ -284,12 +284,24 @@ def lr_update(H: HNode, U, V, eps, step="a7_update"):
 # --------------------------------------------------------------------------------------
 # Dense recursive block QR (Alg. 1)
 # --------------------------------------------------------------------------------------
+def _scaled_norm(v):
+    """||v||_2 without overflow or underflow of the squares: v is divided by its largest
+    magnitude first, as LAPACK's dnrm2 (the norm inside dlarfg) avoids the same."""
+    if v.shape[0] == 0:
+        return 0.0
+    m = float(np.max(np.abs(v)))
+    if m == 0.0:
+        return 0.0
+    w = v / m
+    return m * math.sqrt(float(w @ w))
+
+
 def householder(x):
     """Reflector I - gamma y y^T with (I - gamma y y^T) x = rho e_1 (Alg. 1, n = 1),
     LAPACK dlarfg sign convention."""
     x = np.asarray(x, dtype=np.float64)
     alpha = float(x[0])
-    xnorm = float(np.linalg.norm(x[1:])) if x.shape[0] > 1 else 0.0
+    xnorm = _scaled_norm(x[1:])
     y = np.zeros_like(x)
     y[0] = 1.0
     if xnorm == 0.0:

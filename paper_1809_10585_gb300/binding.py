@@ -69,6 +69,7 @@ _SIGS = {
     "hodlr_dense_qr": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.c_int, _VP, C.c_int]),
     "hodlr_truncate": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, _VP, _VP, C.c_double, C.c_int, _VP, _VP, _PI]),
     "hodlr_dense_qr_noalloc": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.c_int, _VP, C.c_int]),
+    "hodlr_fp64_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, _PD, _PD, _PD]),
 }
 
 SYMBOLS = tuple(_SIGS)
@@ -304,6 +305,13 @@ def qr_batched(ctx: Context, mats, tol: float, anorm: float = 0.0, graph: bool =
 
 def dense_qr(ctx: Context, h, w, A_ptr, lda, T_ptr, ldt):
     check(lib().hodlr_dense_qr(ctx.h, h, w, _VP(A_ptr), lda, _VP(T_ptr), ldt), "hodlr_dense_qr")
+
+
+def fp64_peak(device=0, iters=2000, reps=5):
+    """Measured FP64 TFLOP/s of the device: {"dfma": .., "dmma": .., "sm_mhz": ..}."""
+    a, b, m = C.c_double(), C.c_double(), C.c_double()
+    check(lib().hodlr_fp64_peak(device, iters, reps, C.byref(a), C.byref(b), C.byref(m)), "hodlr_fp64_peak")
+    return {"dfma": a.value, "dmma": b.value, "sm_mhz": m.value}
 
 
 def truncate(ctx: Context, nL, nR, K, L_ptr, Rt_ptr, thr, kmax, Lout_ptr, Rout_ptr):

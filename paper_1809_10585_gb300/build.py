@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libhodlrqr.so")
-SOURCES = ["kernels.cu", "factor.cu", "hodlr.cu"]
+SOURCES = ["kernels.cu", "factor.cu", "hodlr.cu", "peak_fp64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

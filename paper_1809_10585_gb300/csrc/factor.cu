@@ -23,6 +23,8 @@
 // of the cluster after a barrier are never served stale from L1.
 #include <cooperative_groups.h>
 
+#include <atomic>
+
 #include <cstdio>
 #include <cstdlib>
 
@@ -56,6 +58,57 @@ __device__ double block_sum(double v, double* red) {
   if (threadIdx.x == 0) red[QW] = t;
   __syncthreads();
   return red[QW];
+}
+
+__device__ double block_max(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = (threadIdx.x < QW) ? red[threadIdx.x] : 0.0;
+  if (w == 0)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+  if (threadIdx.x == 0) red[QW] = t;
+  __syncthreads();
+  return red[QW];
+}
+
+// Reflector norms of the QR kernels.  The pivot column's squared norm s = |a(j+1:h)|^2 arrives
+// as a plain sum of squares; it is used as is while s and alpha^2 stay far from the overflow
+// and underflow thresholds.  Otherwise (entries beyond about 1e+-150) the whole owner CTA
+// recomputes |(alpha, a(j+1:h))| with the column scaled by a power of two, as LAPACK's dnrm2
+// and dlapy2 do inside dlarfg, so R and the reflectors keep full accuracy at any scale.
+constexpr double kSumHuge = 0x1p960, kSumTiny = 0x1p-960, kAlphaHuge = 0x1p480;
+__device__ __forceinline__ bool norm_needs_scaling(double s, double alpha) {
+  return !(s >= kSumTiny && s <= kSumHuge && fabs(alpha) <= kAlphaHuge);
+}
+// |(alpha, x(lo:h))| with power-of-two scaling; every thread of the CTA calls it with the same
+// arguments (x in shared memory, or in global memory read with ld.global.cg when GLOBAL).
+// *xzero = 1 when x(lo:h) is exactly zero (no reflector, dlarfg's tau = 0).
+template <bool GLOBAL>
+__device__ double scaled_column_norm(const double* x, int lo, int h, double alpha, double* red, bool* xzero) {
+  double m = threadIdx.x == 0 ? fabs(alpha) : 0.0;
+  for (int i = lo + threadIdx.x; i < h; i += QT) m = fmax(m, fabs(GLOBAL ? __ldcg(&x[i]) : x[i]));
+  m = block_max(m, red);
+  if (m == 0.0) {
+    *xzero = true;
+    return 0.0;
+  }
+  int e = 0;
+  frexp(m, &e);
+  const double sc = ldexp(1.0, -e);                     // m * sc in [0.5, 1): exact scaling
+  double ss = 0.0;
+  for (int i = lo + threadIdx.x; i < h; i += QT) {
+    const double v = (GLOBAL ? __ldcg(&x[i]) : x[i]) * sc;
+    ss = fma(v, v, ss);
+  }
+  ss = block_sum(ss, red);
+  *xzero = ss == 0.0;
+  const double a = alpha * sc;
+  return ldexp(sqrt(fma(a, a, ss)), e);
 }
 
 // Cluster barrier and distributed-shared-memory mapping, or their one-CTA forms.
@@ -346,19 +399,30 @@ __device__ __forceinline__ void qr_global_impl(const QRDesc* __restrict__ descs,
   const bool staged = h <= stage_rows;
   const bool in_regs = h <= 32 * kQRRegs;
   for (int j = 0; j < kmax; ++j) {
-    if ((j % C) == crank && threadIdx.x == 0) {
-      const double s = xn_next;
+    if ((j % C) == crank) {
+      double s = xn_next;
       const double alpha = __ldcg(&A[j + j * lda]);
-      double tau = 0.0, scal = 0.0;
-      if (s > 0.0) {
-        const double hn = sqrt(fma(alpha, alpha, s));   // s: plain sum of squares
-        const double beta = -copysign(hn, alpha);
-        tau = (beta - alpha) / beta;
-        scal = 1.0 / (alpha - beta);
-        A[j + j * lda] = beta;
+      double hn = 0.0;
+      if (norm_needs_scaling(s, alpha)) {                // uniform over the owner CTA
+        bool xz = false;
+        hn = scaled_column_norm<true>(A + (size_t)j * lda, j + 1, h, alpha, red, &xz);
+        s = xz ? 0.0 : 1.0;
+        __syncthreads();                                 // red is read above, written below
+      } else if (threadIdx.x == 0) {
+        hn = sqrt(fma(alpha, alpha, s));                 // s: plain sum of squares
       }
-      d.tau[j] = tau;
-      G0[j + j * ldg0] = scal;
+      __syncthreads();                                   // every thread has read alpha
+      if (threadIdx.x == 0) {
+        double tau = 0.0, scal = 0.0;
+        if (s > 0.0) {
+          const double beta = -copysign(hn, alpha);
+          tau = (beta - alpha) / beta;
+          scal = 1.0 / (alpha - beta);
+          A[j + j * lda] = beta;
+        }
+        d.tau[j] = tau;
+        G0[j + j * ldg0] = scal;
+      }
     }
     cl.sync();
     // deferred scaling of the previous pivot column by its owner (nobody reads it any more)
@@ -514,24 +578,32 @@ __device__ __forceinline__ void qr_dsmem_impl(const QRDesc* __restrict__ descs, 
     const int owner = j % C;
     if (owner == crank) {
       double* cj = cols + (size_t)(j / C) * ldc;
+      double s = xn_next;
+      const double alpha = cj[j];
+      double hn = 0.0;
+      if (norm_needs_scaling(s, alpha)) {                // uniform over the owner CTA
+        bool xz = false;
+        hn = scaled_column_norm<false>(cj, j + 1, h, alpha, red, &xz);
+        s = xz ? 0.0 : 1.0;
+        __syncthreads();                                 // red is read above, written below
+      } else if (threadIdx.x == 0) {
+        hn = sqrt(fma(alpha, alpha, s));                 // s: plain sum of squares
+      }
+      double beta = alpha;
       if (threadIdx.x == 0) {
-        const double s = xn_next;
-        const double alpha = cj[j];
         double tau = 0.0, scal = 0.0;
         if (s > 0.0) {
-          // s is already a plain sum of squares, so |(alpha, x)| needs no further scaling
-          const double hn = sqrt(fma(alpha, alpha, s));
-          const double beta = -copysign(hn, alpha);
+          beta = -copysign(hn, alpha);
           tau = (beta - alpha) / beta;
           scal = 1.0 / (alpha - beta);
-          cj[j] = beta;
         }
         sh_tau = tau;
         red[QW] = scal;
         d.tau[j] = tau;
       }
-      __syncthreads();
+      __syncthreads();                                   // every thread has read alpha
       const double scal = red[QW];
+      if (threadIdx.x == 0) cj[j] = beta;
       if (scal != 0.0)
         for (int i = j + 1 + threadIdx.x; i < h; i += QT) cj[i] *= scal;
     }
@@ -1540,29 +1612,32 @@ constexpr size_t kNoAllocDoubles = kNoAllocDescDoubles + kNoAllocMaxK + (size_t)
 constexpr int kNoAllocMaxDevices = 64;
 cudaStream_t ctx_stream(hodlr_ctx* ctx);
 int ctx_cluster(hodlr_ctx* ctx);
+int ctx_device(hodlr_ctx* ctx);
 }  // namespace hq
 
 static __device__ __align__(256) double g_noalloc_scratch[hq::kNoAllocDoubles];
 
 extern "C" int hodlr_dense_qr_noalloc(hodlr_ctx* ctx, int h, int w, double* A, int lda, double* T, int ldt) {
   using namespace hq;
-  if (!ctx || !A || !T || h < 1 || w < 1 || lda < h) return 1;             // HODLR_EINVAL
+  if (!ctx || !A || !T || h < 1 || w < 1 || w > 1024 || lda < h) return 1;  // HODLR_EINVAL
   const int k = h < w ? h : w;
   if (k > kNoAllocMaxK || ldt < k) return 1;                                // beyond the scratch size
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
-    cudaGetLastError();
-    return 6;                                                               // HODLR_ECUDA
-  }
-  // once per device, with that device current: the device address of the scratch array
-  static double* scratch_addr[kNoAllocMaxDevices] = {};
-  if (!scratch_addr[dev]) {
+  // the array, the stream and the caller's buffers all belong to the context's device
+  const int dev = ctx_device(ctx);
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return 1;
+  HQ_CUDA_OK(cudaSetDevice(dev));
+  // once per device, with that device current: the device address of the scratch array.  The
+  // table is shared by host threads; a lookup that two threads make at once stores the same
+  // address twice.
+  static std::atomic<double*> scratch_addr[kNoAllocMaxDevices] = {};
+  double* base = scratch_addr[dev].load(std::memory_order_acquire);
+  if (!base) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) return cuda_fail(e, __FILE__, __LINE__);
-    scratch_addr[dev] = static_cast<double*>(p);
+    base = static_cast<double*>(p);
+    scratch_addr[dev].store(base, std::memory_order_release);
   }
-  double* base = scratch_addr[dev];
   QRDesc q = {};
   q.A = A; q.lda = lda; q.h = h; q.w = w; q.href = -1; q.wref = -1;
   q.tau = base + kNoAllocDescDoubles;

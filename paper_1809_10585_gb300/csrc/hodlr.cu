@@ -25,6 +25,7 @@ using namespace hq;
 namespace hq {
 cudaStream_t ctx_stream(hodlr_ctx* ctx);
 int ctx_cluster(hodlr_ctx* ctx);
+int ctx_device(hodlr_ctx* ctx);
 cudaError_t launch_gemm_reduce(const GemmDesc* d, const int* rd, int nred, int nblocks,
                                const int* devints, cudaStream_t s);
 }
@@ -133,6 +134,7 @@ struct hodlr_mat {
 
 cudaStream_t hq::ctx_stream(hodlr_ctx* ctx) { return ctx->s; }
 int hq::ctx_cluster(hodlr_ctx* ctx) { return ctx->cluster; }
+int hq::ctx_device(hodlr_ctx* ctx) { return ctx->dev; }
 
 // ----------------------------------------------------------------------------- planner
 struct Planner {

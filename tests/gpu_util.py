@@ -91,3 +91,17 @@ def errors_torch(Y, T, R, A, upper=False):
     if upper:
         return torch.linalg.matrix_norm(E1).item(), torch.linalg.matrix_norm(E2).item()
     return norm2(E1), norm2(E2)
+
+
+def errors_both(Y, T, R, A):
+    """((e_orth, e_acc) in the 2-norm, (e_orth, e_acc) in the Frobenius norm) with each error
+    matrix formed once (dense, on the GPU)."""
+    n = Y.shape[0]
+    I = torch.eye(n, dtype=torch.float64, device=Y.device)
+    Q = I - Y @ (T @ Y.T)
+    E1 = Q.T @ Q - I
+    E2 = Q @ R - A
+    del Q
+    two = (norm2(E1), norm2(E2))
+    fro = (torch.linalg.matrix_norm(E1).item(), torch.linalg.matrix_norm(E2).item())
+    return two, fro

@@ -29,7 +29,10 @@ def dgeqrt_full(A):
 # ---------------------------------------------------------------------------------- Alg. 1
 @pytest.mark.parametrize("x", [np.array([3.0, 4.0]), np.array([-2.0, 1.0, 2.0]),
                                np.array([0.0, 1.0, -1.0]), np.array([-0.0, 2.0]),
-                               np.array([5.0]), np.array([2.0, 0.0, 0.0])])
+                               np.array([5.0]), np.array([2.0, 0.0, 0.0]),
+                               # magnitudes whose squares overflow / underflow: dlarfg scales
+                               np.array([3e160, -4e160, 1e160]), np.array([-2e-170, 1e-170, 5e-171]),
+                               np.array([1e-170, 3e160]), np.array([3e160, 1e-170])])
 def test_householder_matches_dlarfg(x):
     y, gamma, rho = O.householder(x)
     beta, xs, tau = lapack.dlarfg(len(x), x[0], x[1:].copy() if len(x) > 1 else np.zeros(1))
@@ -38,7 +41,7 @@ def test_householder_matches_dlarfg(x):
     assert math.isclose(gamma, tau, rel_tol=1e-14, abs_tol=1e-300)
     np.testing.assert_allclose(y[1:], xs, rtol=1e-14, atol=0)
     Hx = x - gamma * y * (y @ x)
-    np.testing.assert_allclose(Hx, np.r_[rho, np.zeros(len(x) - 1)], atol=1e-14 * np.linalg.norm(x))
+    np.testing.assert_allclose(Hx, np.r_[rho, np.zeros(len(x) - 1)], atol=1e-14 * len(x) * np.abs(x).max())
 
 
 @pytest.mark.parametrize("m,n,seed", [(1, 1, 0), (7, 7, 1), (20, 5, 2), (33, 17, 3), (64, 64, 4), (70, 31, 5)])
@@ -48,6 +51,21 @@ def test_block_qr_equals_lapack_dgeqrt(m, n, seed):
     V, Tl, Rl = dgeqrt_full(A)
     sc = np.linalg.norm(A)
     np.testing.assert_allclose(R, Rl, atol=1e-13 * sc)
+    np.testing.assert_allclose(Y, V, atol=1e-12)
+    np.testing.assert_allclose(T, Tl, atol=1e-12)
+
+
+def test_block_qr_equals_lapack_at_extreme_column_scales():
+    # columns near 1e+-160: their squares overflow or underflow unless the norm is scaled
+    A = np.random.default_rng(9).standard_normal((40, 17))
+    A[:, 3] *= 1e160
+    A[:, 5] *= 1e-160
+    A[:, 11] *= 1e-160
+    Y, T, R = O.block_qr(A)
+    V, Tl, Rl = dgeqrt_full(A)
+    assert np.isfinite(R).all() and np.isfinite(Y).all() and np.isfinite(T).all()
+    # column j of R has the scale of column j of A
+    assert (np.abs(R - Rl) / np.abs(Rl).max(axis=0)[None, :]).max() <= 1e-13
     np.testing.assert_allclose(Y, V, atol=1e-12)
     np.testing.assert_allclose(T, Tl, atol=1e-12)
 
