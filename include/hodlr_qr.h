@@ -75,6 +75,19 @@ int hodlr_ctx_get_concurrency(hodlr_ctx* ctx, int* factorizations);
 int hodlr_sync(hodlr_ctx* ctx);
 
 /*
+ * Device memory accounting (not in the paper; admission control for batched and served use).
+ * Every device allocation the library makes for a matrix built through this context (storage,
+ * rank tables, snapshot, the factorization and solve plans with their scratch arenas) is charged
+ * to the context's account and released by hodlr_free.  With a limit set (bytes > 0), an
+ * allocation that would take the account above it fails with HODLR_ENOMEM instead, and the call
+ * that needed it (hodlr_build, hodlr_snapshot, hodlr_qr ...) returns HODLR_ENOMEM with the
+ * handles still valid; a later call may succeed after memory is freed or the limit raised.
+ * bytes = 0 removes the limit.  hodlr_ctx_memory_used reports the account's current total.
+ */
+int hodlr_ctx_set_memory_limit(hodlr_ctx* ctx, size_t bytes);
+int hodlr_ctx_memory_used(hodlr_ctx* ctx, size_t* bytes);
+
+/*
  * hodlr_build — allocate a device-resident HODLR matrix and upload it (Sec. 2.1, Eq. (3)).
  *   n, nleaf        : order, number of leaves (a power of two, >= 1).
  *   leaf_sizes      : host, nleaf entries n_j > 0 summing to n.
@@ -84,7 +97,9 @@ int hodlr_sync(hodlr_ctx* ctx);
  *   r12, r21        : host, nleaf-1 ranks, 0 <= r <= min(m1, m2) and r <= rank_cap.
  *   rank_cap        : storage capacity per off-diagonal block (ranks of Y, T and R produced
  *                     by hodlr_qr must fit; 8 <= rank_cap <= 256).
- * Errors: HODLR_EINVAL on bad sizes, HODLR_ENOMEM.  The copies complete before return.
+ * Errors: HODLR_EINVAL on bad sizes or a non-finite value (NaN, infinity) in any leaf or
+ * factor; HODLR_ENOMEM when an allocation fails or the context's memory limit would be
+ * exceeded.  The copies complete before return.
  */
 int hodlr_build(hodlr_ctx* ctx, int n, int nleaf, const int* leaf_sizes,
                 const double* const* leaves,
@@ -184,6 +199,21 @@ int hodlr_flops(hodlr_ctx* ctx, const hodlr_mat* A, double* out);
  */
 int hodlr_build_dense(hodlr_ctx* ctx, int n, int nleaf, const int* leaf_sizes, const double* A_dev, int lda,
                       double tol, int rank_cap, unsigned long long seed, hodlr_mat** out);
+
+/* Device bytes currently held by matrix A: its storage, tables, snapshot and plans. */
+int hodlr_device_bytes(const hodlr_mat* A, size_t* bytes);
+
+/*
+ * hodlr_footprint — the device bytes that hodlr_build of a matrix with this partition
+ * (n, nleaf, leaf_sizes) and rank capacity, followed by hodlr_snapshot when with_snapshot, by
+ * hodlr_qr (estimate_norm: anorm <= 0, i.e. ||A||_2 estimated on the device) and, when
+ * nrhs > 0, by hodlr_solve_async with nrhs right-hand sides, allocate in total.  Computed on
+ * the host by the planner's measuring pass, without a device; equal to hodlr_device_bytes
+ * after those calls.  The factorization's storage is O(k n log n) (Sec. 2.1) at k = rank_cap;
+ * its scratch does not depend on the ranks.  HODLR_EINVAL for a bad partition or nrhs > 1024.
+ */
+int hodlr_footprint(int n, int nleaf, const int* leaf_sizes, int rank_cap, int estimate_norm, int with_snapshot,
+                    int nrhs, size_t* bytes);
 
 /* Largest stored rank of the lower blocks (Y's after hodlr_qr, A's before), of T and of the
  * upper blocks (R's after hodlr_qr), and the device bytes of the matrix storage (the paper's
@@ -285,12 +315,11 @@ int hodlr_dense_qr_noalloc(hodlr_ctx* ctx, int h, int w, double* A_dev, int lda,
  * measurement utility.  Two paths are timed with CUDA events, best of `reps` launches after one
  * warm-up launch, on a grid of 4 CTAs of 256 threads per SM:
  *   dfma_tflops : fused multiply-add (8 independent chains per thread, 2 flops each);
- *   dmma_tflops : the FP64 tensor-core instruction mma.sync.m8n8k4.f64 (512 flops each);
- *   sm_mhz      : SM clock during the best DFMA launch (cycles of one CTA over its time), or NULL.
+ *   dmma_tflops : the FP64 tensor-core instruction mma.sync.m8n8k4.f64 (512 flops each).
  * `iters` sets the launch length (128 iterations of 16 x 8 operations per thread each).
  * Allocates a few bytes and a stream, synchronous.  HODLR_EINVAL on bad arguments.
  */
-int hodlr_fp64_peak(int device, int iters, int reps, double* dfma_tflops, double* dmma_tflops, double* sm_mhz);
+int hodlr_fp64_peak(int device, int iters, int reps, double* dfma_tflops, double* dmma_tflops);
 
 #ifdef __cplusplus
 }

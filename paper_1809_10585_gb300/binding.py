@@ -69,7 +69,12 @@ _SIGS = {
     "hodlr_dense_qr": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.c_int, _VP, C.c_int]),
     "hodlr_truncate": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, _VP, _VP, C.c_double, C.c_int, _VP, _VP, _PI]),
     "hodlr_dense_qr_noalloc": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.c_int, _VP, C.c_int]),
-    "hodlr_fp64_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, _PD, _PD, _PD]),
+    "hodlr_fp64_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, _PD, _PD]),
+    "hodlr_ctx_set_memory_limit": (C.c_int, [_VP, C.c_size_t]),
+    "hodlr_ctx_memory_used": (C.c_int, [_VP, C.POINTER(C.c_size_t)]),
+    "hodlr_device_bytes": (C.c_int, [_VP, C.POINTER(C.c_size_t)]),
+    "hodlr_footprint": (C.c_int, [C.c_int, C.c_int, _PI, C.c_int, C.c_int, C.c_int, C.c_int,
+                                  C.POINTER(C.c_size_t)]),
 }
 
 SYMBOLS = tuple(_SIGS)
@@ -145,6 +150,14 @@ class Context:
 
     def sync(self):
         check(lib().hodlr_sync(self.h), "hodlr_sync")
+
+    def set_memory_limit(self, nbytes: int):
+        check(lib().hodlr_ctx_set_memory_limit(self.h, int(nbytes)), "hodlr_ctx_set_memory_limit")
+
+    def memory_used(self) -> int:
+        v = C.c_size_t()
+        check(lib().hodlr_ctx_memory_used(self.h, C.byref(v)), "hodlr_ctx_memory_used")
+        return int(v.value)
 
     def ready(self) -> bool:
         r = C.c_int()
@@ -279,6 +292,11 @@ class Matrix:
         check(lib().hodlr_norm2_estimate(self.ctx.h, self.h, iters, C.byref(out)), "hodlr_norm2_estimate")
         return out.value
 
+    def device_bytes(self) -> int:
+        v = C.c_size_t()
+        check(lib().hodlr_device_bytes(self.h, C.byref(v)), "hodlr_device_bytes")
+        return int(v.value)
+
     def storage_bytes(self):
         return int(lib().hodlr_storage_bytes(self.h))
 
@@ -308,10 +326,19 @@ def dense_qr(ctx: Context, h, w, A_ptr, lda, T_ptr, ldt):
 
 
 def fp64_peak(device=0, iters=2000, reps=5):
-    """Measured FP64 TFLOP/s of the device: {"dfma": .., "dmma": .., "sm_mhz": ..}."""
-    a, b, m = C.c_double(), C.c_double(), C.c_double()
-    check(lib().hodlr_fp64_peak(device, iters, reps, C.byref(a), C.byref(b), C.byref(m)), "hodlr_fp64_peak")
-    return {"dfma": a.value, "dmma": b.value, "sm_mhz": m.value}
+    """Measured FP64 TFLOP/s of the device: {"dfma": .., "dmma": ..}."""
+    a, b = C.c_double(), C.c_double()
+    check(lib().hodlr_fp64_peak(device, iters, reps, C.byref(a), C.byref(b)), "hodlr_fp64_peak")
+    return {"dfma": a.value, "dmma": b.value}
+
+
+def footprint(n, leaf_sizes, rank_cap, estimate_norm=True, with_snapshot=False, nrhs=0):
+    """Device bytes of hodlr_build (+ snapshot) + hodlr_qr (+ hodlr_solve_async), from the host."""
+    sizes = (C.c_int * len(leaf_sizes))(*[int(x) for x in leaf_sizes])
+    out = C.c_size_t()
+    check(lib().hodlr_footprint(int(n), len(leaf_sizes), sizes, int(rank_cap), int(bool(estimate_norm)),
+                                int(bool(with_snapshot)), int(nrhs), C.byref(out)), "hodlr_footprint")
+    return int(out.value)
 
 
 def truncate(ctx: Context, nL, nR, K, L_ptr, Rt_ptr, thr, kmax, Lout_ptr, Rout_ptr):

@@ -31,6 +31,9 @@ __host__ __device__ inline int dimv(int lit, int ref, const int* di) {
   return v < 0 ? 0 : (v > lit ? lit : v);
 }
 
+// Output tile of the batched GEMM (rows x columns); the planner sizes the grid with it.
+constexpr int kGemmBM = 64, kGemmBN = 32;
+
 // C = alpha * op(mask(A)) * op(mask(B)) + beta * C.  Masks act on the stored matrices.
 enum Mask { kMaskNone = 0, kMaskUpper = 1, kMaskUnitLower = 2, kMaskLower = 3 };
 // flop accounting mode: 0 = 2mnk, 1 = mnk (one triangular factor), -1 = not counted

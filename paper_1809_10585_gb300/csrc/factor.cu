@@ -379,13 +379,12 @@ __device__ __forceinline__ void qr_global_impl(const QRDesc* __restrict__ descs,
     atomicAdd(&flops[kKindSlot + 2], g);
   }
 
-  // Column j's reflector is v = [1; scal_j * a(j+1:h, j)] with the column left unscaled until
-  // every CTA has used it; its owner scales it after the next cluster barrier.  scal_j is kept
-  // on G's diagonal (the T build uses only G's off-diagonal parts).  The norm of the next
-  // pivot column is produced by the warp that applies the current reflector to it.
+  // Column j's owner forms its reflector v = [1; a(j+1:h, j) / (alpha - beta)] in place before
+  // the cluster barrier that publishes it, so every product with v is taken with the scaled
+  // vector (an unscaled column of magnitude 1e150 times another such column would overflow).
+  // The norm of the next pivot column is produced by the warp that applies the current
+  // reflector to it.
   __shared__ double xn_next;
-  double* G0 = d.G;
-  const size_t ldg0 = d.ldg;
   if (crank == 0 && kmax > 0) {
     double s = 0.0;
     for (int i = 1 + threadIdx.x; i < h; i += QT) {
@@ -421,18 +420,15 @@ __device__ __forceinline__ void qr_global_impl(const QRDesc* __restrict__ descs,
           A[j + j * lda] = beta;
         }
         d.tau[j] = tau;
-        G0[j + j * ldg0] = scal;
+        red[QW] = scal;
       }
+      __syncthreads();
+      const double scal = red[QW];
+      if (scal != 0.0)
+        for (int i = j + 1 + threadIdx.x; i < h; i += QT) A[i + (size_t)j * lda] = __ldcg(&A[i + (size_t)j * lda]) * scal;
     }
     cl.sync();
-    // deferred scaling of the previous pivot column by its owner (nobody reads it any more)
-    if (j > 0 && ((j - 1) % C) == crank) {
-      const double sp = __ldcg(&G0[(j - 1) + (j - 1) * ldg0]);
-      if (sp != 0.0)
-        for (int i = j + threadIdx.x; i < h; i += QT) A[i + (j - 1) * lda] = __ldcg(&A[i + (j - 1) * lda]) * sp;
-    }
     const double tau = __ldcg(&d.tau[j]);
-    const double scal = __ldcg(&G0[j + j * ldg0]);
     const double* y = A + j * lda;
     if (staged && tau != 0.0) {
       for (int i = j + 1 + threadIdx.x; i < h; i += QT) ysm[i] = __ldcg(&y[i]);
@@ -457,15 +453,14 @@ __device__ __forceinline__ void qr_global_impl(const QRDesc* __restrict__ descs,
             }
           }
           t = warp_sum2(t);
-          const double wv = tau * fma(scal, t, __ldcg(&a[j]));
-          const double ws = wv * scal;
+          const double wv = tau * (t + __ldcg(&a[j]));
           const bool pivot = c == j + 1;          // next pivot: its norm below row j + 1 too
 #pragma unroll
           for (int q = 0; q < kQRRegs; ++q) {
             if (q < nq) {
               const int i = j + 1 + lane + 32 * q;
               if (i < h) {
-                const double v = fma(-ws, staged ? ysm[i] : __ldcg(&y[i]), r[q]);
+                const double v = fma(-wv, staged ? ysm[i] : __ldcg(&y[i]), r[q]);
                 a[i] = v;
                 if (pivot && i > j + 1) nn = fma(v, v, nn);
               }
@@ -476,11 +471,10 @@ __device__ __forceinline__ void qr_global_impl(const QRDesc* __restrict__ descs,
           double t = 0.0;
           for (int i = j + 1 + lane; i < h; i += 32) t = fma(staged ? ysm[i] : __ldcg(&y[i]), __ldcg(&a[i]), t);
           t = warp_sum2(t);
-          const double wv = tau * fma(scal, t, __ldcg(&a[j]));
-          const double ws = wv * scal;
+          const double wv = tau * (t + __ldcg(&a[j]));
           const bool pivot = c == j + 1;
           for (int i = j + 1 + lane; i < h; i += 32) {
-            const double v = fma(-ws, staged ? ysm[i] : __ldcg(&y[i]), __ldcg(&a[i]));
+            const double v = fma(-wv, staged ? ysm[i] : __ldcg(&y[i]), __ldcg(&a[i]));
             a[i] = v;
             if (pivot && i > j + 1) nn = fma(v, v, nn);
           }
@@ -499,13 +493,7 @@ __device__ __forceinline__ void qr_global_impl(const QRDesc* __restrict__ descs,
     }
     __syncthreads();
   }
-  // scale the last pivot column
   cl.sync();
-  if (kmax > 0 && ((kmax - 1) % C) == crank) {
-    const double sp = __ldcg(&G0[(kmax - 1) + (kmax - 1) * ldg0]);
-    if (sp != 0.0)
-      for (int i = kmax + threadIdx.x; i < h; i += QT) A[i + (kmax - 1) * lda] = __ldcg(&A[i + (kmax - 1) * lda]) * sp;
-  }
   qr_build_T(d, A, lda, h, kmax, C, crank, cl, false);
 }
 

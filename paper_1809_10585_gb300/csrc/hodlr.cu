@@ -10,11 +10,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/hodlr_qr.h"
@@ -31,7 +34,16 @@ cudaError_t launch_gemm_reduce(const GemmDesc* d, const int* rd, int nred, int n
 }
 
 // ------------------------------------------------------------------------------- objects
+// Device bytes held through one context (its matrices with their plans, arenas and snapshots),
+// against an optional limit set by the caller.  Matrices keep the account alive, so freeing a
+// matrix after its context is destroyed stays correct.
+struct MemAcct {
+  std::atomic<long long> used{0};
+  std::atomic<long long> limit{0};   // 0: no limit
+};
+
 struct hodlr_ctx {
+  std::shared_ptr<MemAcct> mem = std::make_shared<MemAcct>();
   int dev = 0;
   cudaStream_t own = nullptr;
   cudaStream_t s = nullptr;
@@ -95,6 +107,9 @@ struct View {
 };
 
 struct hodlr_mat {
+  std::shared_ptr<MemAcct> mem;                 // account of the context that built it
+  std::unordered_map<void*, size_t> allocs;     // live device allocations and their sizes
+  long long held = 0;                           // their total
   int n = 0, nleaf = 0, levels = 0, kc = 0, ldl = 0, nn = 0;
   std::vector<int> leaf_sizes, lo, hi;  // per heap node
   // device storage
@@ -132,6 +147,50 @@ struct hodlr_mat {
   bool factored = false;
 };
 
+// Device allocation on behalf of matrix M, charged to its context's account.  HODLR_ENOMEM when
+// the account's limit would be exceeded or cudaMalloc fails (*p is then nullptr).
+static int mat_malloc(hodlr_mat* M, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  MemAcct* a = M->mem.get();
+  if (a) {
+    const long long lim = a->limit.load();
+    const long long before = a->used.fetch_add((long long)bytes);
+    if (lim > 0 && before + (long long)bytes > lim) {
+      a->used.fetch_sub((long long)bytes);
+      return HODLR_ENOMEM;
+    }
+  }
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    if (a) a->used.fetch_sub((long long)bytes);
+    return HODLR_ENOMEM;
+  }
+  M->allocs[*p] = bytes;
+  M->held += (long long)bytes;
+  return HODLR_OK;
+}
+template <class T>
+static int mat_alloc(hodlr_mat* M, T** p, size_t bytes) {
+  void* q = nullptr;
+  int rc = mat_malloc(M, &q, bytes);
+  *p = static_cast<T*>(q);
+  return rc;
+}
+static void mat_free(hodlr_mat* M, void* p) {
+  if (!p) return;
+  size_t b = 0;
+  auto it = M->allocs.find(p);
+  if (it != M->allocs.end()) {
+    b = it->second;
+    M->allocs.erase(it);
+  }
+  cudaFree(p);
+  M->held -= (long long)b;
+  if (M->mem) M->mem->used.fetch_sub((long long)b);
+}
+
 cudaStream_t hq::ctx_stream(hodlr_ctx* ctx) { return ctx->s; }
 int hq::ctx_cluster(hodlr_ctx* ctx) { return ctx->cluster; }
 int hq::ctx_device(hodlr_ctx* ctx) { return ctx->dev; }
@@ -140,12 +199,19 @@ int hq::ctx_device(hodlr_ctx* ctx) { return ctx->dev; }
 struct Planner {
   hodlr_mat* M;
   Plan* P;
-  size_t top = 0, high = 0;      // arena bump pointer
+  // Scratch regions.  The main stream's work uses a LIFO arena (mark/release); the side
+  // stream's work uses a second LIFO arena of its own (its work is ordered on its stream, so
+  // one node's side work reuses the memory of the previous one, and the two streams never
+  // alias); buffers that the main stream writes and the side stream reads later (hand-offs)
+  // come from a third region that is never reused.
+  size_t top = 0, high = 0;      // main-stream arena bump pointer
   char* base;                    // arena base (nullptr in the measuring pass)
-  size_t top2 = 0;               // never-reused region (side-stream work and its inputs)
+  size_t top2 = 0;               // never-reused hand-off region
   char* base2 = nullptr;
+  size_t top3 = 0, high3 = 0;    // side-stream arena
+  char* base3 = nullptr;
   int stream = 0;                // stream of the records being emitted
-  bool fresh = false;            // route alloc() to the never-reused region
+  bool fresh = false;            // route alloc() to the never-reused hand-off region
   int int_top;                   // devints bump pointer
   int int_high;
   size_t cnt_top = 0;            // split-K tile counters (never reused, zero between uses)
@@ -161,13 +227,23 @@ struct Planner {
       top2 += bytes;
       return reinterpret_cast<T*>(base2 + off2);
     }
+    if (stream == 1) {
+      size_t off3 = top3;
+      top3 += bytes;
+      high3 = std::max(high3, top3);
+      return reinterpret_cast<T*>(base3 + off3);
+    }
     size_t off = top;
     top += bytes;
     high = std::max(high, top);
     return reinterpret_cast<T*>(base + off);
   }
-  size_t mark() const { return top; }
-  void release(size_t m) { top = m; }
+  // mark / release act on the arena of the stream whose records are being emitted
+  size_t mark() const { return stream == 1 ? top3 : top; }
+  void release(size_t m) {
+    if (stream == 1) top3 = m;
+    else top = m;
+  }
   int event() { return P->nevents++; }
   void ev_record(int st, int ev) {
     Rec r = {};
@@ -215,17 +291,19 @@ struct Planner {
     int redblocks = 0;
     for (auto d : ds) {
       if (d.m <= 0 || d.n <= 0) continue;
-      d.tiles_m = (d.m + 31) / 32;
-      d.tiles_n = (d.n + 31) / 32;
+      d.tiles_m = (d.m + kGemmBM - 1) / kGemmBM;
+      d.tiles_n = (d.n + kGemmBN - 1) / kGemmBN;
       int tiles = d.tiles_m * d.tiles_n;
       d.ksplit = 1;
       d.part = nullptr;
-      // A 32x32 tile retires 2048 flops per k on one SM (~8 GFLOP/s of FP64): split the
-      // reduction so that one launch spreads over the whole GPU and each CTA runs >= 64 k.
-      if (d.k >= 128 && tiles < 608) {
+      // A tile retires a few thousand flops per k on one SM (~7 GFLOP/s of FP64): split the
+      // reduction so that one launch spreads over the whole GPU and each CTA runs >= 64 k.  Only
+      // a literal k is split: a k set by a rank at run time (kref >= 0) is usually far below its
+      // capacity, where splits would only add partial sums and their scratch.
+      if (d.k >= 128 && d.kref < 0 && tiles < 608) {
         int ks = (608 + tiles - 1) / tiles;
         ks = std::min(ks, d.k / 64);
-        ks = std::min(ks, 64);
+        ks = std::min(ks, 16);                   // partial sums: at most 16 x m x n scratch
         if (ks >= 2) d.ksplit = ks;
       }
       d.tile_count = nullptr;
@@ -703,8 +781,7 @@ struct Planner {
     int e_x3 = event();
     ev_record(0, e_x3);
     {
-      stream = 1;
-      fresh = true;
+      stream = 1;                                  // side-stream arena
       ev_wait(1, e_x3);
       Trunc t;
       t.nL = a; t.nR = b;
@@ -714,7 +791,6 @@ struct Planner {
       t.kout_ref = r12(v); t.step = kStepUpdate;
       std::vector<Trunc> ts = {t};
       truncate(ts);
-      fresh = false;
       stream = 0;
     }
     // A^22 = A~22 -_H (B_L21 (Y~_B S_L)) S_R^T
@@ -741,8 +817,8 @@ struct Planner {
     // stream once the second block column is factored; its inputs are final from here on
     int e_c2 = event();
     ev_record(0, e_c2);
-    stream = 1;
-    fresh = true;
+    stream = 1;                                    // side-stream arena, reused node to node
+    const size_t mk3 = mark();
     ev_wait(1, e_c2);
     {
       double* X4 = alloc<double>((size_t)b * kc);
@@ -768,7 +844,7 @@ struct Planner {
     int e_t = event();
     ev_record(1, e_t);
     tdone[v] = e_t;
-    fresh = false;
+    release(mk3);
     stream = 0;
   }
 
@@ -786,26 +862,35 @@ struct Planner {
                      w, -1, w, -1, kc, kref, -1.0, 1.0, kStepUpdate, 0));
     }
     gemm(g);
-    std::vector<Trunc> ts;
-    for (int u : internal) {
-      int a = m1(u), b = m2(u);
-      int c1lo = M->lo[2 * u + 1] - los, c2lo = M->lo[2 * u + 2] - los;
-      Trunc t;
-      t.nL = a; t.nR = b;
-      t.L = {seg(M->U12[u], a, kc, r12(u), 1.0), seg(U + c1lo, ldu, kc, kref, -1.0)};
-      t.R = {seg(M->V12[u], b, kc, r12(u), 1.0), seg(V + c2lo, ldv, kc, kref, 1.0)};
-      t.thr = tol; t.thr_ref = M->dscal; t.Uout = M->U12[u]; t.ldu = a; t.Vout = M->V12[u]; t.ldv = b;
-      t.kout_ref = r12(u); t.step = kStepUpdate;
-      ts.push_back(t);
-      Trunc t2;
-      t2.nL = b; t2.nR = a;
-      t2.L = {seg(M->U21[u], b, kc, r21(u), 1.0), seg(U + c2lo, ldu, kc, kref, -1.0)};
-      t2.R = {seg(M->V21[u], a, kc, r21(u), 1.0), seg(V + c1lo, ldv, kc, kref, 1.0)};
-      t2.thr = tol; t2.thr_ref = M->dscal; t2.Uout = M->U21[u]; t2.ldu = b; t2.Vout = M->V21[u]; t2.ldv = a;
-      t2.kout_ref = r21(u); t2.step = kStepUpdate;
-      ts.push_back(t2);
+    // The truncations of one depth of the subtree form one batch; the batches run depth after
+    // depth, so that each reuses the scratch of the previous one (truncate releases its
+    // scratch) and the arena holds one depth's worth, not the whole subtree's.
+    int maxdep = 0;
+    for (int dd : depth) maxdep = std::max(maxdep, dd);
+    for (int dep = 0; dep <= maxdep; ++dep) {
+      std::vector<Trunc> ts;
+      for (size_t q = 0; q < internal.size(); ++q) {
+        if (depth[q] != dep) continue;
+        const int u = internal[q];
+        int a = m1(u), b = m2(u);
+        int c1lo = M->lo[2 * u + 1] - los, c2lo = M->lo[2 * u + 2] - los;
+        Trunc t;
+        t.nL = a; t.nR = b;
+        t.L = {seg(M->U12[u], a, kc, r12(u), 1.0), seg(U + c1lo, ldu, kc, kref, -1.0)};
+        t.R = {seg(M->V12[u], b, kc, r12(u), 1.0), seg(V + c2lo, ldv, kc, kref, 1.0)};
+        t.thr = tol; t.thr_ref = M->dscal; t.Uout = M->U12[u]; t.ldu = a; t.Vout = M->V12[u]; t.ldv = b;
+        t.kout_ref = r12(u); t.step = kStepUpdate;
+        ts.push_back(t);
+        Trunc t2;
+        t2.nL = b; t2.nR = a;
+        t2.L = {seg(M->U21[u], b, kc, r21(u), 1.0), seg(U + c2lo, ldu, kc, kref, -1.0)};
+        t2.R = {seg(M->V21[u], a, kc, r21(u), 1.0), seg(V + c1lo, ldv, kc, kref, 1.0)};
+        t2.thr = tol; t2.thr_ref = M->dscal; t2.Uout = M->U21[u]; t2.ldu = b; t2.Vout = M->V21[u]; t2.ldv = a;
+        t2.kout_ref = r21(u); t2.step = kStepUpdate;
+        ts.push_back(t2);
+      }
+      truncate(ts);
     }
-    truncate(ts);
   }
 
   // ||A||_2 by power iteration on A^T A (device), result into dscal[0]
@@ -937,15 +1022,15 @@ static int run_plan(hodlr_ctx* ctx, hodlr_mat* M, Plan& P, Profiler* prof = null
   return run_plan_on(ctx, M, P, prof, ctx->s, ctx->side);
 }
 
-static int upload_plan(Plan& P) {
+static int upload_plan(hodlr_mat* M, Plan& P) {
   for (auto e : P.events) cudaEventDestroy(e);
   P.events.assign(P.nevents, nullptr);
   for (auto& e : P.events)
     if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return HODLR_ECUDA;
-  if (P.dblob) cudaFree(P.dblob);
+  mat_free(M, P.dblob);
   P.dblob = nullptr;
   P.dblob_bytes = std::max<size_t>(P.blob.size(), 16);
-  HQ_CUDA_OK(cudaMalloc(&P.dblob, P.dblob_bytes));
+  if (int rc = mat_alloc(M, &P.dblob, P.dblob_bytes)) return rc;
   if (!P.blob.empty()) HQ_CUDA_OK(cudaMemcpy(P.dblob, P.blob.data(), P.blob.size(), cudaMemcpyHostToDevice));
   // a pageable upload may still be in flight when cudaMemcpy returns, and the context's streams
   // do not wait for the legacy stream: finish it before any launch reads the descriptors
@@ -953,73 +1038,90 @@ static int upload_plan(Plan& P) {
   return HODLR_OK;
 }
 
-// Build the factorization plan: measure the arena, allocate it, plan again for real.
+// Device bytes of a plan's scratch, measured by the planner's first (measuring) pass: the
+// main-stream arena, the hand-off region followed by the side-stream arena, the split-K tile
+// counters and the descriptor blob.
+struct PlanSizes {
+  size_t arena = 0, hand = 0, side = 0, counters = 0, blob = 0;
+  size_t arena_bytes() const { return arena + 4096; }
+  size_t arena2_bytes() const { return hand + side + 4096; }
+  size_t counter_bytes() const { return sizeof(int) * counters; }
+  size_t blob_bytes() const { return std::max<size_t>(blob, 16); }
+};
+
+template <class F>
+static int measure_plan(hodlr_mat* M, Plan& P, double tol, F&& body, PlanSizes* out) {
+  P.recs.clear();
+  P.blob.clear();
+  Planner pl;
+  pl.M = M; pl.P = &P; pl.base = nullptr; pl.base2 = nullptr; pl.base3 = nullptr; pl.cnt_base = nullptr;
+  P.nevents = 0;
+  pl.int_top = 3 * M->nn; pl.int_high = pl.int_top;
+  pl.cluster = 0; pl.tol = tol;
+  body(pl);
+  if (pl.int_high > M->n_devints) return HODLR_ENOMEM;
+  if (pl.too_wide) return HODLR_EINVAL;
+  out->arena = pl.high;
+  out->hand = (pl.top2 + 255) & ~size_t(255);
+  out->side = pl.high3;
+  out->counters = pl.cnt_top;
+  out->blob = P.blob.size();
+  return HODLR_OK;
+}
+
+// Build a plan: measure its scratch, allocate what is missing, plan again for real.
 template <class F>
 static int build_plan(hodlr_mat* M, Plan& P, int cluster, double tol, F&& body, bool solve_arenas = false) {
   char** ar1 = solve_arenas ? &M->sarena : &M->arena;
   size_t* ar1b = solve_arenas ? &M->sarena_bytes : &M->arena_bytes;
   char** ar2 = solve_arenas ? &M->sarena2 : &M->arena2;
   size_t* ar2b = solve_arenas ? &M->sarena2_bytes : &M->arena2_bytes;
-  for (int pass = 0; pass < 2; ++pass) {
-    P.recs.clear();
-    P.blob.clear();
-    Planner pl;
-    pl.M = M; pl.P = &P; pl.base = pass == 0 ? nullptr : *ar1;
-    pl.base2 = pass == 0 ? nullptr : *ar2;
-    pl.cnt_base = pass == 0 ? nullptr : P.counters;
-    P.nevents = 0;
-    pl.int_top = 3 * M->nn; pl.int_high = pl.int_top;
-    pl.cluster = cluster; pl.tol = tol;
-    body(pl);
-    if (pl.int_high > M->n_devints) return HODLR_ENOMEM;
-    if (pl.too_wide) return HODLR_EINVAL;
-    if (pass == 0) {
-      size_t need = pl.high + 4096;
-      if (need > *ar1b) {
-        if (*ar1) cudaFree(*ar1);
-        *ar1 = nullptr;
-        *ar1b = 0;
-        if (cudaMalloc(ar1, need) != cudaSuccess) {
-          cudaGetLastError();
-          return HODLR_ENOMEM;
-        }
-        *ar1b = need;
-      }
-      if (pl.cnt_top > P.counters_n) {
-        if (P.counters) cudaFree(P.counters);
-        P.counters = nullptr;
-        P.counters_n = 0;
-        if (cudaMalloc(&P.counters, sizeof(int) * pl.cnt_top) != cudaSuccess) {
-          cudaGetLastError();
-          return HODLR_ENOMEM;
-        }
-        P.counters_n = pl.cnt_top;
-        HQ_CUDA_OK(cudaMemset(P.counters, 0, sizeof(int) * pl.cnt_top));
-        HQ_CUDA_OK(cudaStreamSynchronize(cudaStreamLegacy));
-      }
-      size_t need2 = pl.top2 + 4096;
-      if (need2 > *ar2b) {
-        if (*ar2) cudaFree(*ar2);
-        *ar2 = nullptr;
-        *ar2b = 0;
-        if (cudaMalloc(ar2, need2) != cudaSuccess) {
-          cudaGetLastError();
-          return HODLR_ENOMEM;
-        }
-        *ar2b = need2;
-      }
-    }
+  PlanSizes ps;
+  if (int rc = measure_plan(M, P, tol, body, &ps)) return rc;
+  if (ps.arena_bytes() > *ar1b) {
+    mat_free(M, *ar1);
+    *ar1 = nullptr;
+    *ar1b = 0;
+    if (int rc = mat_alloc(M, ar1, ps.arena_bytes())) return rc;
+    *ar1b = ps.arena_bytes();
   }
-  return upload_plan(P);
+  if (ps.counters > P.counters_n) {
+    mat_free(M, P.counters);
+    P.counters = nullptr;
+    P.counters_n = 0;
+    if (int rc = mat_alloc(M, &P.counters, ps.counter_bytes())) return rc;
+    P.counters_n = ps.counters;
+    HQ_CUDA_OK(cudaMemset(P.counters, 0, ps.counter_bytes()));
+    HQ_CUDA_OK(cudaStreamSynchronize(cudaStreamLegacy));
+  }
+  if (ps.arena2_bytes() > *ar2b) {
+    mat_free(M, *ar2);
+    *ar2 = nullptr;
+    *ar2b = 0;
+    if (int rc = mat_alloc(M, ar2, ps.arena2_bytes())) return rc;
+    *ar2b = ps.arena2_bytes();
+  }
+  P.recs.clear();
+  P.blob.clear();
+  Planner pl;
+  pl.M = M; pl.P = &P; pl.base = *ar1;
+  pl.base2 = *ar2;
+  pl.base3 = *ar2 + ps.hand;
+  pl.cnt_base = P.counters;
+  P.nevents = 0;
+  pl.int_top = 3 * M->nn; pl.int_high = pl.int_top;
+  pl.cluster = cluster; pl.tol = tol;
+  body(pl);
+  return upload_plan(M, P);
 }
 
-static void free_plan(Plan& P) {
+static void free_plan(hodlr_mat* M, Plan& P) {
   for (auto e : P.events) cudaEventDestroy(e);
   P.events.clear();
   P.nevents = 0;
-  if (P.dblob) cudaFree(P.dblob);
+  mat_free(M, P.dblob);
   P.dblob = nullptr;
-  if (P.counters) cudaFree(P.counters);
+  mat_free(M, P.counters);
   P.counters = nullptr;
   P.counters_n = 0;
   P.recs.clear();
@@ -1141,6 +1243,21 @@ static int upload_values(hodlr_ctx* ctx, hodlr_mat* M, const double* const* leav
   }
   for (int j = 0; j < M->nleaf; ++j)
     if (!leaves || !leaves[j]) return HODLR_EINVAL;
+  // every value must be finite: a NaN or infinity would spread through the whole factorization
+  auto finite = [](const double* p, size_t cnt) {
+    for (size_t i = 0; i < cnt; ++i)
+      if (!std::isfinite(p[i])) return false;
+    return true;
+  };
+  for (int j = 0; j < M->nleaf; ++j) {
+    const size_t w = M->leaf_sizes[j];
+    if (!finite(leaves[j], w * w)) return HODLR_EINVAL;
+  }
+  for (int v = 0; v < M->nn; ++v) {
+    const size_t a = M->hi[2 * v + 1] - M->lo[2 * v + 1], b = M->hi[2 * v + 2] - M->lo[2 * v + 2];
+    if (r12[v] && (!finite(U12[v], a * r12[v]) || !finite(V12[v], b * r12[v]))) return HODLR_EINVAL;
+    if (r21[v] && (!finite(U21[v], b * r21[v]) || !finite(V21[v], a * r21[v]))) return HODLR_EINVAL;
+  }
   cudaStream_t s = ctx->s;
   for (int j = 0; j < M->nleaf; ++j) {
     int w = M->leaf_sizes[j];
@@ -1174,28 +1291,19 @@ static int upload_values(hodlr_ctx* ctx, hodlr_mat* M, const double* const* leav
 void hodlr_free(hodlr_mat* M) {
   if (!M) return;
   if (M->gexec) cudaGraphExecDestroy(M->gexec);
-  free_plan(M->plan);
-  cudaFree(M->store);
-  cudaFree(M->devints);
-  cudaFree(M->dscal);
-  cudaFree(M->dstatus);
-  if (M->snapshot) cudaFree(M->snapshot);
-  if (M->snap_ints) cudaFree(M->snap_ints);
-  if (M->arena) cudaFree(M->arena);
-  if (M->arena2) cudaFree(M->arena2);
-  free_plan(M->splan);
-  if (M->sbuf) cudaFree(M->sbuf);
-  if (M->sarena) cudaFree(M->sarena);
-  if (M->sarena2) cudaFree(M->sarena2);
+  free_plan(M, M->plan);
+  free_plan(M, M->splan);
+  for (auto& kv : M->allocs) cudaFree(kv.first);   // storage, tables, snapshot, arenas, buffers
+  if (M->mem) M->mem->used.fetch_sub(M->held);
+  M->allocs.clear();
   delete M;
 }
 
 }  // extern "C"
 
-// Allocate a matrix of the given partition with all values and ranks zero.
-static int alloc_mat(hodlr_ctx* ctx, int n, int nleaf, const int* leaf_sizes, int rank_cap, hodlr_mat** out) {
-  if (!ctx || !out || !leaf_sizes || n <= 0 || nleaf <= 0 || (nleaf & (nleaf - 1)) || rank_cap < 1 ||
-      rank_cap > 256)
+// Sizes, cluster tree and storage layout of a matrix of the given partition (host only).
+static int layout_mat(hodlr_mat* M, int n, int nleaf, const int* leaf_sizes, int rank_cap) {
+  if (!leaf_sizes || n <= 0 || nleaf <= 0 || (nleaf & (nleaf - 1)) || rank_cap < 1 || rank_cap > 256)
     return HODLR_EINVAL;
   long sum = 0;
   int maxw = 0;
@@ -1205,9 +1313,6 @@ static int alloc_mat(hodlr_ctx* ctx, int n, int nleaf, const int* leaf_sizes, in
     maxw = std::max(maxw, leaf_sizes[j]);
   }
   if (sum != n) return HODLR_EINVAL;
-  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
-  hodlr_mat* M = new (std::nothrow) hodlr_mat();
-  if (!M) return HODLR_ENOMEM;
   M->n = n; M->nleaf = nleaf; M->kc = rank_cap; M->ldl = maxw; M->nn = nleaf - 1;
   int lev = 0;
   while ((1 << lev) < nleaf) ++lev;
@@ -1236,13 +1341,16 @@ static int alloc_mat(hodlr_ctx* ctx, int n, int nleaf, const int* leaf_sizes, in
   }
   M->a_doubles = leafd + afac;
   M->store_doubles = 2 * leafd + afac + tfac;
-  if (cudaMalloc(&M->store, M->store_doubles * sizeof(double)) != cudaSuccess) {
-    cudaGetLastError();
-    delete M;
-    return HODLR_ENOMEM;
-  }
-  cudaMemsetAsync(M->store, 0, M->store_doubles * sizeof(double), ctx->s);
-  double* p = M->store;
+  M->n_devints = 3 * M->nn + 64 * nleaf + 4096;
+  return HODLR_OK;
+}
+
+// Pointers of the leaf and factor pools inside the storage block starting at `store`.
+static void place_mat(hodlr_mat* M, double* store) {
+  const int rank_cap = M->kc;
+  const size_t leafd = (size_t)M->nleaf * M->ldl * M->ldl;
+  double* p = store;
+  M->store = store;
   M->D = p;
   p += leafd;
   M->U12.resize(M->nn); M->V12.resize(M->nn); M->U21.resize(M->nn); M->V21.resize(M->nn);
@@ -1261,11 +1369,33 @@ static int alloc_mat(hodlr_ctx* ctx, int n, int nleaf, const int* leaf_sizes, in
     M->TU[v] = p; p += a * rank_cap;
     M->TV[v] = p; p += b * rank_cap;
   }
-  M->n_devints = 3 * M->nn + 64 * nleaf + 4096;
-  if (cudaMalloc(&M->devints, sizeof(int) * M->n_devints) != cudaSuccess ||
-      cudaMalloc(&M->dscal, sizeof(double) * 32) != cudaSuccess ||
-      cudaMalloc(&M->dstatus, sizeof(int) * 4) != cudaSuccess) {
-    cudaGetLastError();
+}
+
+// Allocate a matrix of the given partition with all values and ranks zero.
+static int alloc_mat(hodlr_ctx* ctx, int n, int nleaf, const int* leaf_sizes, int rank_cap, hodlr_mat** out) {
+  if (!ctx || !out) return HODLR_EINVAL;
+  hodlr_mat* M = new (std::nothrow) hodlr_mat();
+  if (!M) return HODLR_ENOMEM;
+  int rc = layout_mat(M, n, nleaf, leaf_sizes, rank_cap);
+  if (rc != HODLR_OK) {
+    delete M;
+    return rc;
+  }
+  if (cudaSetDevice(ctx->dev) != cudaSuccess) {
+    delete M;
+    return cuda_fail(cudaGetLastError(), __FILE__, __LINE__);
+  }
+  M->mem = ctx->mem;
+  double* store = nullptr;
+  if (mat_alloc(M, &store, M->store_doubles * sizeof(double)) != HODLR_OK) {
+    hodlr_free(M);
+    return HODLR_ENOMEM;
+  }
+  cudaMemsetAsync(store, 0, M->store_doubles * sizeof(double), ctx->s);
+  place_mat(M, store);
+  if (mat_alloc(M, &M->devints, sizeof(int) * M->n_devints) != HODLR_OK ||
+      mat_alloc(M, &M->dscal, sizeof(double) * 32) != HODLR_OK ||
+      mat_alloc(M, &M->dstatus, sizeof(int) * 4) != HODLR_OK) {
     hodlr_free(M);
     return HODLR_ENOMEM;
   }
@@ -1309,9 +1439,10 @@ int hodlr_upload(hodlr_ctx* ctx, hodlr_mat* A, const double* const* leaves, cons
 int hodlr_snapshot(hodlr_ctx* ctx, hodlr_mat* A) {
   if (!ctx || !A) return HODLR_EINVAL;
   if (!A->snapshot) {
-    if (cudaMalloc(&A->snapshot, A->a_doubles * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&A->snap_ints, sizeof(int) * std::max(1, 3 * A->nn)) != cudaSuccess) {
-      cudaGetLastError();
+    if (mat_alloc(A, &A->snapshot, A->a_doubles * sizeof(double)) != HODLR_OK ||
+        mat_alloc(A, &A->snap_ints, sizeof(int) * std::max(1, 3 * A->nn)) != HODLR_OK) {
+      mat_free(A, A->snapshot);
+      A->snapshot = nullptr;
       return HODLR_ENOMEM;
     }
   }
@@ -1331,26 +1462,27 @@ int hodlr_restore(hodlr_ctx* ctx, hodlr_mat* A) {
   return HODLR_OK;
 }
 
+// The factorization: clear the flop counters and status, estimate ||A||_2 unless given, Alg. 2.
+static void plan_qr(Planner& pl, hodlr_mat* A, bool estimate_norm) {
+  Rec z = {};
+  z.type = R_FILL; z.p0 = A->dscal + 1; z.cnt = 16; z.v = 0.0;
+  pl.P->recs.push_back(z);
+  Rec zs = {};
+  zs.type = R_MEMSET_INT; zs.ip = A->dstatus; zs.cnt = sizeof(int) * 4;
+  pl.P->recs.push_back(zs);
+  if (estimate_norm) pl.norm_estimate(30);
+  pl.node(0);
+}
+
 static int ensure_plan(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm) {
   bool est = !(anorm > 0);
   if (A->planned && A->plan_tol == tol && ((A->plan_anorm > 0) == !est)) return HODLR_OK;
-  free_plan(A->plan);
+  free_plan(A, A->plan);
   if (A->gexec) {
     cudaGraphExecDestroy(A->gexec);
     A->gexec = nullptr;
   }
-  int rc = build_plan(A, A->plan, ctx->cluster, tol, [&](Planner& pl) {
-    Rec z = {};
-    z.type = R_FILL; z.p0 = A->dscal + 1; z.cnt = 16; z.v = 0.0;
-    pl.P->recs.push_back(z);
-    Rec zs = {};
-    zs.type = R_MEMSET_INT; zs.ip = A->dstatus; zs.cnt = sizeof(int) * 4;
-    pl.P->recs.push_back(zs);
-    if (est) {
-      pl.norm_estimate(30);
-    }
-    pl.node(0);
-  });
+  int rc = build_plan(A, A->plan, ctx->cluster, tol, [&](Planner& pl) { plan_qr(pl, A, est); });
   if (rc != HODLR_OK) return rc;
   A->planned = true;
   A->plan_tol = tol;
@@ -1588,7 +1720,7 @@ int hodlr_flops(hodlr_ctx* ctx, const hodlr_mat* A, double* out) {
 static int run_temp_plan(hodlr_ctx* ctx, hodlr_mat* A, Plan& P) {
   int rc = run_plan(ctx, A, P);
   cudaError_t e = cudaStreamSynchronize(ctx->s);
-  free_plan(P);
+  free_plan(A, P);
   if (rc) return rc;
   if (e != cudaSuccess) return cuda_fail(e, __FILE__, __LINE__);
   return HODLR_OK;
@@ -1604,11 +1736,11 @@ static int temp_plan(hodlr_ctx* ctx, hodlr_mat* A, F&& body) {
   char* before2 = A->arena2;
   int rc = build_plan(A, P, ctx->cluster, 0.0, body);
   if (rc) {
-    free_plan(P);
+    free_plan(A, P);
     return rc;
   }
   if ((A->arena != before || A->arena2 != before2) && A->planned) {
-    free_plan(A->plan);
+    free_plan(A, A->plan);
     A->planned = false;
     if (A->gexec) {
       cudaGraphExecDestroy(A->gexec);
@@ -1706,14 +1838,12 @@ int hodlr_solve(hodlr_ctx* ctx, const hodlr_mat* Ac, int nrhs, double* B, int ld
     plan_upper_solve(pl, A, 0, B, ldb, nrhs);
   });
   if (rc) return rc;
-  int* flag;
-  HQ_CUDA_OK(cudaMalloc(&flag, sizeof(int)));
-  cudaMemsetAsync(flag, 0, sizeof(int), ctx->s);
-  launch_check_finite(B, ldb, A->n, nrhs, flag, ctx->s);
+  int* flag = A->dstatus + 2;                      // status word 2: non-finite solution seen
+  HQ_CUDA_OK(cudaMemsetAsync(flag, 0, sizeof(int), ctx->s));
+  HQ_CUDA_OK(launch_check_finite(B, ldb, A->n, nrhs, flag, ctx->s));
   int h = 0;
   cudaError_t e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->s);
-  cudaStreamSynchronize(ctx->s);
-  cudaFree(flag);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->s);
   if (e != cudaSuccess) return cuda_fail(e, __FILE__, __LINE__);
   return h ? HODLR_ESINGULAR : HODLR_OK;
 }
@@ -1724,14 +1854,11 @@ int hodlr_solve_async(hodlr_ctx* ctx, hodlr_mat* A, int nrhs, double* B, int ldb
   HQ_CUDA_OK(cudaSetDevice(ctx->dev));
   const int n = A->n;
   if (!A->splan.dblob || A->splan_nrhs < nrhs) {
-    free_plan(A->splan);
-    if (A->sbuf) cudaFree(A->sbuf);
+    free_plan(A, A->splan);
+    mat_free(A, A->sbuf);
     A->sbuf = nullptr;
     int cap = std::max(nrhs, std::max(1, A->splan_nrhs));
-    if (cudaMalloc(&A->sbuf, sizeof(double) * (size_t)n * cap) != cudaSuccess) {
-      cudaGetLastError();
-      return HODLR_ENOMEM;
-    }
+    if (int rc = mat_alloc(A, &A->sbuf, sizeof(double) * (size_t)n * cap)) return rc;
     int rc = build_plan(A, A->splan, ctx->cluster, 0.0, [&](Planner& pl) {
       plan_apply(pl, A, cap, A->sbuf, n, true);
       plan_upper_solve(pl, A, 0, A->sbuf, n, cap);
@@ -1823,12 +1950,11 @@ int hodlr_truncate(hodlr_ctx* ctx, int nL, int nR, int K, const double* L, const
   hodlr_mat M;
   M.n = nL; M.nleaf = 1; M.nn = 0; M.kc = kmax; M.ldl = 1;
   M.n_devints = 64;
+  M.mem = ctx->mem;
   int rc = HODLR_OK;
-  if (cudaMalloc(&M.devints, sizeof(int) * 64) != cudaSuccess || cudaMalloc(&M.dstatus, sizeof(int) * 4) != cudaSuccess ||
-      cudaMalloc(&M.dscal, sizeof(double) * 32) != cudaSuccess) {
-    cudaGetLastError();
+  if (mat_alloc(&M, &M.devints, sizeof(int) * 64) != HODLR_OK || mat_alloc(&M, &M.dstatus, sizeof(int) * 4) != HODLR_OK ||
+      mat_alloc(&M, &M.dscal, sizeof(double) * 32) != HODLR_OK)
     rc = HODLR_ENOMEM;
-  }
   Plan P;
   if (!rc) {
     cudaMemsetAsync(M.devints, 0, sizeof(int) * 64, ctx->s);
@@ -1855,13 +1981,10 @@ int hodlr_truncate(hodlr_ctx* ctx, int nL, int nR, int K, const double* L, const
     if (cudaGetLastError() != cudaSuccess) rc = HODLR_ECUDA;
     else if (st == HODLR_ERANK) rc = HODLR_ERANK;
   }
-  free_plan(P);
-  cudaFree(M.devints);
-  cudaFree(M.dstatus);
-  cudaFree(M.dscal);
-  if (M.arena) cudaFree(M.arena);
-  if (M.arena2) cudaFree(M.arena2);
-  M.devints = nullptr; M.dstatus = nullptr; M.dscal = nullptr; M.arena = nullptr; M.arena2 = nullptr;
+  free_plan(&M, P);
+  for (auto& kv : M.allocs) cudaFree(kv.first);    // tables and arenas of the shell
+  if (M.mem) M.mem->used.fetch_sub(M.held);
+  M.allocs.clear();
   return rc;
 }
 
@@ -1883,6 +2006,62 @@ int hodlr_build_dense(hodlr_ctx* ctx, int n, int nleaf, const int* leaf_sizes, c
     return rc;
   }
   *out = M;
+  return HODLR_OK;
+}
+
+int hodlr_ctx_set_memory_limit(hodlr_ctx* ctx, size_t bytes) {
+  if (!ctx) return HODLR_EINVAL;
+  ctx->mem->limit.store((long long)bytes);
+  return HODLR_OK;
+}
+
+int hodlr_ctx_memory_used(hodlr_ctx* ctx, size_t* bytes) {
+  if (!ctx || !bytes) return HODLR_EINVAL;
+  const long long u = ctx->mem->used.load();
+  *bytes = u > 0 ? (size_t)u : 0;
+  return HODLR_OK;
+}
+
+int hodlr_device_bytes(const hodlr_mat* A, size_t* bytes) {
+  if (!A || !bytes) return HODLR_EINVAL;
+  *bytes = A->held > 0 ? (size_t)A->held : 0;
+  return HODLR_OK;
+}
+
+int hodlr_footprint(int n, int nleaf, const int* leaf_sizes, int rank_cap, int estimate_norm, int with_snapshot,
+                    int nrhs, size_t* bytes) {
+  if (!bytes || nrhs < 0 || nrhs > 1024) return HODLR_EINVAL;
+  // A host-only shell of the matrix: its pools are laid out from a fixed, never dereferenced base,
+  // so the planner's measuring pass sees the same sizes as for a real matrix.
+  hodlr_mat S;
+  int rc = layout_mat(&S, n, nleaf, leaf_sizes, rank_cap);
+  if (rc) return rc;
+  static double fake[1];
+  place_mat(&S, fake);
+  S.devints = reinterpret_cast<int*>(fake);
+  S.dscal = fake;
+  S.dstatus = reinterpret_cast<int*>(fake);
+  size_t total = S.store_doubles * sizeof(double) + sizeof(int) * S.n_devints + sizeof(double) * 32 + sizeof(int) * 4;
+  if (with_snapshot) total += S.a_doubles * sizeof(double) + sizeof(int) * std::max(1, 3 * S.nn);
+  Plan P;
+  PlanSizes ps;
+  rc = measure_plan(&S, P, 1.0, [&](Planner& pl) { plan_qr(pl, &S, estimate_norm != 0); }, &ps);
+  if (rc) return rc;
+  total += ps.arena_bytes() + ps.arena2_bytes() + (ps.counters ? ps.counter_bytes() : 0) + ps.blob_bytes();
+  if (nrhs > 0) {
+    // hodlr_solve_async: staging buffer, its own arenas and plan
+    S.sbuf = fake;
+    Plan Q;
+    PlanSizes qs;
+    rc = measure_plan(&S, Q, 0.0, [&](Planner& pl) {
+      plan_apply(pl, &S, nrhs, S.sbuf, S.n, true);
+      plan_upper_solve(pl, &S, 0, S.sbuf, S.n, nrhs);
+    }, &qs);
+    if (rc) return rc;
+    total += sizeof(double) * (size_t)S.n * nrhs + qs.arena_bytes() + qs.arena2_bytes() +
+             (qs.counters ? qs.counter_bytes() : 0) + qs.blob_bytes();
+  }
+  *bytes = total;
   return HODLR_OK;
 }
 

@@ -24,7 +24,11 @@ __device__ inline double warp_sum(double v) {
 }
 
 // ----------------------------------------------------------------------------------- GEMM
-constexpr int BM = 32, BN = 32, BK = 16, GT = 256;
+// Tiles of BM x BN outputs, k in chunks of BK, GT threads.  Each thread owns a register
+// micro-tile of MR x NR outputs (MR consecutive rows, NR consecutive columns).
+constexpr int BM = kGemmBM, BN = kGemmBN, BK = 16, GT = 256, MR = 4, NR = 2;
+constexpr int LDA_S = BM + 2, LDB_S = BN + 2;   // shared row strides: 16-byte aligned, few conflicts
+static_assert(BM * BN == GT * MR * NR, "one micro-tile per thread covers the tile");
 
 __device__ inline double masked(const double* M, int ld, int r, int c, int mask) {
   if (mask == kMaskNone) return M[r + (size_t)c * ld];
@@ -76,51 +80,52 @@ __global__ void __launch_bounds__(GT, 4) gemm_kernel(const GemmDesc* __restrict_
   }
   const int row0 = tm * BM, col0 = tn * BN;
   const bool to_part = d.ksplit > 1;
-  if (row0 >= m || col0 >= n) {
-    // nothing to compute; partial slots of an active split still need zeros
-    return;
-  }
+  if (row0 >= m || col0 >= n) return;   // nothing to compute (partial slots beyond k unused)
   int kchunk = (k + d.ksplit - 1) / d.ksplit;
   kchunk = (kchunk + BK - 1) / BK * BK;
   const int k0 = split * kchunk;
   const int k1 = min(k, k0 + kchunk);
 
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN + 1];
+  __shared__ __align__(16) double As[BK][LDA_S];
+  __shared__ __align__(16) double Bs[BK][LDB_S];
   // The outputs of this tile that exist (ma x na: sizes are known only on the device, and most
-  // products here multiply by a block of a few columns) are dealt to the threads in
-  // column-major order, one per thread per pass, up to four passes for a full 32 x 32 tile.
-  // A warp whose outputs all lie beyond ma x na issues nothing, so the FP64 pipe, the limit
-  // of this kernel, spends no instruction on padding rows or columns except in the last warp
-  // of a pass (its idle lanes repeat the last output and do not store).  Two FMA chains per
-  // output (even and odd k) halve the dependent latency.
+  // products here multiply by a block of a few columns) are covered by micro-tiles of MR x NR,
+  // dealt to the threads in column-major order (consecutive threads, consecutive row groups).
+  // A warp whose micro-tiles all lie beyond ma x na issues nothing, so the FP64 pipe, the limit
+  // of this kernel, spends instructions only on the partial row / column groups at the edges.
+  // The MR x NR accumulators are independent FMA chains (ILP 8 per thread).
   const int ma = min(BM, m - row0), na = min(BN, n - col0);
-  const int nout = ma * na;
-  const int wbase = threadIdx.x & ~31;
-  int oi[4], oj[4];
+  const int mrow = (ma + MR - 1) / MR, mcol = (na + NR - 1) / NR;
+  const int nmic = mrow * mcol;
+  const int tid = threadIdx.x;
+  const bool active = tid < nmic;
+  const bool warp_active = (tid & ~31) < nmic;            // warp-uniform
+  const int mi = active ? tid % mrow : 0, nj = active ? tid / mrow : 0;
+  const int r0 = mi * MR, c0 = nj * NR;
+  double acc[MR][NR];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int o = min((int)threadIdx.x + GT * u, nout - 1);
-    oj[u] = o / ma;
-    oi[u] = o - oj[u] * ma;
-  }
-  double acc[4][2];
+  for (int u = 0; u < MR; ++u)
 #pragma unroll
-  for (int u = 0; u < 4; ++u) acc[u][0] = acc[u][1] = 0.0;
+    for (int v = 0; v < NR; ++v) acc[u][v] = 0.0;
   // Operand tiles pass through registers: the loads of chunk kk + BK are in flight while chunk
-  // kk is multiplied.  Element e = threadIdx.x + GT p (p = 0, 1) of each tile is mapped so that
-  // consecutive threads read consecutive addresses of the stored (possibly transposed) operand.
-  double pa[2], pb[2];
+  // kk is multiplied.  Element e = tid + GT p of each tile is mapped so that consecutive
+  // threads read consecutive addresses of the stored (possibly transposed) operand.
+  constexpr int PA = BM * BK / GT, PB = BN * BK / GT;
+  double pa[PA], pb[PB];
   auto fetch = [&](int kk) {
     const int kl = min(BK, k1 - kk);
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-      const int e = threadIdx.x + GT * p;
+    for (int p = 0; p < PA; ++p) {
+      const int e = tid + GT * p;
       const int i = d.ta ? e / BK : e % BM, l = d.ta ? e % BK : e / BM;
       double v = 0.0;
       if (i < ma && l < kl)
         v = d.ta ? masked(d.A, d.lda, kk + l, row0 + i, d.mska) : masked(d.A, d.lda, row0 + i, kk + l, d.mska);
       pa[p] = v;
+    }
+#pragma unroll
+    for (int p = 0; p < PB; ++p) {
+      const int e = tid + GT * p;
       const int j = d.tb ? e % BN : e / BK, lb = d.tb ? e / BN : e % BK;
       double w = 0.0;
       if (j < na && lb < kl)
@@ -132,53 +137,57 @@ __global__ void __launch_bounds__(GT, 4) gemm_kernel(const GemmDesc* __restrict_
   for (int kk = k0; kk < k1; kk += BK) {
     const int kl = min(BK, k1 - kk);
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-      const int e = threadIdx.x + GT * p;
+    for (int p = 0; p < PA; ++p) {
+      const int e = tid + GT * p;
       const int i = d.ta ? e / BK : e % BM, l = d.ta ? e % BK : e / BM;
       As[l][i] = pa[p];
+    }
+#pragma unroll
+    for (int p = 0; p < PB; ++p) {
+      const int e = tid + GT * p;
       const int j = d.tb ? e % BN : e / BK, lb = d.tb ? e / BN : e % BK;
-      if (j < na) Bs[lb][j] = pb[p];
+      Bs[lb][j] = pb[p];
     }
     __syncthreads();
     if (kk + BK < k1) fetch(kk + BK);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (wbase + GT * u < nout) {                      // warp-uniform
-        const int i = oi[u], j = oj[u];
-        if (kl == BK) {
-#pragma unroll
-          for (int l = 0; l < BK; l += 2) {
-            acc[u][0] = fma(As[l][i], Bs[l][j], acc[u][0]);
-            acc[u][1] = fma(As[l + 1][i], Bs[l + 1][j], acc[u][1]);
-          }
-        } else {
-          int l = 0;
-          for (; l + 1 < kl; l += 2) {
-            acc[u][0] = fma(As[l][i], Bs[l][j], acc[u][0]);
-            acc[u][1] = fma(As[l + 1][i], Bs[l + 1][j], acc[u][1]);
-          }
-          if (l < kl) acc[u][0] = fma(As[l][i], Bs[l][j], acc[u][0]);
-        }
+    if (warp_active) {
+      // rows / columns beyond ma / na hold zeros: a partial micro-tile computes zeros there
+#pragma unroll 8
+      for (int l = 0; l < kl; ++l) {
+        const double2 a01 = *reinterpret_cast<const double2*>(&As[l][r0]);
+        const double2 a23 = *reinterpret_cast<const double2*>(&As[l][r0 + 2]);
+        const double2 b01 = *reinterpret_cast<const double2*>(&Bs[l][c0]);
+        acc[0][0] = fma(a01.x, b01.x, acc[0][0]);
+        acc[1][0] = fma(a01.y, b01.x, acc[1][0]);
+        acc[2][0] = fma(a23.x, b01.x, acc[2][0]);
+        acc[3][0] = fma(a23.y, b01.x, acc[3][0]);
+        acc[0][1] = fma(a01.x, b01.y, acc[0][1]);
+        acc[1][1] = fma(a01.y, b01.y, acc[1][1]);
+        acc[2][1] = fma(a23.x, b01.y, acc[2][1]);
+        acc[3][1] = fma(a23.y, b01.y, acc[3][1]);
       }
     }
     __syncthreads();
   }
   double alpha = d.alpha;
   if (d.alpha_ref) alpha *= *d.alpha_ref;
+  if (active) {
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    if ((int)threadIdx.x + GT * u < nout) {
-      const int gi = row0 + oi[u], gj = col0 + oj[u];
-      const double sacc = acc[u][0] + acc[u][1];
-      if (to_part) {
-        d.part[(size_t)split * d.m * d.n + gi + (size_t)gj * d.m] = sacc;
-      } else {
-        double* c = d.C + gi + (size_t)gj * d.ldc;
-        double v = alpha * sacc;
-        if (d.beta != 0.0) v = fma(d.beta, *c, v);
-        *c = v;
+    for (int v = 0; v < NR; ++v)
+#pragma unroll
+      for (int u = 0; u < MR; ++u) {
+        if (r0 + u < ma && c0 + v < na) {
+          const int gi = row0 + r0 + u, gj = col0 + c0 + v;
+          if (to_part) {
+            d.part[(size_t)split * d.m * d.n + gi + (size_t)gj * d.m] = acc[u][v];
+          } else {
+            double* c = d.C + gi + (size_t)gj * d.ldc;
+            double val = alpha * acc[u][v];
+            if (d.beta != 0.0) val = fma(d.beta, *c, val);
+            *c = val;
+          }
+        }
       }
-    }
   }
   if (!to_part || d.tile_count == nullptr) return;
   // split-K: the last split to finish this tile sums the partials in split order (the result
@@ -197,17 +206,14 @@ __global__ void __launch_bounds__(GT, 4) gemm_kernel(const GemmDesc* __restrict_
   int nsp = 0;
   for (int sp = 0; sp < d.ksplit; ++sp)
     if (sp * kchunk < k) nsp = sp + 1;
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    if ((int)threadIdx.x + GT * u < nout) {
-      const int gi = row0 + oi[u], gj = col0 + oj[u];
-      double sacc = 0.0;
-      for (int sp = 0; sp < nsp; ++sp) sacc += __ldcg(&d.part[(size_t)sp * d.m * d.n + gi + (size_t)gj * d.m]);
-      double* c = d.C + gi + (size_t)gj * d.ldc;
-      double v = alpha * sacc;
-      if (d.beta != 0.0) v = fma(d.beta, *c, v);
-      *c = v;
-    }
+  for (int o = tid; o < ma * na; o += GT) {
+    const int gi = row0 + o % ma, gj = col0 + o / ma;
+    double sacc = 0.0;
+    for (int sp = 0; sp < nsp; ++sp) sacc += __ldcg(&d.part[(size_t)sp * d.m * d.n + gi + (size_t)gj * d.m]);
+    double* c = d.C + gi + (size_t)gj * d.ldc;
+    double val = alpha * sacc;
+    if (d.beta != 0.0) val = fma(d.beta, *c, val);
+    *c = val;
   }
 }
 

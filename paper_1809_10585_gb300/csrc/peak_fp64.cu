@@ -3,13 +3,12 @@
 // not by memory traffic).  Two instruction paths are timed:
 //
 //  * DFMA: each thread runs 8 independent fused multiply-add chains (enough independent work
-//    to hide the FMA latency), grid of `blocks_per_sm` x SM count CTAs of 256 threads;
+//    to hide the FMA latency), grid of 4 CTAs of 256 threads per SM;
 //  * DMMA: the FP64 tensor-core instruction mma.sync.m8n8k4 (one 8x8x4 product, 512 flops
 //    per warp instruction), 8 independent accumulator pairs per warp, same grid.
 //
 // The elapsed time is taken with CUDA events around each launch on a private stream, best of
-// `reps` launches; the SM clock during the launch is the clock64() cycles of CTA 0 divided by
-// that time.
+// `reps` launches.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,28 +22,23 @@ constexpr int kPeakThreads = 256;
 constexpr int kPeakChains = 8;
 constexpr int kPeakUnroll = 16;
 
-__global__ void __launch_bounds__(kPeakThreads) dfma_peak_kernel(double* sink, long long* cycles, int iters,
-                                                                 double a, double b) {
+__global__ void __launch_bounds__(kPeakThreads) dfma_peak_kernel(double* sink, int iters, double a, double b) {
   double x[kPeakChains];
 #pragma unroll
   for (int c = 0; c < kPeakChains; ++c) x[c] = 1e-3 * (threadIdx.x + 1) + c;
-  const long long t0 = clock64();
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
     for (int u = 0; u < kPeakUnroll; ++u)
 #pragma unroll
       for (int c = 0; c < kPeakChains; ++c) x[c] = fma(x[c], a, b);
   }
-  const long long t1 = clock64();
   double s = 0.0;
 #pragma unroll
   for (int c = 0; c < kPeakChains; ++c) s += x[c];
   if (s == -1.0) sink[0] = s;                     // never taken; keeps the chains live
-  if (blockIdx.x == 0 && threadIdx.x == 0) cycles[0] = t1 - t0;
 }
 
-__global__ void __launch_bounds__(kPeakThreads) dmma_peak_kernel(double* sink, long long* cycles, int iters,
-                                                                 double a, double b) {
+__global__ void __launch_bounds__(kPeakThreads) dmma_peak_kernel(double* sink, int iters, double a, double b) {
   double c0[kPeakChains], c1[kPeakChains];
 #pragma unroll
   for (int c = 0; c < kPeakChains; ++c) {
@@ -52,7 +46,6 @@ __global__ void __launch_bounds__(kPeakThreads) dmma_peak_kernel(double* sink, l
     c1[c] = 2e-3 * threadIdx.x - c;
   }
   const double av = a * (1.0 + 1e-6 * (threadIdx.x & 31)), bv = b;
-  const long long t0 = clock64();
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
     for (int u = 0; u < kPeakUnroll; ++u)
@@ -62,18 +55,15 @@ __global__ void __launch_bounds__(kPeakThreads) dmma_peak_kernel(double* sink, l
                      : "+d"(c0[c]), "+d"(c1[c])
                      : "d"(av), "d"(bv));
   }
-  const long long t1 = clock64();
   double s = 0.0;
 #pragma unroll
   for (int c = 0; c < kPeakChains; ++c) s += c0[c] + c1[c];
   if (s == -1.0) sink[0] = s;
-  if (blockIdx.x == 0 && threadIdx.x == 0) cycles[0] = t1 - t0;
 }
 
 }  // namespace hq
 
-extern "C" int hodlr_fp64_peak(int device, int iters, int reps, double* dfma_tflops, double* dmma_tflops,
-                               double* sm_mhz) {
+extern "C" int hodlr_fp64_peak(int device, int iters, int reps, double* dfma_tflops, double* dmma_tflops) {
   using namespace hq;
   if (iters < 1 || reps < 1 || !dfma_tflops || !dmma_tflops) return HODLR_EINVAL;
   int ndev = 0;
@@ -86,17 +76,16 @@ extern "C" int hodlr_fp64_peak(int device, int iters, int reps, double* dfma_tfl
   HQ_CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
   const int blocks = 4 * sms;          // 4 x 256 threads per SM: 32 warps of independent chains
   double* sink = nullptr;
-  long long* cyc = nullptr;
   cudaStream_t s = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = HODLR_OK;
-  if (cudaMalloc(&sink, sizeof(double)) != cudaSuccess || cudaMalloc(&cyc, sizeof(long long)) != cudaSuccess ||
+  if (cudaMalloc(&sink, sizeof(double)) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
       cudaEventCreate(&e1) != cudaSuccess) {
     cudaGetLastError();
     rc = HODLR_ENOMEM;
   }
-  double best[2] = {0.0, 0.0}, mhz = 0.0;
+  double best[2] = {0.0, 0.0};
   for (int kind = 0; kind < 2 && rc == HODLR_OK; ++kind) {
     // flops of one launch: DFMA 2 per lane per FMA; DMMA 2 * 8 * 8 * 4 per warp instruction
     const double per_iter = kind == 0 ? 2.0 * kPeakChains * kPeakUnroll * kPeakThreads
@@ -104,8 +93,8 @@ extern "C" int hodlr_fp64_peak(int device, int iters, int reps, double* dfma_tfl
     const double flops = per_iter * iters * blocks;
     for (int r = 0; r <= reps && rc == HODLR_OK; ++r) {   // launch 0 warms up
       cudaEventRecord(e0, s);
-      if (kind == 0) dfma_peak_kernel<<<blocks, kPeakThreads, 0, s>>>(sink, cyc, iters, 0.9999999, 1e-7);
-      else dmma_peak_kernel<<<blocks, kPeakThreads, 0, s>>>(sink, cyc, iters, 0.9999999, 1e-7);
+      if (kind == 0) dfma_peak_kernel<<<blocks, kPeakThreads, 0, s>>>(sink, iters, 0.9999999, 1e-7);
+      else dmma_peak_kernel<<<blocks, kPeakThreads, 0, s>>>(sink, iters, 0.9999999, 1e-7);
       cudaEventRecord(e1, s);
       if (cudaStreamSynchronize(s) != cudaSuccess) {
         rc = cuda_fail(cudaGetLastError(), __FILE__, __LINE__);
@@ -113,24 +102,16 @@ extern "C" int hodlr_fp64_peak(int device, int iters, int reps, double* dfma_tfl
       }
       float ms = 0.0f;
       cudaEventElapsedTime(&ms, e0, e1);
-      long long c = 0;
-      cudaMemcpy(&c, cyc, sizeof(long long), cudaMemcpyDeviceToHost);
       if (r == 0 || ms <= 0.0f) continue;
-      const double tf = flops / (ms * 1e-3) / 1e12;
-      if (tf > best[kind]) {
-        best[kind] = tf;
-        if (kind == 0) mhz = (double)c / (ms * 1e3);     // cycles of CTA 0 over the launch time
-      }
+      best[kind] = std::max(best[kind], flops / (ms * 1e-3) / 1e12);
     }
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (s) cudaStreamDestroy(s);
   if (sink) cudaFree(sink);
-  if (cyc) cudaFree(cyc);
   if (rc) return rc;
   *dfma_tflops = best[0];
   *dmma_tflops = best[1];
-  if (sm_mhz) *sm_mhz = mhz;
   return HODLR_OK;
 }

@@ -10,58 +10,79 @@ import itertools
 
 import numpy as np
 
-GT, BM, BN, BK = 256, 32, 32, 16           # gemm_kernel: threads, tile rows, tile columns, k chunk
+GT, BM, BN, BK, MR, NR = 256, 64, 32, 16, 4, 2   # gemm_kernel: threads, tile, k chunk, micro-tile
+LDA_S, LDB_S = BM + 2, BN + 2                      # shared-memory row strides of the operand tiles
 
 
 def shfl_xor(vals, o):
     return [vals[l ^ o] for l in range(32)]
 
 
-def test_gemm_outputs_dealt_densely():
-    """gemm_kernel: the ma x na outputs of a tile go to threads in column-major order, one per
-    thread per pass; only warps holding an output issue the FMA chain, only lanes holding one
-    store, and the wasted lanes of a pass are those of its last warp."""
+def test_gemm_micro_tiles_cover_outputs_once():
+    """gemm_kernel: the ma x na outputs of a tile are covered by MR x NR micro-tiles dealt to
+    threads in column-major order; every existing output is stored by exactly one thread, every
+    micro-tile lies inside the BM x BN tile (shared reads stay in bounds), only warps holding a
+    micro-tile issue FMAs, and the FMAs spent beyond ma x na are those of the edge micro-tiles."""
     for ma in range(1, BM + 1):
         for na in range(1, BN + 1):
-            nout = ma * na
+            mrow, mcol = -(-ma // MR), -(-na // NR)
+            nmic = mrow * mcol
+            assert nmic <= GT
             stored = []
-            for u in range(4):
-                busy = 0
-                for t in range(GT):
-                    o = min(t + GT * u, nout - 1)
-                    j = o // ma
-                    i = o - j * ma
-                    assert 0 <= i < ma and 0 <= j < na
-                    computes = (t & ~31) + GT * u < nout
-                    if computes:
-                        busy += 1
-                    if t + GT * u < nout:
-                        assert computes
-                        stored.append((i, j))
-                assert busy - max(0, min(GT, nout - GT * u)) < 32
+            computing_warps = set()
+            for t in range(GT):
+                active = t < nmic
+                if (t & ~31) < nmic:
+                    computing_warps.add(t // 32)
+                if not active:
+                    continue
+                mi, nj = t % mrow, t // mrow
+                r0, c0 = mi * MR, nj * NR
+                assert r0 + MR <= BM and c0 + NR <= BN
+                assert (r0 * 8) % 16 == 0 and (c0 * 8) % 16 == 0          # double2 reads aligned
+                for v in range(NR):
+                    for u in range(MR):
+                        if r0 + u < ma and c0 + v < na:
+                            stored.append((r0 + u, c0 + v))
             assert sorted(stored) == [(i, j) for i in range(ma) for j in range(na)]
+            assert computing_warps == set(range(-(-nmic // 32)))
+            waste = nmic * MR * NR - ma * na
+            assert waste <= (MR - 1) * mcol * NR + (NR - 1) * mrow * MR
+
+
+def test_gemm_shared_strides_keep_vector_reads_aligned():
+    """Rows of As / Bs start on 16-byte boundaries, so the double2 reads of a micro-tile's rows
+    and columns are aligned for every k in the chunk."""
+    for l in range(BK):
+        assert (l * LDA_S * 8) % 16 == 0 and (l * LDB_S * 8) % 16 == 0
 
 
 def test_gemm_operand_tiles_covered_once_and_coalesced():
-    """gemm_kernel prefetch: element e = t + 256 p (p = 0, 1) of the 32 x 16 A tile and the
-    16 x 32 B tile; consecutive threads read consecutive addresses of the stored operand."""
+    """gemm_kernel prefetch: element e = t + 256 p of the 64 x 16 A tile (p < 4) and of the
+    16 x 32 B tile (p < 2); consecutive threads read consecutive addresses of the stored operand."""
+    PA, PB = BM * BK // GT, BN * BK // GT
     for ta in (0, 1):
         cells = []
-        for e in range(2 * GT):
+        for e in range(PA * GT):
             i, l = (e // BK, e % BK) if ta else (e % BM, e // BM)
             cells.append((i, l))
         assert sorted(cells) == [(i, l) for i in range(BM) for l in range(BK)]
         lda = 1000
-        for w in range(0, 2 * GT, 32):          # a warp's 32 consecutive elements
+        for w in range(0, PA * GT, 32):          # a warp's 32 consecutive elements
             addr = [(l + i * lda) if ta else (i + l * lda) for i, l in cells[w:w + 32]]
             runs = sum(1 for a, b in zip(addr, addr[1:]) if b != a + 1)
             assert runs <= 1                     # at most two contiguous runs per warp
     for tb in (0, 1):
         cells = []
-        for e in range(2 * GT):
+        for e in range(PB * GT):
             j, lb = (e % BN, e // BN) if tb else (e // BK, e % BK)
             cells.append((j, lb))
         assert sorted(cells) == [(j, l) for j in range(BN) for l in range(BK)]
+        ldb = 1000
+        for w in range(0, PB * GT, 32):
+            addr = [(j + lb * ldb) if tb else (lb + j * ldb) for j, lb in cells[w:w + 32]]
+            runs = sum(1 for a, b in zip(addr, addr[1:]) if b != a + 1)
+            assert runs <= 1
 
 
 def _vote_search(work0, item):

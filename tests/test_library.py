@@ -54,3 +54,60 @@ def test_product_never_imports_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", text, re.M), f
+
+
+# --------------------------------------------------------------- memory footprint (host only)
+def _children(leaf_sizes):
+    """(range of child 1, range of child 2) of every internal node of the cluster tree."""
+    import workloads as W
+    rng = W.node_ranges(leaf_sizes)
+    return [(rng[2 * v + 1], rng[2 * v + 2]) for v in range(len(leaf_sizes) - 1)]
+
+
+def _storage_doubles(n, leaf_sizes, kc):
+    """Storage of the flattened HODLR container (Sec. 2.1, O(k n log n)): dense leaves of A and
+    T padded to the largest leaf, plus four factor blocks of A and two of T per internal node at
+    rank capacity kc."""
+    import workloads as W
+    nleaf = len(leaf_sizes)
+    maxw = max(leaf_sizes)
+    leafd = nleaf * maxw * maxw
+    fac = 0
+    for (lo1, hi1), (lo2, hi2) in _children(leaf_sizes):
+        fac += 3 * ((hi1 - lo1) + (hi2 - lo2)) * kc
+    return 2 * leafd + fac
+
+
+@pytest.mark.parametrize("n,nmin,kc", [(1024, 128, 64), (8192, 256, 128), (1000, 100, 32), (96, 128, 16)])
+def test_footprint_counts_storage_and_grows_with_rank_capacity(libpath, n, nmin, kc):
+    import workloads as W
+    from paper_1809_10585_gb300 import binding as B
+    ls = W.balanced_leaf_sizes(n, nmin)
+    base = B.footprint(n, ls, kc, estimate_norm=True)
+    store = 8 * _storage_doubles(n, ls, kc)
+    assert base > store                               # storage plus tables, plans and scratch
+    # a snapshot adds exactly the A part of the storage and the rank table
+    snap = B.footprint(n, ls, kc, estimate_norm=True, with_snapshot=True) - base
+    leafd = len(ls) * max(ls) ** 2
+    afac = sum(2 * ((h1 - l1) + (h2 - l2)) * kc for (l1, h1), (l2, h2) in _children(ls))
+    assert snap == 8 * (leafd + afac) + 4 * max(1, 3 * (len(ls) - 1))
+    # more rank capacity, more bytes; a solve plan adds at least its staging buffer
+    if len(ls) > 1:
+        assert B.footprint(n, ls, 2 * kc) > base
+    else:                                             # one dense leaf: no factors, no ranks
+        assert B.footprint(n, ls, 2 * kc) == base
+    assert B.footprint(n, ls, kc, nrhs=8) - base >= 8 * n * 8
+    # the norm estimate's plan is extra work, never less memory
+    assert B.footprint(n, ls, kc, estimate_norm=False) <= base
+
+
+def test_footprint_rejects_bad_partitions(libpath):
+    import ctypes as C
+    from paper_1809_10585_gb300 import binding as B
+    out = C.c_size_t()
+    sizes = (C.c_int * 3)(100, 100, 100)                       # not a power of two of leaves
+    assert B.lib().hodlr_footprint(300, 3, sizes, 32, 1, 0, 0, C.byref(out)) == B.HODLR_EINVAL
+    sizes = (C.c_int * 2)(100, 100)
+    assert B.lib().hodlr_footprint(201, 2, sizes, 32, 1, 0, 0, C.byref(out)) == B.HODLR_EINVAL   # sum != n
+    assert B.lib().hodlr_footprint(200, 2, sizes, 0, 1, 0, 0, C.byref(out)) == B.HODLR_EINVAL    # rank_cap
+    assert B.lib().hodlr_footprint(200, 2, sizes, 32, 1, 0, 2000, C.byref(out)) == B.HODLR_EINVAL
