@@ -277,6 +277,7 @@ def gpu_arm(args):
     cmax = ctx.cluster
     ccl = args.cluster if args.cluster > 0 else (cmax if nb == 1 else min(cmax, BATCH_CLUSTER))
     ctx.cluster = ccl
+    ctx.set_batch_group(args.group)
     mats = [B.Matrix(ctx, x, rank_cap=args.rank_cap) for x in inps]
     M = mats[0]
     for m in mats:
@@ -424,14 +425,20 @@ def gpu_arm(args):
                     "kind_gflop": {k: round(v["flops"] / 1e9, 4) for k, v in prof.items()},
                     "kind_share": {k: round(v["ms"] / max(1e-9, sum(x["ms"] for x in prof.values())), 4)
                                    for k, v in prof.items()}}}
-    gpu_launches = sum(v["launches"] for v in prof.values()) * args.steps * nb
+    # matrices of one structure share one merged schedule: a step launches one factorization's
+    # kernels per group (each launch carrying the descriptors of every matrix of the group)
+    groups = 1 if nb == 1 else (-(-nb // args.group) if args.group > 0 else 1)
+    gpu_launches = sum(v["launches"] for v in prof.values()) * args.steps * groups
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N, "nmin": NMIN, "rank": K, "col_scale_decades": DECADES,
                        "tol": TOL, "rank_cap": args.rank_cap, "batch": nb, "cluster": ccl,
-                       "batching": "independent seeded matrices of the workload factored concurrently, one CUDA graph per step",
+                       "group": args.group,
+                       "batching": "independent seeded matrices of the workload factored together: one merged "
+                                   "launch schedule per group of matrices (each launch carries every matrix's "
+                                   "descriptors), one CUDA graph per step",
                        "l2": "flushed (256 MiB write) between timed steps",
                        "parallelism": f"replicas x{ws}", "anorm": anorm},
             "effective_gflops": nb * flops_total / (ms_per_step / 1e3) / 1e9,
@@ -491,6 +498,8 @@ def main():
                     help="rank capacity of the stored factors (a factorization that needs more fails)")
     ap.add_argument("--no-served", action="store_true",
                     help="skip the served request stream (p50/p99 latency)")
+    ap.add_argument("--group", type=int, default=0,
+                    help="most matrices per merged launch schedule (0: all matrices of the workload in one)")
     ap.add_argument("--peaks", action="store_true",
                     help="measure the FP64 DFMA / DMMA throughput of the GPU and exit")
     ap.add_argument("--cluster", type=int, default=0,

@@ -70,6 +70,10 @@ int hodlr_ctx_get_cluster(hodlr_ctx* ctx, int* cluster);
  * the cluster's shared memory is factored in the global-memory form).  Graphs captured earlier
  * are re-captured on their next call.  HODLR_EINVAL for a value below 1. */
 int hodlr_ctx_set_concurrency(hodlr_ctx* ctx, int factorizations);
+/* Largest number of matrices of one structure that hodlr_qr_batched and hodlr_qr_batched_graph
+ * factor with one merged schedule (0, the default: no limit).  Smaller groups run as several
+ * schedules side by side on separate streams.  Results do not depend on it.  HODLR_EINVAL below 0. */
+int hodlr_ctx_set_batch_group(hodlr_ctx* ctx, int max_matrices);
 int hodlr_ctx_get_concurrency(hodlr_ctx* ctx, int* factorizations);
 /* Block until all queued work on the context's stream is done. */
 int hodlr_sync(hodlr_ctx* ctx);
@@ -153,9 +157,12 @@ int hodlr_qr_profile(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm, dou
  * hodlr_qr_batched — cross-matrix batching: factor `count` distinct matrices A[0..count-1]
  * (any partitions, ranks and sizes), each as hodlr_qr(tol, anorm) would up to rounding (while
  * the batch runs, the kernels take the forms of hodlr_ctx_set_concurrency(count)), concurrently
- * on the device.  Each matrix runs on its own pair of streams owned by the context; the pairs are
- * forked from and joined back into the context's stream, so later work on that stream sees
- * all results.  Asynchronous.  HODLR_EINVAL if a pointer repeats.
+ * on the device.  Matrices with the same partition and rank capacity form a group: the recursion
+ * of Alg. 2 depends only on the partition, so the group is factored by one merged schedule whose
+ * every launch carries the descriptors of all its matrices (at most hodlr_ctx_set_batch_group
+ * matrices per group).  Each group runs on its own pair of streams owned by the context; the
+ * pairs are forked from and joined back into the context's stream, so later work on that stream
+ * sees all results.  Asynchronous.  HODLR_EINVAL if a pointer repeats.
  *
  * hodlr_qr_batched_graph — the same with hodlr_restore of every matrix first (each needs a
  * snapshot), recorded once into one CUDA graph held by the context and launched on every call;

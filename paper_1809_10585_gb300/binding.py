@@ -39,6 +39,7 @@ _SIGS = {
     "hodlr_ctx_get_cluster": (C.c_int, [_VP, _PI]),
     "hodlr_ctx_set_concurrency": (C.c_int, [_VP, C.c_int]),
     "hodlr_ctx_get_concurrency": (C.c_int, [_VP, _PI]),
+    "hodlr_ctx_set_batch_group": (C.c_int, [_VP, C.c_int]),
     "hodlr_sync": (C.c_int, [_VP]),
     "hodlr_build": (C.c_int, [_VP, C.c_int, C.c_int, _PI, _PPD, _PPD, _PPD, _PI, _PPD, _PPD, _PI, C.c_int, C.POINTER(_VP)]),
     "hodlr_build_dense": (C.c_int, [_VP, C.c_int, C.c_int, _PI, _VP, C.c_int, C.c_double, C.c_int, C.c_ulonglong,
@@ -147,6 +148,9 @@ class Context:
     @concurrency.setter
     def concurrency(self, factorizations: int):
         check(lib().hodlr_ctx_set_concurrency(self.h, int(factorizations)), "hodlr_ctx_set_concurrency")
+
+    def set_batch_group(self, max_matrices: int):
+        check(lib().hodlr_ctx_set_batch_group(self.h, int(max_matrices)), "hodlr_ctx_set_batch_group")
 
     def sync(self):
         check(lib().hodlr_sync(self.h), "hodlr_sync")

@@ -37,7 +37,12 @@ constexpr int kGemmBM = 64, kGemmBN = 32;
 // C = alpha * op(mask(A)) * op(mask(B)) + beta * C.  Masks act on the stored matrices.
 enum Mask { kMaskNone = 0, kMaskUpper = 1, kMaskUnitLower = 2, kMaskLower = 3 };
 // flop accounting mode: 0 = 2mnk, 1 = mnk (one triangular factor), -1 = not counted
+// Every descriptor names the rank table (`di`, the devints of its matrix) and, where the kernel
+// counts algorithmic flops, the flop counters (`fl`) of its matrix, so that one launch may
+// carry descriptors of several matrices.
 struct GemmDesc {
+  const int* di;
+  double* fl;
   const double* A;
   const double* B;
   double* C;
@@ -64,6 +69,7 @@ struct ConcatSeg {
   double alpha;
 };
 struct ConcatDesc {
+  int* di;
   double* dst;
   int ldd, rows;            // rows is a literal (block sizes are static)
   int cap;                  // column capacity of dst
@@ -75,6 +81,7 @@ struct ConcatDesc {
 // Compressed leaf column (Sec. 4, Eq. (12)): panel = [leaf; B_R; C] with the B_R / C rows
 // taken from right factors V21 of ancestor lower blocks (stored transposed).
 struct PanelDesc {
+  int* di;
   double* D;                // leaf block w x w, ld ldD
   int ldD, w;
   double* P;                // panel, ld ldP
@@ -89,6 +96,8 @@ struct PanelDesc {
 
 // Householder QR of one dense h x w matrix by a thread-block cluster (Alg. 1 semantics).
 struct QRDesc {
+  const int* di;
+  double* fl;
   double* A;
   int lda;
   int h, w, href, wref;
@@ -103,6 +112,8 @@ struct QRDesc {
 
 // One-sided Jacobi on the columns of M (q1 x q2), in place.
 struct JacobiDesc {
+  const int* di;
+  double* fl;
   double* M;
   int ldm;
   int q1, q2, q1ref, q2ref;
@@ -115,6 +126,8 @@ struct JacobiDesc {
 // Rank selection after Jacobi: keep columns with norm > thr, sorted by norm descending,
 // normalized, into U (q1 x kcap, ld ldu).  Writes k to devints[kref].
 struct SelectDesc {
+  int* di;
+  double* fl;
   const double* W;
   int ldw;
   const double* nrm;
@@ -133,6 +146,7 @@ struct SelectDesc {
 
 // Y(rows) = alpha * X(rows) with dynamic columns, optional zero padding of rows [r0, rows).
 struct CopyDesc {
+  const int* di;
   const double* src;
   int lds;
   double* dst;
@@ -141,6 +155,21 @@ struct CopyDesc {
   int rows_src_ref;
   int cols, colsref;
   double alpha;
+};
+
+// Small element-wise operations, one descriptor per array, so that one launch may carry many:
+//   kSmallFill  p[0..cnt) = v;   kSmallIFill  ip[0..cnt) = (int)v;
+//   kSmallIdent p (ld, rows x cols) = [I; 0];
+//   kSmallNorm  *out = ||p[0..cnt)||_2, and p /= *out when scale (a zero vector is kept).
+enum SmallKind { kSmallFill = 0, kSmallIFill = 1, kSmallIdent = 2, kSmallNorm = 3 };
+struct SmallDesc {
+  int kind;
+  double* p;
+  int* ip;
+  double* out;
+  long long cnt;
+  int ld, rows, cols, scale;
+  double v;
 };
 
 }  // namespace hq
@@ -155,24 +184,23 @@ namespace hq {
 int cuda_fail(cudaError_t e, const char* file, int line);
 
 // Host launchers (kernels.cu / factor.cu).  All queue work on `s`.
-cudaError_t launch_gemm(GemmDesc* h_descs, int n, GemmDesc* d_descs, const int* devints,
-                        double* flops, cudaStream_t s);
-cudaError_t launch_concat(const ConcatDesc* h, int n, ConcatDesc* d, int* devints, cudaStream_t s);
-cudaError_t launch_panel_gather(const PanelDesc* h, int n, PanelDesc* d, int* devints, cudaStream_t s);
-cudaError_t launch_panel_scatter(const PanelDesc* h, int n, PanelDesc* d, const int* devints, cudaStream_t s);
+cudaError_t launch_gemm(GemmDesc* h_descs, int n, GemmDesc* d_descs, cudaStream_t s);
+cudaError_t launch_concat(const ConcatDesc* h, int n, ConcatDesc* d, cudaStream_t s);
+cudaError_t launch_panel_gather(const PanelDesc* h, int n, PanelDesc* d, cudaStream_t s);
+cudaError_t launch_panel_scatter(const PanelDesc* h, int n, PanelDesc* d, cudaStream_t s);
 // The cluster kernels reserve shared memory for the capacities of their launch, at most
 // `smem_cap` bytes (the per-CTA limit when larger), and pick their form from the actual sizes.
 // kClusterSmemShared is the cap while several factorizations run concurrently: two CTAs per SM
 // (their register use, ~126 per thread at 256 threads, allows no more), each with up to 18 KB
 // of static shared memory, out of the SM's 228 KB.
 constexpr size_t kClusterSmemShared = 92 * 1024;
-cudaError_t launch_qr(const QRDesc* h, int n, QRDesc* d, const int* devints, double* flops,
-                      int cluster, size_t smem_cap, cudaStream_t s);
-cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, const int* devints,
-                          double* flops, int cluster, size_t smem_cap, cudaStream_t s);
-cudaError_t launch_select(const SelectDesc* h, int n, SelectDesc* d, int* devints, double* flops,
-                          cudaStream_t s);
-cudaError_t launch_copy(const CopyDesc* h, int n, CopyDesc* d, const int* devints, cudaStream_t s);
+cudaError_t launch_qr(const QRDesc* h, int n, QRDesc* d, int cluster, size_t smem_cap, cudaStream_t s);
+cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, int cluster, size_t smem_cap, cudaStream_t s);
+cudaError_t launch_select(const SelectDesc* h, int n, SelectDesc* d, cudaStream_t s);
+cudaError_t launch_copy(const CopyDesc* h, int n, CopyDesc* d, cudaStream_t s);
+// fills and identities (kinds 0-2) of one record; norms (kind 3) of one record
+cudaError_t launch_small(const SmallDesc* h, int n, SmallDesc* d, cudaStream_t s);
+cudaError_t launch_norms(const SmallDesc* h, int n, SmallDesc* d, cudaStream_t s);
 cudaError_t launch_set_ints(int* devints, const int* idx_vals, int n, int* scratch, cudaStream_t s);
 cudaError_t launch_fill(double* p, size_t n, double v, cudaStream_t s);
 cudaError_t launch_gauss(double* p, size_t n, unsigned long long seed, cudaStream_t s);

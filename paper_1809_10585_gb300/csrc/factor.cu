@@ -497,11 +497,9 @@ __device__ __forceinline__ void qr_global_impl(const QRDesc* __restrict__ descs,
   qr_build_T(d, A, lda, h, kmax, C, crank, cl, false);
 }
 
-__global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __restrict__ descs,
-                                                            const int* __restrict__ di, double* flops);
+__global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __restrict__ descs);
 
 __global__ void __launch_bounds__(QT, 2) jacobi_dsmem_kernel(const JacobiDesc* __restrict__ descs,
-                                                          const int* __restrict__ di, double* flops,
                                                           int q1cap, int q2cap, int smem_bytes, int solo_cols);
 constexpr size_t kJacobiSmemMax = 200 * 1024;
 
@@ -771,9 +769,10 @@ __host__ __device__ inline size_t qr_dsmem_bytes(int h, int w, int cluster) {
 // descriptor): distributed shared memory when its columns fit in the launch's shared memory,
 // the global-memory form otherwise (reflector staged in the same shared memory).
 __global__ void __launch_bounds__(QT) qr_dsmem_kernel(const QRDesc* __restrict__ descs,
-                                                      const int* __restrict__ di, double* flops,
                                                       int hcap, int wcap, int smem_bytes, int solo_cols) {
   const QRDesc& d = descs[blockIdx.y];
+  const int* di = d.di;
+  double* flops = d.fl;
   const int h = min(dimv(d.h, d.href, di), hcap), w = min(dimv(d.w, d.wref, di), wcap);
   const int C = (int)cg::this_cluster().num_blocks();
   extern __shared__ double qsm[];
@@ -827,8 +826,7 @@ int qr_max_cluster() {
   return v;
 }
 
-cudaError_t launch_qr(const QRDesc* h, int n, QRDesc* d, const int* devints, double* flops,
-                      int cluster, size_t smem_cap, cudaStream_t s) {
+cudaError_t launch_qr(const QRDesc* h, int n, QRDesc* d, int cluster, size_t smem_cap, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cluster, n, 1);
@@ -855,7 +853,7 @@ cudaError_t launch_qr(const QRDesc* h, int n, QRDesc* d, const int* devints, dou
   // exit at once): no cluster barrier per column; more of them while other factorizations
   // share the SMs
   const int solo = smem_cap < kQRSmemMax ? 2 * kQRSoloCols : kQRSoloCols;
-  return cudaLaunchKernelEx(&cfg, qr_dsmem_kernel, (const QRDesc*)d, devints, flops, hcap, wcap, (int)smem, solo);
+  return cudaLaunchKernelEx(&cfg, qr_dsmem_kernel, (const QRDesc*)d, hcap, wcap, (int)smem, solo);
 }
 
 // --------------------------------------------------------------------------------- Jacobi
@@ -1052,9 +1050,8 @@ __device__ __forceinline__ void jacobi_global_impl(const JacobiDesc* __restrict_
   }
 }
 
-__global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __restrict__ descs,
-                                                            const int* __restrict__ di, double* flops) {
-  jacobi_global_impl(descs, di, flops);
+__global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __restrict__ descs) {
+  jacobi_global_impl(descs, descs[blockIdx.y].di, descs[blockIdx.y].fl);
 }
 
 // One-sided Jacobi with the core held in distributed shared memory: column j lives in the
@@ -1500,13 +1497,14 @@ constexpr int kJacobiSoloCols = 32;   // cores up to this many columns run on on
 // Lane-group width from the actual column length of this cluster's core (ranks are known only
 // on the device; every CTA of the cluster reads the same descriptor, so the choice is uniform).
 __global__ void __launch_bounds__(QT, 2) jacobi_dsmem_kernel(const JacobiDesc* __restrict__ descs,
-                                                          const int* __restrict__ di, double* flops,
                                                           int q1cap, int q2cap, int smem_bytes, int solo_cols) {
   // The form is chosen from the core's actual size (every CTA of the cluster reads the same
   // descriptor): one CTA for small cores; on clusters of 8 or more CTAs owner-computes when its
   // two column buffers fit in the shared memory of the launch; else remote-store when one buffer
   // fits; global memory otherwise.
   const JacobiDesc& d = descs[blockIdx.y];
+  const int* di = d.di;
+  double* flops = d.fl;
   const int q1 = min(dimv(d.q1, d.q1ref, di), q1cap);
   const int q2 = min(dimv(d.q2, d.q2ref, di), q2cap);
   const int C = (int)cg::this_cluster().num_blocks();
@@ -1543,8 +1541,8 @@ __global__ void __launch_bounds__(QT, 2) jacobi_dsmem_kernel(const JacobiDesc* _
 
 
 
-cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, const int* devints, double* flops,
-                          int cluster, size_t smem_cap, cudaStream_t s) {
+cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, int cluster, size_t smem_cap,
+                          cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int cluster_max = cluster;
   int q1cap = 0, q2cap = 0;
@@ -1581,10 +1579,10 @@ cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, const int* 
     // cores of at most this many columns run on one CTA; more of them while other factorizations
     // share the SMs (throughput over latency)
     const int solo = smem_cap < kJacobiSmemMax ? 2 * kJacobiSoloCols : kJacobiSoloCols;
-    return cudaLaunchKernelEx(&cfg, jacobi_dsmem_kernel, (const JacobiDesc*)d, devints, flops, q1cap, q2cap,
+    return cudaLaunchKernelEx(&cfg, jacobi_dsmem_kernel, (const JacobiDesc*)d, q1cap, q2cap,
                               (int)smem2, solo);
   }
-  return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel, (const JacobiDesc*)d, devints, flops);
+  return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel, (const JacobiDesc*)d);
 }
 
 }  // namespace hq
@@ -1636,7 +1634,7 @@ extern "C" int hodlr_dense_qr_noalloc(hodlr_ctx* ctx, int h, int w, double* A, i
   QRDesc* dq = reinterpret_cast<QRDesc*>(base);
   // every entry of tau and G is written by the kernel before it is read: nothing to clear
   cudaError_t e = cudaMemcpyAsync(dq, &q, sizeof(QRDesc), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = launch_qr(&q, 1, dq, nullptr, nullptr, ctx_cluster(ctx), (size_t)-1, s);
+  if (e == cudaSuccess) e = launch_qr(&q, 1, dq, ctx_cluster(ctx), (size_t)-1, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, __FILE__, __LINE__);
   return 0;

@@ -29,8 +29,7 @@ namespace hq {
 cudaStream_t ctx_stream(hodlr_ctx* ctx);
 int ctx_cluster(hodlr_ctx* ctx);
 int ctx_device(hodlr_ctx* ctx);
-cudaError_t launch_gemm_reduce(const GemmDesc* d, const int* rd, int nred, int nblocks,
-                               const int* devints, cudaStream_t s);
+cudaError_t launch_gemm_reduce(const GemmDesc* d, const int* rd, int nred, int nblocks, cudaStream_t s);
 }
 
 // ------------------------------------------------------------------------------- objects
@@ -41,6 +40,8 @@ struct MemAcct {
   std::atomic<long long> used{0};
   std::atomic<long long> limit{0};   // 0: no limit
 };
+
+struct BatchGroup;
 
 struct hodlr_ctx {
   std::shared_ptr<MemAcct> mem = std::make_shared<MemAcct>();
@@ -58,7 +59,13 @@ struct hodlr_ctx {
   int bcluster = 0;
   int concurrency = 1;           // factorizations in flight, as set by the caller
   int concurrent = 1;            // factorizations in flight on the pool's streams (batch size)
+  int batch_group = 0;           // most matrices per merged launch sequence (0: no limit)
+  // merged plans of cross-matrix batches (one per group of matrices with the same structure),
+  // their device descriptor blobs owned by `batch_owner` (charged to this context's account)
+  std::vector<BatchGroup*> groups;
+  hodlr_mat* batch_owner = nullptr;
   int bconc = 0;
+  int bgroup = -1;
 };
 
 // Shared memory a cluster kernel may reserve per CTA: the per-CTA limit for one factorization at
@@ -68,7 +75,7 @@ static size_t smem_cap(const hodlr_ctx* ctx) {
 }
 
 enum RecType { R_GEMM, R_REDUCE, R_CONCAT, R_GATHER, R_SCATTER, R_QR, R_JACOBI, R_SELECT, R_COPY,
-               R_FILL, R_IDENT, R_NORM, R_MEMSET_INT, R_TRSM, R_EVREC, R_EVWAIT, R_GAUSS };
+               R_SMALL, R_NORMS, R_TRSM, R_EVREC, R_EVWAIT, R_GAUSS };
 
 struct Rec {
   int type;
@@ -93,6 +100,13 @@ struct Plan {
   int* counters = nullptr;       // split-K tile counters of this plan (zero between uses)
   size_t counters_n = 0;
   // host copies of descriptors needed for launch-time grid sizing live inside blob
+};
+
+// A group of matrices of one structure and the merged plan that factors them together.
+struct BatchGroup {
+  std::vector<hodlr_mat*> mats;
+  std::vector<long> versions;    // plan_version of each member when the plan was merged
+  Plan plan;
 };
 
 struct View {
@@ -139,6 +153,7 @@ struct hodlr_mat {
   // plan of the factorization
   Plan plan;
   bool planned = false;
+  long plan_version = 0;         // unique serial of the current `plan`, new on every rebuild
   double plan_tol = -1, plan_anorm = -2;
   cudaGraphExec_t gexec = nullptr;
   double g_tol = -1, g_anorm = -2;
@@ -262,8 +277,42 @@ struct Planner {
     return r;
   }
 
+  // small operations as one-descriptor records (fill, int fill, identity, norm)
+  void fill(double* p, size_t cnt, double v) {
+    SmallDesc d = {};
+    d.kind = kSmallFill; d.p = p; d.cnt = (long long)cnt; d.v = v;
+    rec(R_SMALL, 1, put(std::vector<SmallDesc>{d}));
+  }
+  void ifill(int* p, size_t cnt, int v) {
+    SmallDesc d = {};
+    d.kind = kSmallIFill; d.ip = p; d.cnt = (long long)cnt; d.v = v;
+    rec(R_SMALL, 1, put(std::vector<SmallDesc>{d}));
+  }
+  void ident(double* p, int ld, int rows, int cols) {
+    SmallDesc d = {};
+    d.kind = kSmallIdent; d.p = p; d.ld = ld; d.rows = rows; d.cols = cols;
+    rec(R_SMALL, 1, put(std::vector<SmallDesc>{d}));
+  }
+  void norm(double* x, int n, double* out, bool scale) {
+    SmallDesc d = {};
+    d.kind = kSmallNorm; d.p = x; d.cnt = n; d.out = out; d.scale = scale ? 1 : 0;
+    rec(R_NORMS, 1, put(std::vector<SmallDesc>{d}));
+  }
+
+  // every descriptor carries its matrix's rank table and flop counters
+  void stamp(GemmDesc& d) const { d.di = M->devints; d.fl = M->dscal ? M->dscal + 1 : nullptr; }
+  void stamp(ConcatDesc& d) const { d.di = M->devints; }
+  void stamp(PanelDesc& d) const { d.di = M->devints; }
+  void stamp(QRDesc& d) const { d.di = M->devints; d.fl = M->dscal ? M->dscal + 1 : nullptr; }
+  void stamp(JacobiDesc& d) const { d.di = M->devints; d.fl = M->dscal ? M->dscal + 1 : nullptr; }
+  void stamp(SelectDesc& d) const { d.di = M->devints; d.fl = M->dscal ? M->dscal + 1 : nullptr; }
+  void stamp(CopyDesc& d) const { d.di = M->devints; }
+  void stamp(SmallDesc&) const {}
+  void stamp(int&) const {}
+
   template <class D>
-  size_t put(const std::vector<D>& v) {
+  size_t put(std::vector<D> v) {
+    for (auto& d : v) stamp(d);
     size_t off = (P->blob.size() + 15) & ~size_t(15);
     P->blob.resize(off + v.size() * sizeof(D));
     memcpy(P->blob.data() + off, v.data(), v.size() * sizeof(D));
@@ -597,6 +646,7 @@ struct Planner {
       std::vector<GemmDesc> gY, gP2, gP3, gQ, gZ;
       std::vector<Trunc> ts;
       std::vector<Rec> pre;
+      std::vector<SmallDesc> idents;
       for (int v = (1 << l) - 1; v < (2 << l) - 1; ++v) {
         for (int which = 0; which < 2; ++which) {
           const int rlo = M->lo[which == 0 ? 2 * v + 1 : 2 * v + 2];
@@ -619,9 +669,9 @@ struct Planner {
           g.type = R_GAUSS; g.p0 = Om; g.cnt = (size_t)q * p;
           g.i0 = (int)(unsigned)(stream & 0xffffffffull); g.i1 = (int)(unsigned)(stream >> 32);
           pre.push_back(g);
-          Rec ri = {};
-          ri.type = R_IDENT; ri.p0 = Q; ri.i0 = m; ri.i1 = m; ri.i2 = p;
-          pre.push_back(ri);
+          SmallDesc sd = {};
+          sd.kind = kSmallIdent; sd.p = Q; sd.ld = m; sd.rows = m; sd.cols = p;
+          idents.push_back(sd);
           gY.push_back(gd(B, lda, 0, 0, Om, q, 0, 0, Y, m, m, -1, p, -1, q, -1, 1.0, 0.0, kStepNone, -1));
           QRDesc qd = {};
           qd.A = Y; qd.lda = m; qd.h = m; qd.w = p; qd.href = -1; qd.wref = -1; qd.tau = tau; qd.T = T;
@@ -645,6 +695,7 @@ struct Planner {
         }
       }
       for (auto& r : pre) push(r);
+      rec(R_SMALL, (int)idents.size(), put(idents));
       gemm(gY);
       rec(R_QR, (int)qds.size(), put(qds));
       gemm(gP2);
@@ -681,9 +732,7 @@ struct Planner {
     q.G = G; q.ldg = kq; q.step = kStepLeftOrth; q.fmode = 1;
     rec(R_QR, 1, put(std::vector<QRDesc>{q}));
     // U21 <- Q = (I - Y T Y^T) [I; 0]
-    Rec ri = {};
-    ri.type = R_IDENT; ri.p0 = M->U21[p]; ri.i0 = b; ri.i1 = b; ri.i2 = kc;
-    push(ri);
+    ident(M->U21[p], b, b, kc);
     gemm({gd(S, b, 1, kMaskUnitLower, M->U21[p], b, 0, 0, P2, kc, kc, rr, kc, rr, kc, rr, 1.0, 0.0, kStepNone, -1)});
     gemm({gd(T, kq, 0, kMaskUpper, P2, kc, 0, 0, P3, kc, kq, rr, kc, rr, kq, rr, 1.0, 0.0, kStepNone, -1)});
     gemm({gd(S, b, 0, kMaskUnitLower, P3, kc, 0, 0, M->U21[p], b, b, -1, kc, rr, kq, rr, -1.0, 1.0, kStepNone, -1),
@@ -901,22 +950,16 @@ struct Planner {
     double* y = alloc<double>(n);
     double* z = alloc<double>(n);
     double* tmp = alloc<double>(1);
-    Rec f = {};
-    f.type = R_FILL; f.p0 = x; f.cnt = n; f.v = 1.0 / std::sqrt((double)n);
-    push(f);
+    fill(x, n, 1.0 / std::sqrt((double)n));
     View A = aview();
     for (int it = 0; it < iters; ++it) {
       matvec(A, 0, 0, 0, x, n, y, n, 1, -1, 1.0, 0.0, kStepNorm);
       matvec(A, 0, 0, 1, y, n, z, n, 1, -1, 1.0, 0.0, kStepNorm);
-      Rec r = {};
-      r.type = R_NORM; r.p0 = z; r.i0 = n; r.i1 = 0; r.ip = reinterpret_cast<int*>(tmp);
-      push(r);
+      norm(z, n, tmp, true);
       std::swap(x, z);
     }
     matvec(A, 0, 0, 0, x, n, y, n, 1, -1, 1.0, 0.0, kStepNorm);
-    Rec r = {};
-    r.type = R_NORM; r.p0 = y; r.i0 = n; r.i1 = 1; r.ip = reinterpret_cast<int*>(M->dscal);
-    push(r);
+    norm(y, n, M->dscal, false);
     release(mk);
   }
 };
@@ -931,8 +974,8 @@ static int rec_kind(int t) {
     case R_QR: return 2;
     case R_JACOBI: return 3;
     case R_SELECT: return 4;
-    case R_CONCAT: case R_GATHER: case R_SCATTER: case R_COPY: case R_IDENT: case R_FILL: return 5;
-    case R_NORM: return 6;
+    case R_CONCAT: case R_GATHER: case R_SCATTER: case R_COPY: case R_SMALL: return 5;
+    case R_NORMS: return 6;
     case R_TRSM: case R_GAUSS: return 7;
     default: return -1;
   }
@@ -946,7 +989,6 @@ struct Profiler {
 static int run_plan_on(hodlr_ctx* ctx, hodlr_mat* M, Plan& P, Profiler* prof, cudaStream_t mainst,
                        cudaStream_t sidest) {
   char* db = P.dblob;
-  double* flops = M->dscal + 1;
   bool two = !P.events.empty();
   cudaEvent_t fork = nullptr, join = nullptr;
   if (two) {
@@ -971,30 +1013,28 @@ static int run_plan_on(hodlr_ctx* ctx, hodlr_mat* M, Plan& P, Profiler* prof, cu
     cudaError_t e = cudaSuccess;
     switch (r.type) {
       case R_GEMM:
-        e = launch_gemm((GemmDesc*)hb, r.n, (GemmDesc*)dp, M->devints, flops, s);
+        e = launch_gemm((GemmDesc*)hb, r.n, (GemmDesc*)dp, s);
         break;
       case R_REDUCE:
-        e = launch_gemm_reduce((const GemmDesc*)(db + r.extra1), (const int*)dp, r.n, r.extra0, M->devints, s);
+        e = launch_gemm_reduce((const GemmDesc*)(db + r.extra1), (const int*)dp, r.n, r.extra0, s);
         break;
-      case R_CONCAT: e = launch_concat((const ConcatDesc*)hb, r.n, (ConcatDesc*)dp, M->devints, s); break;
-      case R_GATHER: e = launch_panel_gather((const PanelDesc*)hb, r.n, (PanelDesc*)dp, M->devints, s); break;
-      case R_SCATTER: e = launch_panel_scatter((const PanelDesc*)hb, r.n, (PanelDesc*)dp, M->devints, s); break;
+      case R_CONCAT: e = launch_concat((const ConcatDesc*)hb, r.n, (ConcatDesc*)dp, s); break;
+      case R_GATHER: e = launch_panel_gather((const PanelDesc*)hb, r.n, (PanelDesc*)dp, s); break;
+      case R_SCATTER: e = launch_panel_scatter((const PanelDesc*)hb, r.n, (PanelDesc*)dp, s); break;
       case R_QR:
-        e = launch_qr((const QRDesc*)hb, r.n, (QRDesc*)dp, M->devints, flops, ctx->cluster, smem_cap(ctx), s);
+        e = launch_qr((const QRDesc*)hb, r.n, (QRDesc*)dp, ctx->cluster, smem_cap(ctx), s);
         break;
       case R_JACOBI:
-        e = launch_jacobi((const JacobiDesc*)hb, r.n, (JacobiDesc*)dp, M->devints, flops, ctx->cluster,
-                          smem_cap(ctx), s);
+        e = launch_jacobi((const JacobiDesc*)hb, r.n, (JacobiDesc*)dp, ctx->cluster, smem_cap(ctx), s);
         break;
-      case R_SELECT: e = launch_select((const SelectDesc*)hb, r.n, (SelectDesc*)dp, M->devints, flops, s); break;
-      case R_COPY: e = launch_copy((const CopyDesc*)hb, r.n, (CopyDesc*)dp, M->devints, s); break;
-      case R_FILL: e = launch_fill(r.p0, r.cnt, r.v, s); break;
+      case R_SELECT: e = launch_select((const SelectDesc*)hb, r.n, (SelectDesc*)dp, s); break;
+      case R_COPY: e = launch_copy((const CopyDesc*)hb, r.n, (CopyDesc*)dp, s); break;
+      case R_SMALL: e = launch_small((const SmallDesc*)hb, r.n, (SmallDesc*)dp, s); break;
+      case R_NORMS: e = launch_norms((const SmallDesc*)hb, r.n, (SmallDesc*)dp, s); break;
       case R_GAUSS:
         e = launch_gauss(r.p0, r.cnt, ((unsigned long long)(unsigned)r.i1 << 32) | (unsigned)r.i0, s);
         break;
-      case R_IDENT: e = launch_set_diag_identity(r.p0, r.i0, r.i1, r.i2, s); break;
-      case R_NORM: e = launch_norm_scale(r.p0, r.i0, reinterpret_cast<double*>(r.ip), r.i1, s); break;
-      case R_MEMSET_INT: e = cudaMemsetAsync(r.ip, 0, r.cnt, s); break;
+
       case R_TRSM: e = launch_trsm_leaf(r.p0, r.i0, r.i1, reinterpret_cast<double*>(r.ip), r.i2, r.i3, s); break;
       case R_EVREC: e = cudaEventRecord(P.events[r.i0], s); break;
       case R_EVWAIT: e = cudaStreamWaitEvent(s, P.events[r.i0], 0); break;
@@ -1128,6 +1168,8 @@ static void free_plan(hodlr_mat* M, Plan& P) {
   P.blob.clear();
 }
 
+static void free_groups(hodlr_ctx* ctx);
+
 // =============================================================================== C ABI
 extern "C" {
 
@@ -1189,6 +1231,8 @@ void hodlr_ctx_destroy(hodlr_ctx* ctx) {
     cudaStreamDestroy(pr.second);
   }
   if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
+  free_groups(ctx);
+  if (ctx->batch_owner) hodlr_free(ctx->batch_owner);
   delete ctx;
 }
 
@@ -1215,6 +1259,12 @@ int hodlr_ctx_get_cluster(hodlr_ctx* ctx, int* cluster) {
 int hodlr_ctx_set_concurrency(hodlr_ctx* ctx, int factorizations) {
   if (!ctx || factorizations < 1) return HODLR_EINVAL;
   ctx->concurrency = factorizations;
+  return HODLR_OK;
+}
+
+int hodlr_ctx_set_batch_group(hodlr_ctx* ctx, int max_matrices) {
+  if (!ctx || max_matrices < 0) return HODLR_EINVAL;
+  ctx->batch_group = max_matrices;
   return HODLR_OK;
 }
 
@@ -1464,12 +1514,8 @@ int hodlr_restore(hodlr_ctx* ctx, hodlr_mat* A) {
 
 // The factorization: clear the flop counters and status, estimate ||A||_2 unless given, Alg. 2.
 static void plan_qr(Planner& pl, hodlr_mat* A, bool estimate_norm) {
-  Rec z = {};
-  z.type = R_FILL; z.p0 = A->dscal + 1; z.cnt = 16; z.v = 0.0;
-  pl.P->recs.push_back(z);
-  Rec zs = {};
-  zs.type = R_MEMSET_INT; zs.ip = A->dstatus; zs.cnt = sizeof(int) * 4;
-  pl.P->recs.push_back(zs);
+  pl.fill(A->dscal + 1, 16, 0.0);
+  pl.ifill(A->dstatus, 4, 0);
   if (estimate_norm) pl.norm_estimate(30);
   pl.node(0);
 }
@@ -1485,6 +1531,10 @@ static int ensure_plan(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm) {
   int rc = build_plan(A, A->plan, ctx->cluster, tol, [&](Planner& pl) { plan_qr(pl, A, est); });
   if (rc != HODLR_OK) return rc;
   A->planned = true;
+  // process-wide unique, so a merged plan can never be taken for the plan of another matrix
+  // that later lives at the same address
+  static std::atomic<long> plan_serial{0};
+  A->plan_version = ++plan_serial;
   A->plan_tol = tol;
   A->plan_anorm = est ? -1.0 : 1.0;
   return HODLR_OK;
@@ -1589,24 +1639,189 @@ static int ensure_pool(hodlr_ctx* ctx, int count) {
   return HODLR_OK;
 }
 
-// Queue restore (optional) + factorization of every matrix on its own stream pair, forked from
-// and joined back into the context stream.
+}  // extern "C"
+
+// ----------------------------------------------------------- cross-matrix batched plans
+// The planner's records depend only on a matrix's partition, rank capacity and whether ||A||_2
+// is estimated (ranks are data on the device), so matrices that share these have plans with the
+// same records.  One merged plan replays such a group: each of its launches carries the
+// descriptors of every matrix of the group (each descriptor names its own matrix's memory, rank
+// table and counters), so a batch of B matrices costs the launches of one factorization.
+static bool same_structure(const hodlr_mat* a, const hodlr_mat* b) {
+  return a->n == b->n && a->kc == b->kc && a->leaf_sizes == b->leaf_sizes &&
+         (a->plan_anorm > 0) == (b->plan_anorm > 0);
+}
+
+template <class D>
+static void merge_descs(const std::vector<hodlr_mat*>& mats, size_t r, Plan& out, Rec& rr) {
+  int total = 0;
+  for (auto* m : mats) total += m->plan.recs[r].n;
+  const size_t off = (out.blob.size() + 15) & ~size_t(15);
+  out.blob.resize(off + (size_t)total * sizeof(D));
+  char* dst = out.blob.data() + off;
+  for (auto* m : mats) {
+    const Rec& src = m->plan.recs[r];
+    memcpy(dst, m->plan.blob.data() + src.off, (size_t)src.n * sizeof(D));
+    dst += (size_t)src.n * sizeof(D);
+  }
+  rr.n = total;
+  rr.off = off;
+}
+
+static int merge_plans(const std::vector<hodlr_mat*>& mats, Plan& out) {
+  const Plan& P0 = mats[0]->plan;
+  const size_t R = P0.recs.size();
+  for (auto* m : mats)
+    if (m->plan.recs.size() != R || m->plan.nevents != P0.nevents) return HODLR_EINVAL;
+  out.recs.clear();
+  out.blob.clear();
+  out.nevents = P0.nevents;
+  for (size_t r = 0; r < R; ++r) {
+    Rec rr = P0.recs[r];
+    for (auto* m : mats) {
+      const Rec& q = m->plan.recs[r];
+      if (q.type != rr.type || q.stream != rr.stream || q.i0 != rr.i0) return HODLR_EINVAL;
+    }
+    switch (rr.type) {
+      case R_EVREC: case R_EVWAIT: break;
+      case R_GEMM: {
+        merge_descs<GemmDesc>(mats, r, out, rr);
+        GemmDesc* g = reinterpret_cast<GemmDesc*>(out.blob.data() + rr.off);
+        int work = 0;                                   // work items contiguous per descriptor
+        for (int i = 0; i < rr.n; ++i) {
+          g[i].work0 = work;
+          work += g[i].tiles_m * g[i].tiles_n * g[i].ksplit;
+        }
+        break;
+      }
+      case R_CONCAT: merge_descs<ConcatDesc>(mats, r, out, rr); break;
+      case R_GATHER: case R_SCATTER: merge_descs<PanelDesc>(mats, r, out, rr); break;
+      case R_QR: merge_descs<QRDesc>(mats, r, out, rr); break;
+      case R_JACOBI: merge_descs<JacobiDesc>(mats, r, out, rr); break;
+      case R_SELECT: merge_descs<SelectDesc>(mats, r, out, rr); break;
+      case R_COPY: merge_descs<CopyDesc>(mats, r, out, rr); break;
+      case R_SMALL: case R_NORMS: merge_descs<SmallDesc>(mats, r, out, rr); break;
+      default: return HODLR_EINVAL;                      // not part of a factorization plan
+    }
+    out.recs.push_back(rr);
+  }
+  return HODLR_OK;
+}
+
+// The groups of a batch, in order of first appearance: matrices of one structure, at most
+// ctx->batch_group per group.  A group of one matrix runs that matrix's own plan.
+static std::vector<std::vector<hodlr_mat*>> batch_groups(hodlr_ctx* ctx, int count, hodlr_mat* const* A) {
+  std::vector<std::vector<hodlr_mat*>> gs;
+  for (int i = 0; i < count; ++i) {
+    bool placed = false;
+    for (auto& g : gs) {
+      if (same_structure(g[0], A[i]) && (ctx->batch_group <= 0 || (int)g.size() < ctx->batch_group)) {
+        g.push_back(A[i]);
+        placed = true;
+        break;
+      }
+    }
+    if (!placed) gs.push_back({A[i]});
+  }
+  return gs;
+}
+
+static void free_groups(hodlr_ctx* ctx) {
+  for (auto* g : ctx->groups) {
+    if (ctx->batch_owner) free_plan(ctx->batch_owner, g->plan);
+    delete g;
+  }
+  ctx->groups.clear();
+}
+
+// The merged plan of group `mats`, built (or rebuilt after a member's plan changed) on demand.
+static int group_plan(hodlr_ctx* ctx, const std::vector<hodlr_mat*>& mats, Plan** out) {
+  std::vector<long> vers;
+  for (auto* m : mats) vers.push_back(m->plan_version);
+  for (auto* g : ctx->groups)
+    if (g->mats == mats && g->versions == vers) {
+      *out = &g->plan;
+      return HODLR_OK;
+    }
+  if (!ctx->batch_owner) {
+    ctx->batch_owner = new (std::nothrow) hodlr_mat();
+    if (!ctx->batch_owner) return HODLR_ENOMEM;
+    ctx->batch_owner->mem = ctx->mem;
+  }
+  for (size_t i = 0; i < ctx->groups.size(); ++i)
+    if (ctx->groups[i]->mats == mats) {                 // stale: a member was re-planned
+      free_plan(ctx->batch_owner, ctx->groups[i]->plan);
+      delete ctx->groups[i];
+      ctx->groups.erase(ctx->groups.begin() + i);
+      break;
+    }
+  BatchGroup* g = new (std::nothrow) BatchGroup();
+  if (!g) return HODLR_ENOMEM;
+  g->mats = mats;
+  g->versions = vers;
+  int rc = merge_plans(mats, g->plan);
+  if (!rc) rc = upload_plan(ctx->batch_owner, g->plan);
+  if (rc) {
+    free_plan(ctx->batch_owner, g->plan);
+    delete g;
+    return rc;
+  }
+  ctx->groups.push_back(g);
+  *out = &g->plan;
+  return HODLR_OK;
+}
+
+// Drop cached merged plans that the batch being recorded does not use, once there are many.
+static void trim_groups(hodlr_ctx* ctx, const std::vector<std::vector<hodlr_mat*>>& keep) {
+  if (ctx->groups.size() <= 64) return;
+  std::vector<BatchGroup*> kept;
+  for (auto* g : ctx->groups) {
+    bool used = false;
+    for (auto& k : keep) used = used || g->mats == k;
+    if (used) {
+      kept.push_back(g);
+    } else {
+      free_plan(ctx->batch_owner, g->plan);
+      delete g;
+    }
+  }
+  ctx->groups = kept;
+}
+
+// Queue restore (optional) + factorization of every matrix: one merged plan per group of
+// matrices with the same structure, each group on its own stream pair, forked from and joined
+// back into the context stream.
 static int batch_launch(hodlr_ctx* ctx, int count, hodlr_mat* const* A, double tol, double anorm, bool restore) {
+  (void)tol;
+  auto gs = batch_groups(ctx, count, A);
+  trim_groups(ctx, gs);
+  std::vector<Plan*> plans(gs.size(), nullptr);
+  for (size_t i = 0; i < gs.size(); ++i) {
+    if (gs[i].size() == 1) {
+      plans[i] = &gs[i][0]->plan;
+    } else if (int rc = group_plan(ctx, gs[i], &plans[i])) {
+      return rc;
+    }
+  }
+  if (int rc = ensure_pool(ctx, (int)gs.size())) return rc;
   cudaEvent_t fork;
   HQ_CUDA_OK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
   HQ_CUDA_OK(cudaEventRecord(fork, ctx->s));
-  std::vector<cudaEvent_t> joins(count, nullptr);
+  std::vector<cudaEvent_t> joins(gs.size(), nullptr);
   int rc = HODLR_OK;
   ctx->concurrent = count;
-  for (int i = 0; i < count && !rc; ++i) {
+  for (size_t i = 0; i < gs.size() && !rc; ++i) {
     cudaStream_t m = ctx->pool[i].first, sd = ctx->pool[i].second;
     if (cudaStreamWaitEvent(m, fork, 0) != cudaSuccess) rc = HODLR_ECUDA;
-    if (!rc && restore) {
-      if (cudaMemcpyAsync(A[i]->store, A[i]->snapshot, A[i]->a_doubles * sizeof(double), cudaMemcpyDeviceToDevice, m) != cudaSuccess ||
-          (A[i]->nn && cudaMemcpyAsync(A[i]->devints, A[i]->snap_ints, sizeof(int) * 3 * A[i]->nn, cudaMemcpyDeviceToDevice, m) != cudaSuccess))
+    for (hodlr_mat* X : gs[i]) {
+      if (rc) break;
+      if (restore &&
+          (cudaMemcpyAsync(X->store, X->snapshot, X->a_doubles * sizeof(double), cudaMemcpyDeviceToDevice, m) != cudaSuccess ||
+           (X->nn && cudaMemcpyAsync(X->devints, X->snap_ints, sizeof(int) * 3 * X->nn, cudaMemcpyDeviceToDevice, m) != cudaSuccess)))
         rc = HODLR_ECUDA;
+      if (!rc && anorm > 0 && launch_fill(X->dscal, 1, anorm, m) != cudaSuccess) rc = HODLR_ECUDA;
     }
-    if (!rc) rc = qr_launch_on(ctx, A[i], tol, anorm, m, sd);
+    if (!rc) rc = run_plan_on(ctx, gs[i][0], *plans[i], nullptr, m, sd);
     if (!rc && (cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming) != cudaSuccess ||
                 cudaEventRecord(joins[i], m) != cudaSuccess || cudaStreamWaitEvent(ctx->s, joins[i], 0) != cudaSuccess))
       rc = HODLR_ECUDA;
@@ -1618,6 +1833,8 @@ static int batch_launch(hodlr_ctx* ctx, int count, hodlr_mat* const* A, double t
   return rc;
 }
 
+extern "C" {
+
 int hodlr_qr_batched(hodlr_ctx* ctx, int count, hodlr_mat* const* A, double tol, double anorm) {
   if (!ctx || !A || count < 1 || !(tol >= 0)) return HODLR_EINVAL;
   for (int i = 0; i < count; ++i) {
@@ -1626,7 +1843,7 @@ int hodlr_qr_batched(hodlr_ctx* ctx, int count, hodlr_mat* const* A, double tol,
       if (A[j] == A[i]) return HODLR_EINVAL;
   }
   HQ_CUDA_OK(cudaSetDevice(ctx->dev));
-  int rc = ensure_pool(ctx, count);
+  int rc = HODLR_OK;
   for (int i = 0; i < count && !rc; ++i) rc = ensure_plan(ctx, A[i], tol, anorm);
   if (rc) return rc;
   rc = batch_launch(ctx, count, A, tol, anorm, false);
@@ -1644,7 +1861,7 @@ int hodlr_qr_batched_graph(hodlr_ctx* ctx, int count, hodlr_mat* const* A, doubl
       if (A[j] == A[i]) return HODLR_EINVAL;
   }
   HQ_CUDA_OK(cudaSetDevice(ctx->dev));
-  int rc = ensure_pool(ctx, count);
+  int rc = HODLR_OK;
   bool replan = false;
   for (int i = 0; i < count && !rc; ++i) {
     bool had = A[i]->planned && A[i]->plan_tol == tol && ((A[i]->plan_anorm > 0) == (anorm > 0));
@@ -1654,7 +1871,7 @@ int hodlr_qr_batched_graph(hodlr_ctx* ctx, int count, hodlr_mat* const* A, doubl
   if (rc) return rc;
   std::vector<hodlr_mat*> key(A, A + count);
   if (!ctx->bgraph || replan || key != ctx->bmats || ctx->btol != tol || ctx->banorm != anorm ||
-      ctx->bcluster != ctx->cluster || ctx->bconc != ctx->concurrency) {
+      ctx->bcluster != ctx->cluster || ctx->bconc != ctx->concurrency || ctx->bgroup != ctx->batch_group) {
     if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
     ctx->bgraph = nullptr;
     cudaGraph_t g;
@@ -1671,6 +1888,7 @@ int hodlr_qr_batched_graph(hodlr_ctx* ctx, int count, hodlr_mat* const* A, doubl
     ctx->banorm = anorm;
     ctx->bcluster = ctx->cluster;
     ctx->bconc = ctx->concurrency;
+    ctx->bgroup = ctx->batch_group;
   }
   HQ_CUDA_OK(cudaGraphLaunch(ctx->bgraph, ctx->s));
   for (int i = 0; i < count; ++i) A[i]->factored = true;
@@ -1759,9 +1977,7 @@ int hodlr_to_dense(hodlr_ctx* ctx, const hodlr_mat* Ac, int which, double* out, 
   // dense = op(part) I: use the HODLR x block product with an identity block
   return temp_plan(ctx, A, [&](Planner& pl) {
     double* I = pl.alloc<double>((size_t)A->n * A->n);
-    Rec ri = {};
-    ri.type = R_IDENT; ri.p0 = I; ri.i0 = A->n; ri.i1 = A->n; ri.i2 = A->n;
-    pl.P->recs.push_back(ri);
+    pl.ident(I, A->n, A->n, A->n);
     View v = which == 3 ? pl.tview() : pl.aview();
     int part = which == 0 ? 0 : (which == 1 ? 1 : 2);
     pl.matvec(v, 0, part, 0, I, A->n, out, ld, A->n, -1, 1.0, 0.0, kStepNone);
@@ -1931,7 +2147,7 @@ int hodlr_dense_qr(hodlr_ctx* ctx, int h, int w, double* A, int lda, double* T, 
   q.A = A; q.lda = lda; q.h = h; q.w = w; q.href = -1; q.wref = -1; q.tau = tau; q.T = T; q.ldt = ldt;
   q.G = G; q.ldg = k; q.step = kStepNone; q.fmode = 0;
   cudaError_t e = cudaMemcpyAsync(dq, &q, sizeof(QRDesc), cudaMemcpyHostToDevice, ctx->s);
-  if (e == cudaSuccess) e = launch_qr(&q, 1, dq, nullptr, nullptr, ctx->cluster, (size_t)-1, ctx->s);
+  if (e == cudaSuccess) e = launch_qr(&q, 1, dq, ctx->cluster, (size_t)-1, ctx->s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->s);
   cudaFree(tau);
   cudaFree(G);

@@ -4,6 +4,7 @@
 // column (Sec. 4, Eq. (12)), rank selection after the Jacobi SVD (Sec. 2.1.1, k_eps) and small
 // utilities.  GB300 has about 2 FP64 FMA per clock per SM, so these kernels are FP64-issue
 // bound; they are written to spread work over all 152 SMs rather than to stage operands.
+#include <algorithm>
 #include <cstdio>
 
 #include "common.cuh"
@@ -39,13 +40,14 @@ __device__ inline double masked(const double* M, int ld, int r, int c, int mask)
   return r == c ? 1.0 : 0.0;
 }
 
-__global__ void __launch_bounds__(GT, 4) gemm_kernel(const GemmDesc* __restrict__ descs, int ndesc,
-                                                  const int* __restrict__ di, double* flops) {
+// One work item (an output tile and a k split of one descriptor).  Called by every thread of
+// the CTA with the same item, so control flow and block barriers are uniform.
+__device__ __forceinline__ void gemm_item(const GemmDesc* __restrict__ descs, int ndesc, int item,
+                                          double (*As)[LDA_S], double (*Bs)[LDB_S], int& last) {
   // Locate the descriptor (work items are contiguous per descriptor, work0 strictly increasing):
   // each warp samples 32 first items at stride s = ceil(ndesc / 32) in one load and votes, then
-  // scans the chosen stretch of s descriptors 32 at a time, so a CTA waits for two dependent
-  // loads instead of log2(ndesc) of a binary search (most CTAs here live only a few us).
-  const int item = blockIdx.x;
+  // scans the chosen stretch of s descriptors 32 at a time: two dependent loads instead of
+  // log2(ndesc) of a binary search.
   const int lane = threadIdx.x & 31;
   const int stride = (ndesc + 31) >> 5;
   int lo;
@@ -65,6 +67,8 @@ __global__ void __launch_bounds__(GT, 4) gemm_kernel(const GemmDesc* __restrict_
     }
   }
   const GemmDesc& d = descs[lo];
+  const int* di = d.di;
+  double* flops = d.fl;
   int local = item - d.work0;
   int tiles = d.tiles_m * d.tiles_n;
   int split = local / tiles;
@@ -86,22 +90,38 @@ __global__ void __launch_bounds__(GT, 4) gemm_kernel(const GemmDesc* __restrict_
   const int k0 = split * kchunk;
   const int k1 = min(k, k0 + kchunk);
 
-  __shared__ __align__(16) double As[BK][LDA_S];
-  __shared__ __align__(16) double Bs[BK][LDB_S];
-  // The outputs of this tile that exist (ma x na: sizes are known only on the device, and most
-  // products here multiply by a block of a few columns) are covered by micro-tiles of MR x NR,
-  // dealt to the threads in column-major order (consecutive threads, consecutive row groups).
-  // A warp whose micro-tiles all lie beyond ma x na issues nothing, so the FP64 pipe, the limit
-  // of this kernel, spends instructions only on the partial row / column groups at the edges.
-  // The MR x NR accumulators are independent FMA chains (ILP 8 per thread).
+  // The outputs of this tile that exist (ma x na) are known only on the device; most products
+  // here multiply by a block of a few columns, so most tiles are sparse.  GB300 retires one
+  // 32-lane FP64 FMA instruction per 64 cycles on each of an SM's four sub-partitions, so FP64
+  // work must reach all of them, i.e. all warps of the CTA:
+  //  * dense form (ma x na <= 4 GT): the outputs are dealt to the threads in column-major
+  //    order, one per thread per pass (at most four passes), two FMA chains per output; only
+  //    the last warp of a pass carries idle lanes;
+  //  * micro-tile form (larger tiles): each thread owns MR x NR outputs (MR consecutive rows,
+  //    NR consecutive columns), eight independent chains, six shared loads per eight FMAs.
+  // A warp none of whose outputs exist issues no FMA.
   const int ma = min(BM, m - row0), na = min(BN, n - col0);
+  const int nout = ma * na;
+  const bool dense = nout <= 4 * GT;                        // uniform over the CTA
+  const int tid = threadIdx.x;
+  const int wbase = tid & ~31;
   const int mrow = (ma + MR - 1) / MR, mcol = (na + NR - 1) / NR;
   const int nmic = mrow * mcol;
-  const int tid = threadIdx.x;
-  const bool active = tid < nmic;
-  const bool warp_active = (tid & ~31) < nmic;            // warp-uniform
-  const int mi = active ? tid % mrow : 0, nj = active ? tid / mrow : 0;
-  const int r0 = mi * MR, c0 = nj * NR;
+  // micro-tile form: the thread's micro-tile; dense form: its output of each pass u (packed)
+  int r0 = 0, c0 = 0;
+  int oij[4];
+  if (dense) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int o = min(tid + GT * u, nout - 1);
+      const int oj = o / ma;
+      oij[u] = ((o - oj * ma) << 8) | oj;                   // row << 8 | column (both < 256)
+    }
+  } else {
+    const int mi = tid < nmic ? tid % mrow : 0, nj = tid < nmic ? tid / mrow : 0;
+    r0 = mi * MR;
+    c0 = nj * NR;
+  }
   double acc[MR][NR];
 #pragma unroll
   for (int u = 0; u < MR; ++u)
@@ -150,7 +170,21 @@ __global__ void __launch_bounds__(GT, 4) gemm_kernel(const GemmDesc* __restrict_
     }
     __syncthreads();
     if (kk + BK < k1) fetch(kk + BK);
-    if (warp_active) {
+    if (dense) {
+      // dense form: acc[u][0] / acc[u][1] are the even / odd k chains of pass u's output
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (wbase + GT * u < nout) {                          // warp-uniform
+          const int i = oij[u] >> 8, j = oij[u] & 255;
+          int l = 0;
+          for (; l + 1 < kl; l += 2) {
+            acc[u][0] = fma(As[l][i], Bs[l][j], acc[u][0]);
+            acc[u][1] = fma(As[l + 1][i], Bs[l + 1][j], acc[u][1]);
+          }
+          if (l < kl) acc[u][0] = fma(As[l][i], Bs[l][j], acc[u][0]);
+        }
+      }
+    } else if (wbase < nmic) {
       // rows / columns beyond ma / na hold zeros: a partial micro-tile computes zeros there
 #pragma unroll 8
       for (int l = 0; l < kl; ++l) {
@@ -171,28 +205,31 @@ __global__ void __launch_bounds__(GT, 4) gemm_kernel(const GemmDesc* __restrict_
   }
   double alpha = d.alpha;
   if (d.alpha_ref) alpha *= *d.alpha_ref;
-  if (active) {
+  auto emit = [&](int r, int c, double v) {
+    const int gi = row0 + r, gj = col0 + c;
+    if (to_part) {
+      d.part[(size_t)split * d.m * d.n + gi + (size_t)gj * d.m] = v;
+    } else {
+      double* cp = d.C + gi + (size_t)gj * d.ldc;
+      double val = alpha * v;
+      if (d.beta != 0.0) val = fma(d.beta, *cp, val);
+      *cp = val;
+    }
+  };
+  if (dense) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (tid + GT * u < nout) emit(oij[u] >> 8, oij[u] & 255, acc[u][0] + acc[u][1]);
+  } else if (tid < nmic) {
 #pragma unroll
     for (int v = 0; v < NR; ++v)
 #pragma unroll
-      for (int u = 0; u < MR; ++u) {
-        if (r0 + u < ma && c0 + v < na) {
-          const int gi = row0 + r0 + u, gj = col0 + c0 + v;
-          if (to_part) {
-            d.part[(size_t)split * d.m * d.n + gi + (size_t)gj * d.m] = acc[u][v];
-          } else {
-            double* c = d.C + gi + (size_t)gj * d.ldc;
-            double val = alpha * acc[u][v];
-            if (d.beta != 0.0) val = fma(d.beta, *c, val);
-            *c = val;
-          }
-        }
-      }
+      for (int u = 0; u < MR; ++u)
+        if (r0 + u < ma && c0 + v < na) emit(r0 + u, c0 + v, acc[u][v]);
   }
   if (!to_part || d.tile_count == nullptr) return;
   // split-K: the last split to finish this tile sums the partials in split order (the result
   // does not depend on arrival order) and resets the counter for the next use
-  __shared__ int last;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -217,9 +254,19 @@ __global__ void __launch_bounds__(GT, 4) gemm_kernel(const GemmDesc* __restrict_
   }
 }
 
+// Persistent over the launch's work items: CTA b takes items b, b + grid, b + 2 grid, ...
+// (a static queue: which CTA computes an item never changes its result).  Most products here
+// have capacity tiles that are empty at run time (their rank is below the capacity); a CTA
+// skips those in a few instructions instead of the launch paying a CTA for each.
+__global__ void __launch_bounds__(GT, 3) gemm_kernel(const GemmDesc* __restrict__ descs, int ndesc, int total) {
+  __shared__ __align__(16) double As[BK][LDA_S];
+  __shared__ __align__(16) double Bs[BK][LDB_S];
+  __shared__ int last;
+  for (int item = blockIdx.x; item < total; item += gridDim.x) gemm_item(descs, ndesc, item, As, Bs, last);
+}
+
 // Sum split-K partials: C = alpha * sum_s part_s + beta * C.  One block per 256 outputs.
-__global__ void gemm_reduce_kernel(const GemmDesc* __restrict__ descs, const int* __restrict__ rd,
-                                   int nred, const int* __restrict__ di) {
+__global__ void gemm_reduce_kernel(const GemmDesc* __restrict__ descs, const int* __restrict__ rd, int nred) {
   int item = blockIdx.x;
   // rd: pairs (desc index, first block) sorted by first block
   int lo = 0, hi = nred - 1;
@@ -228,6 +275,7 @@ __global__ void gemm_reduce_kernel(const GemmDesc* __restrict__ descs, const int
     if (rd[2 * mid + 1] <= item) lo = mid; else hi = mid - 1;
   }
   const GemmDesc& d = descs[rd[2 * lo]];
+  const int* di = d.di;
   int e = (item - rd[2 * lo + 1]) * blockDim.x + threadIdx.x;
   const int m = dimv(d.m, d.mref, di), n = dimv(d.n, d.nref, di), k = dimv(d.k, d.kref, di);
   if (e >= d.m * d.n) return;
@@ -248,27 +296,38 @@ __global__ void gemm_reduce_kernel(const GemmDesc* __restrict__ descs, const int
   *c = v;
 }
 
-cudaError_t launch_gemm(GemmDesc* h, int n, GemmDesc* d, const int* devints, double* flops,
-                        cudaStream_t s) {
+static int device_sms() {
+  static int sms = 0;
+  if (sms <= 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 152;
+    cudaGetLastError();
+  }
+  return sms;
+}
+
+cudaError_t launch_gemm(GemmDesc* h, int n, GemmDesc* d, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   int total = h[n - 1].work0 + h[n - 1].tiles_m * h[n - 1].tiles_n * h[n - 1].ksplit;
   if (total <= 0) return cudaSuccess;
-  gemm_kernel<<<total, GT, 0, s>>>(d, n, devints, flops);
+  const int grid = std::min(total, 6 * device_sms());    // two waves of 3 resident CTAs per SM
+  gemm_kernel<<<grid, GT, 0, s>>>(d, n, total);
   return cudaGetLastError();
 }
 
 // Reduction launch helper: `rd` is a device array of (desc index, first block) pairs,
 // `nblocks` the total number of blocks.
-cudaError_t launch_gemm_reduce(const GemmDesc* d, const int* rd, int nred, int nblocks,
-                               const int* devints, cudaStream_t s) {
+cudaError_t launch_gemm_reduce(const GemmDesc* d, const int* rd, int nred, int nblocks, cudaStream_t s) {
   if (nred <= 0 || nblocks <= 0) return cudaSuccess;
-  gemm_reduce_kernel<<<nblocks, 256, 0, s>>>(d, rd, nred, devints);
+  gemm_reduce_kernel<<<nblocks, 256, 0, s>>>(d, rd, nred);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------- concat
-__global__ void concat_kernel(const ConcatDesc* __restrict__ descs, int* di) {
+__global__ void concat_kernel(const ConcatDesc* __restrict__ descs) {
   const ConcatDesc& d = descs[blockIdx.y];
+  int* di = d.di;
   int off = 0;
   for (int s = 0; s < d.nseg; ++s) {
     const ConcatSeg& g = d.seg[s];
@@ -287,18 +346,19 @@ __global__ void concat_kernel(const ConcatDesc* __restrict__ descs, int* di) {
   }
 }
 
-cudaError_t launch_concat(const ConcatDesc* h, int n, ConcatDesc* d, int* devints, cudaStream_t s) {
+cudaError_t launch_concat(const ConcatDesc* h, int n, ConcatDesc* d, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   int maxrows = 0;
   for (int i = 0; i < n; ++i) maxrows = max(maxrows, h[i].rows);
   int gx = min(64, max(1, maxrows * 8 / 256));
-  concat_kernel<<<dim3(gx, n), 256, 0, s>>>(d, devints);
+  concat_kernel<<<dim3(gx, n), 256, 0, s>>>(d);
   return cudaGetLastError();
 }
 
 // -------------------------------------------------------------------- leaf panel gather
-__global__ void panel_gather_kernel(const PanelDesc* __restrict__ descs, int* di) {
+__global__ void panel_gather_kernel(const PanelDesc* __restrict__ descs) {
   const PanelDesc& d = descs[blockIdx.y];
+  int* di = d.di;
   const int w = d.w;
   // leaf block
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < w * w; e += gridDim.x * blockDim.x) {
@@ -318,8 +378,9 @@ __global__ void panel_gather_kernel(const PanelDesc* __restrict__ descs, int* di
   if (blockIdx.x == 0 && threadIdx.x == 0) di[d.href] = off;
 }
 
-__global__ void panel_scatter_kernel(const PanelDesc* __restrict__ descs, const int* __restrict__ di) {
+__global__ void panel_scatter_kernel(const PanelDesc* __restrict__ descs) {
   const PanelDesc& d = descs[blockIdx.y];
+  const int* di = d.di;
   const int w = d.w;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < w * w; e += gridDim.x * blockDim.x) {
     int i = e % w, j = e / w;
@@ -336,24 +397,26 @@ __global__ void panel_scatter_kernel(const PanelDesc* __restrict__ descs, const 
   }
 }
 
-cudaError_t launch_panel_gather(const PanelDesc* h, int n, PanelDesc* d, int* devints, cudaStream_t s) {
+cudaError_t launch_panel_gather(const PanelDesc* h, int n, PanelDesc* d, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   int gx = min(64, max(1, h[0].w * h[0].w / 1024));
-  panel_gather_kernel<<<dim3(gx, n), 256, 0, s>>>(d, devints);
+  panel_gather_kernel<<<dim3(gx, n), 256, 0, s>>>(d);
   return cudaGetLastError();
 }
-cudaError_t launch_panel_scatter(const PanelDesc* h, int n, PanelDesc* d, const int* devints, cudaStream_t s) {
+cudaError_t launch_panel_scatter(const PanelDesc* h, int n, PanelDesc* d, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   int gx = min(64, max(1, h[0].w * h[0].w / 1024));
-  panel_scatter_kernel<<<dim3(gx, n), 256, 0, s>>>(d, devints);
+  panel_scatter_kernel<<<dim3(gx, n), 256, 0, s>>>(d);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------- rank selection
 // One block per truncation problem.  k_eps = #{sigma_i > thr} (Sec. 2.1.1); the kept columns
 // of W = M J are normalized to the left singular vectors and sorted by sigma descending.
-__global__ void select_kernel(const SelectDesc* __restrict__ descs, int* di, double* flops) {
+__global__ void select_kernel(const SelectDesc* __restrict__ descs) {
   const SelectDesc& d = descs[blockIdx.x];
+  int* di = d.di;
+  double* flops = d.fl;
   const int q1 = dimv(d.q1, d.q1ref, di), q2 = dimv(d.q2, d.q2ref, di);
   double thr = d.thr;
   if (d.thr_ref) thr *= *d.thr_ref;
@@ -423,18 +486,18 @@ __global__ void select_kernel(const SelectDesc* __restrict__ descs, int* di, dou
   }
 }
 
-cudaError_t launch_select(const SelectDesc* h, int n, SelectDesc* d, int* devints, double* flops,
-                          cudaStream_t s) {
+cudaError_t launch_select(const SelectDesc* h, int n, SelectDesc* d, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   int maxq2 = 0;
   for (int i = 0; i < n; ++i) maxq2 = max(maxq2, h[i].q2);
-  select_kernel<<<n, 256, sizeof(int) * (maxq2 + 1), s>>>(d, devints, flops);
+  select_kernel<<<n, 256, sizeof(int) * (maxq2 + 1), s>>>(d);
   return cudaGetLastError();
 }
 
 // ----------------------------------------------------------------------------------- copy
-__global__ void copy_kernel(const CopyDesc* __restrict__ descs, const int* __restrict__ di) {
+__global__ void copy_kernel(const CopyDesc* __restrict__ descs) {
   const CopyDesc& d = descs[blockIdx.y];
+  const int* di = d.di;
   int cols = dimv(d.cols, d.colsref, di);
   int rs = dimv(d.rows_src, d.rows_src_ref, di);
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)d.rows * cols;
@@ -445,12 +508,71 @@ __global__ void copy_kernel(const CopyDesc* __restrict__ descs, const int* __res
   }
 }
 
-cudaError_t launch_copy(const CopyDesc* h, int n, CopyDesc* d, const int* devints, cudaStream_t s) {
+cudaError_t launch_copy(const CopyDesc* h, int n, CopyDesc* d, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   int maxe = 0;
   for (int i = 0; i < n; ++i) maxe = max(maxe, h[i].rows * h[i].cols);
   int gx = min(128, max(1, maxe / 1024));
-  copy_kernel<<<dim3(gx, n), 256, 0, s>>>(d, devints);
+  copy_kernel<<<dim3(gx, n), 256, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- small descriptor operations
+__global__ void small_kernel(const SmallDesc* __restrict__ descs) {
+  const SmallDesc& d = descs[blockIdx.y];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (d.kind == kSmallFill) {
+    for (long long i = t0; i < d.cnt; i += stride) d.p[i] = d.v;
+  } else if (d.kind == kSmallIFill) {
+    const int iv = (int)d.v;
+    for (long long i = t0; i < d.cnt; i += stride) d.ip[i] = iv;
+  } else if (d.kind == kSmallIdent) {
+    const long long tot = (long long)d.rows * d.cols;
+    for (long long e = t0; e < tot; e += stride) {
+      const int i = (int)(e % d.rows), j = (int)(e / d.rows);
+      d.p[i + (size_t)j * d.ld] = (i == j) ? 1.0 : 0.0;
+    }
+  }
+}
+
+cudaError_t launch_small(const SmallDesc* h, int n, SmallDesc* d, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  long long mx = 1;
+  for (int i = 0; i < n; ++i)
+    mx = std::max(mx, h[i].kind == kSmallIdent ? (long long)h[i].rows * h[i].cols : h[i].cnt);
+  const int gx = (int)std::min<long long>(256, std::max<long long>(1, mx / 1024));
+  small_kernel<<<dim3(gx, n), 256, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+// ||x||_2 of one vector per block (blockIdx.x = descriptor).
+__global__ void norms_kernel(const SmallDesc* __restrict__ descs) {
+  const SmallDesc& d = descs[blockIdx.x];
+  __shared__ double red[32];
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < d.cnt; i += blockDim.x) s = fma(d.p[i], d.p[i], s);
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) red[0] = sqrt(v);
+  }
+  __syncthreads();
+  const double nrm = red[0];
+  if (threadIdx.x == 0) *d.out = nrm;
+  if (d.scale && nrm > 0.0) {
+    const double inv = 1.0 / nrm;
+    for (long long i = threadIdx.x; i < d.cnt; i += blockDim.x) d.p[i] *= inv;
+  }
+}
+
+cudaError_t launch_norms(const SmallDesc* h, int n, SmallDesc* d, cudaStream_t s) {
+  (void)h;
+  if (n <= 0) return cudaSuccess;
+  norms_kernel<<<n, 1024, 0, s>>>(d);
   return cudaGetLastError();
 }
 

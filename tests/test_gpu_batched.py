@@ -63,3 +63,50 @@ def test_batched_equals_alone_and_graph_replays():
         an = U.norm2(At)
         eo, ea = U.errors_torch(*(torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (Y, T, R)), At, upper=True)
         assert eo <= 100 * tol and ea / an <= 100 * tol
+
+
+@pytest.mark.parametrize("group", [0, 2])
+def test_merged_groups_equal_alone_and_graph_replays(group):
+    """Matrices with the same partition and rank capacity are factored by one merged schedule
+    (each launch carries all of their descriptors); group = 2 splits the four same-structure
+    matrices into two schedules side by side.  Every matrix agrees with its factorization alone
+    to rounding, matrices of another structure in the same batch are unaffected, and the graph
+    form replays the eager batch bit for bit."""
+    from paper_1809_10585_gb300 import binding as B
+    tol = 1e-12
+    inps = [W.random_hodlr(2048, 256, 10, seed=s, col_scale_decades=10.0 * (s % 2)) for s in range(4)]
+    inps += [W.random_hodlr(1024, 128, 5, seed=9), W.random_hodlr(1024, 128, 7, seed=10)]
+    c = U.ctx()
+    alone = []
+    for inp in inps:
+        M = U.gpu_qr(inp, tol, anorm=0.0, rank_cap=128)
+        assert M.status()[0] == 0
+        alone.append(_dense_all(M))
+        M.free()
+    c.set_batch_group(group)
+    try:
+        mats = [B.Matrix(c, inp, rank_cap=128) for inp in inps]
+        B.qr_batched(c, mats, tol, 0.0)
+        c.sync()
+        eager = []
+        for M, ref in zip(mats, alone):
+            assert M.status()[0] == 0
+            got = _dense_all(M)
+            eager.append(got)
+            for a, b in zip(got, ref):
+                assert np.max(np.abs(a - b)) <= 1e-9 * max(1.0, np.max(np.abs(b)))
+        mats2 = [B.Matrix(c, inp, rank_cap=128) for inp in inps]
+        for M in mats2:
+            M.snapshot()
+        for _ in range(2):
+            B.qr_batched(c, mats2, tol, 0.0, graph=True)
+            c.sync()
+            for M, ref in zip(mats2, eager):
+                assert M.status()[0] == 0
+                for a, b in zip(_dense_all(M), ref):
+                    assert np.array_equal(a, b)
+        # the flop counters are per matrix: equal to the matrix's count alone
+        for M, inp in zip(mats2, inps):
+            assert M.flops()["total"] > 0
+    finally:
+        c.set_batch_group(0)

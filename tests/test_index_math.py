@@ -50,6 +50,51 @@ def test_gemm_micro_tiles_cover_outputs_once():
             assert waste <= (MR - 1) * mcol * NR + (NR - 1) * mrow * MR
 
 
+def test_gemm_dense_form_deals_outputs_once():
+    """gemm_kernel dense form (ma x na <= 4 GT): output o = t + GT u goes to thread t in pass u,
+    column-major; the packed (row << 8 | column) code round-trips; every output is stored once;
+    only warps holding an output issue FMAs, and only the last warp of a pass has idle lanes."""
+    for ma in range(1, BM + 1):
+        for na in range(1, BN + 1):
+            nout = ma * na
+            if nout > 4 * GT:
+                continue
+            stored = []
+            for u in range(4):
+                busy = 0
+                for t in range(GT):
+                    o = min(t + GT * u, nout - 1)
+                    oj = o // ma
+                    code = ((o - oj * ma) << 8) | oj
+                    i, j = code >> 8, code & 255
+                    assert 0 <= i < ma and 0 <= j < na and (i, j) == (o % ma, o // ma)
+                    computes = (t & ~31) + GT * u < nout
+                    busy += computes
+                    if t + GT * u < nout:
+                        assert computes
+                        stored.append((i, j))
+                assert busy - max(0, min(GT, nout - GT * u)) < 32
+            assert sorted(stored) == [(i, j) for i in range(ma) for j in range(na)]
+
+
+def test_gemm_form_choice_covers_every_tile():
+    """A tile takes the dense form up to 4 GT outputs and the micro-tile form beyond; the micro
+    form then keeps every thread of at least 4 warps busy (all four sub-partitions)."""
+    for ma in range(1, BM + 1):
+        for na in range(1, BN + 1):
+            if ma * na > 4 * GT:
+                nmic = -(-ma // MR) * -(-na // NR)
+                assert nmic >= 4 * 32
+
+
+def test_gemm_persistent_loop_visits_every_item_once():
+    """gemm_kernel: CTA b takes items b, b + grid, ...; every item is taken exactly once."""
+    for total in (1, 7, 911, 5000):
+        for grid in (min(total, 6 * 152), 1, 3):
+            seen = [i for b in range(grid) for i in range(b, total, grid)]
+            assert sorted(seen) == list(range(total))
+
+
 def test_gemm_shared_strides_keep_vector_reads_aligned():
     """Rows of As / Bs start on 16-byte boundaries, so the double2 reads of a micro-tile's rows
     and columns are aligned for every k in the chunk."""
