@@ -11,7 +11,8 @@ Timed arms (one JSON line on rank 0):
              launch per step, CUDA events on the library's stream around each step, L2 flushed
              (256 MiB write) between steps outside the timed events.
   e2e        the same through the public C ABI with host buffers: pinned host -> device upload of
-             the matrix, factorization, and a device -> host read of the whole factorization.
+             the matrix, factorization, and a device -> host read of the whole factorization in
+             compact form (every factor at its stored rank).
   single_matrix  the plain one-matrix-at-a-time path (16-CTA clusters) on the same GPU.
   roofline   the batched step against the FP64 ALU peak: algorithmic flops of one graph launch
              (all factorizations of the step; QR, Jacobi and GEMM kernels run concurrently)
@@ -366,7 +367,8 @@ def gpu_arm(args):
     pinps = [W.HodlrInput(x.n, x.leaf_sizes, pin_list(x.leaves), pin_list(x.U12), pin_list(x.V12),
                           pin_list(x.U21), pin_list(x.V21), name=x.name) for x in inps]
     h2d = sum(a.nbytes for x in inps for lst in (x.leaves, x.U12, x.V12, x.U21, x.V21) for a in lst)
-    out_bytes = sum(m.storage_bytes() for m in mats)
+    # the factorization comes back compact: every factor at its stored rank, not the capacity
+    out_bytes = sum(m.compact_bytes() for m in mats)
     host_outs = [torch.empty(m.storage_bytes(), dtype=torch.uint8, pin_memory=True).numpy() for m in mats]
     e2e_steps = max(1, min(args.steps, 10))
 
@@ -378,7 +380,7 @@ def gpu_arm(args):
             m.snapshot()
         factor_all()
         for m, h in zip(mats, host_outs):
-            m.download(h)
+            m.download_compact(h)
     with torch.cuda.stream(stream):
         e2e_step()
     barrier()

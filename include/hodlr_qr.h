@@ -273,6 +273,23 @@ size_t hodlr_storage_bytes(const hodlr_mat* A);
 int hodlr_download(hodlr_ctx* ctx, const hodlr_mat* A, void* host, size_t bytes);
 
 /*
+ * Compact copy of a factorization (or of an unfactored matrix) into host memory, with every
+ * off-diagonal factor at its stored rank instead of the rank capacity (the O(k n log n) storage
+ * of Sec. 2.1 at the actual k).  hodlr_compact_bytes returns the size (synchronous: it reads
+ * the ranks).  Layout, all column-major with leading dimension = rows:
+ *   int header[4 + nleaf + 3 nn] = {n, nleaf, nn = nleaf - 1, 0, leaf_sizes[nleaf],
+ *                                   r12[nn], r21[nn], rT[nn]}, padded to 8 bytes;
+ *   the nleaf dense leaves of the A/Y/R storage (n_j x n_j each), then the nleaf leaves of T;
+ *   per internal node v (heap order): U12 (m1 x r12), V12 (m2 x r12), U21 (m2 x r21),
+ *   V21 (m1 x r21), TU (m1 x rT), TV (m2 x rT), where T12 = TU TV^T.
+ * The blocks are packed on the device into a staging buffer held by A (allocated on the first
+ * call, charged to the context's account) and copied back once.  HODLR_EINVAL if bytes is too
+ * small.  Synchronous.
+ */
+int hodlr_compact_bytes(hodlr_ctx* ctx, const hodlr_mat* A, size_t* bytes);
+int hodlr_download_compact(hodlr_ctx* ctx, const hodlr_mat* A, void* host, size_t bytes);
+
+/*
  * Primitives of the hot path, exposed for testing kernel by kernel.
  *
  * hodlr_dense_qr — Householder QR in compact WY form of one dense h x w device matrix

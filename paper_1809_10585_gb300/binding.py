@@ -67,6 +67,8 @@ _SIGS = {
     "hodlr_norm2_estimate": (C.c_int, [_VP, _VP, C.c_int, _PD]),
     "hodlr_storage_bytes": (C.c_size_t, [_VP]),
     "hodlr_download": (C.c_int, [_VP, _VP, _VP, C.c_size_t]),
+    "hodlr_compact_bytes": (C.c_int, [_VP, _VP, C.POINTER(C.c_size_t)]),
+    "hodlr_download_compact": (C.c_int, [_VP, _VP, _VP, C.c_size_t]),
     "hodlr_dense_qr": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.c_int, _VP, C.c_int]),
     "hodlr_truncate": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, _VP, _VP, C.c_double, C.c_int, _VP, _VP, _PI]),
     "hodlr_dense_qr_noalloc": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.c_int, _VP, C.c_int]),
@@ -307,6 +309,15 @@ class Matrix:
     def download(self, host: np.ndarray):
         check(lib().hodlr_download(self.ctx.h, self.h, _VP(host.ctypes.data), host.nbytes), "hodlr_download")
 
+    def compact_bytes(self) -> int:
+        v = C.c_size_t()
+        check(lib().hodlr_compact_bytes(self.ctx.h, self.h, C.byref(v)), "hodlr_compact_bytes")
+        return int(v.value)
+
+    def download_compact(self, host: np.ndarray):
+        check(lib().hodlr_download_compact(self.ctx.h, self.h, _VP(host.ctypes.data), host.nbytes),
+              "hodlr_download_compact")
+
     def free(self):
         if self.h:
             lib().hodlr_free(self.h)
@@ -334,6 +345,40 @@ def fp64_peak(device=0, iters=2000, reps=5):
     a, b = C.c_double(), C.c_double()
     check(lib().hodlr_fp64_peak(device, iters, reps, C.byref(a), C.byref(b)), "hodlr_fp64_peak")
     return {"dfma": a.value, "dmma": b.value}
+
+
+def unpack_compact(buf):
+    """Parse a hodlr_download_compact buffer into (leaf_sizes, ranks (r12, r21, rT), leaves A,
+    leaves T, per-node dict of factor arrays).  Marshalling only: no arithmetic."""
+    ints = np.frombuffer(buf, dtype=np.int32)
+    n, nleaf, nn = int(ints[0]), int(ints[1]), int(ints[2])
+    ls = [int(x) for x in ints[4:4 + nleaf]]
+    rk = ints[4 + nleaf:4 + nleaf + 3 * nn].reshape(3, nn) if nn else np.zeros((3, 0), dtype=np.int32)
+    off = ((4 + nleaf + 3 * nn) * 4 + 7) // 8 * 8
+    dbl = np.frombuffer(buf, dtype=np.float64, offset=off)
+    pos = 0
+
+    def take(rows, cols):
+        nonlocal pos
+        a = dbl[pos:pos + rows * cols].reshape(cols, rows).T
+        pos += rows * cols
+        return a
+    leavesA = [take(w, w) for w in ls]
+    leavesT = [take(w, w) for w in ls]
+    lo = np.concatenate([[0], np.cumsum(ls)])
+    rng = [None] * (2 * nleaf - 1)
+    for j in range(nleaf):
+        rng[nleaf - 1 + j] = (lo[j], lo[j + 1])
+    for v in range(nleaf - 2, -1, -1):
+        rng[v] = (rng[2 * v + 1][0], rng[2 * v + 2][1])
+    nodes = []
+    for v in range(nn):
+        a = rng[2 * v + 1][1] - rng[2 * v + 1][0]
+        b = rng[2 * v + 2][1] - rng[2 * v + 2][0]
+        r12, r21, rT = int(rk[0, v]), int(rk[1, v]), int(rk[2, v])
+        nodes.append({"U12": take(a, r12), "V12": take(b, r12), "U21": take(b, r21), "V21": take(a, r21),
+                      "TU": take(a, rT), "TV": take(b, rT)})
+    return ls, rk, leavesA, leavesT, nodes
 
 
 def footprint(n, leaf_sizes, rank_cap, estimate_norm=True, with_snapshot=False, nrhs=0):

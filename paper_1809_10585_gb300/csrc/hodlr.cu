@@ -146,6 +146,8 @@ struct hodlr_mat {
   Plan splan;
   int splan_nrhs = 0;
   double* sbuf = nullptr;      // n x splan_nrhs staging buffer of the right-hand sides
+  char* pack = nullptr;        // device staging of hodlr_download_compact (grown on demand)
+  size_t pack_bytes = 0;
   char* sarena = nullptr;
   size_t sarena_bytes = 0;
   char* sarena2 = nullptr;
@@ -1791,19 +1793,31 @@ static void trim_groups(hodlr_ctx* ctx, const std::vector<std::vector<hodlr_mat*
 // Queue restore (optional) + factorization of every matrix: one merged plan per group of
 // matrices with the same structure, each group on its own stream pair, forked from and joined
 // back into the context stream.
-static int batch_launch(hodlr_ctx* ctx, int count, hodlr_mat* const* A, double tol, double anorm, bool restore) {
-  (void)tol;
-  auto gs = batch_groups(ctx, count, A);
-  trim_groups(ctx, gs);
-  std::vector<Plan*> plans(gs.size(), nullptr);
-  for (size_t i = 0; i < gs.size(); ++i) {
-    if (gs[i].size() == 1) {
-      plans[i] = &gs[i][0]->plan;
-    } else if (int rc = group_plan(ctx, gs[i], &plans[i])) {
+struct BatchSetup {
+  std::vector<std::vector<hodlr_mat*>> groups;
+  std::vector<Plan*> plans;
+};
+
+// Everything that allocates (merged plans and their device blobs, streams) happens here, before
+// any stream capture begins.
+static int batch_prepare(hodlr_ctx* ctx, int count, hodlr_mat* const* A, BatchSetup* b) {
+  b->groups = batch_groups(ctx, count, A);
+  trim_groups(ctx, b->groups);
+  b->plans.assign(b->groups.size(), nullptr);
+  for (size_t i = 0; i < b->groups.size(); ++i) {
+    if (b->groups[i].size() == 1) {
+      b->plans[i] = &b->groups[i][0]->plan;
+    } else if (int rc = group_plan(ctx, b->groups[i], &b->plans[i])) {
       return rc;
     }
   }
-  if (int rc = ensure_pool(ctx, (int)gs.size())) return rc;
+  return ensure_pool(ctx, (int)b->groups.size());
+}
+
+static int batch_launch(hodlr_ctx* ctx, const BatchSetup& b, double anorm, bool restore) {
+  const auto& gs = b.groups;
+  const auto& plans = b.plans;
+  const int count = [&] { int c = 0; for (auto& g : gs) c += (int)g.size(); return c; }();
   cudaEvent_t fork;
   HQ_CUDA_OK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
   HQ_CUDA_OK(cudaEventRecord(fork, ctx->s));
@@ -1846,7 +1860,9 @@ int hodlr_qr_batched(hodlr_ctx* ctx, int count, hodlr_mat* const* A, double tol,
   int rc = HODLR_OK;
   for (int i = 0; i < count && !rc; ++i) rc = ensure_plan(ctx, A[i], tol, anorm);
   if (rc) return rc;
-  rc = batch_launch(ctx, count, A, tol, anorm, false);
+  BatchSetup b;
+  rc = batch_prepare(ctx, count, A, &b);
+  if (!rc) rc = batch_launch(ctx, b, anorm, false);
   if (rc) return rc;
   for (int i = 0; i < count; ++i) A[i]->factored = true;
   return HODLR_OK;
@@ -1874,9 +1890,11 @@ int hodlr_qr_batched_graph(hodlr_ctx* ctx, int count, hodlr_mat* const* A, doubl
       ctx->bcluster != ctx->cluster || ctx->bconc != ctx->concurrency || ctx->bgroup != ctx->batch_group) {
     if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
     ctx->bgraph = nullptr;
+    BatchSetup b;
+    if (int r1 = batch_prepare(ctx, count, A, &b)) return r1;
     cudaGraph_t g;
     HQ_CUDA_OK(cudaStreamBeginCapture(ctx->s, cudaStreamCaptureModeThreadLocal));
-    int r2 = batch_launch(ctx, count, A, tol, anorm, true);
+    int r2 = batch_launch(ctx, b, anorm, true);
     cudaError_t e = cudaStreamEndCapture(ctx->s, &g);
     if (r2) return r2;
     if (e != cudaSuccess) return cuda_fail(e, __FILE__, __LINE__);
@@ -2129,6 +2147,96 @@ int hodlr_download(hodlr_ctx* ctx, const hodlr_mat* A, void* host, size_t bytes)
   if (A->nn)
     HQ_CUDA_OK(cudaMemcpyAsync((char*)host + A->store_doubles * sizeof(double), A->devints, sizeof(int) * 3 * A->nn,
                                cudaMemcpyDeviceToHost, ctx->s));
+  HQ_CUDA_OK(cudaStreamSynchronize(ctx->s));
+  return HODLR_OK;
+}
+
+}  // extern "C"
+
+// Compact layout of a factorization (hodlr_download_compact): a header of ints, then the dense
+// leaves of A (Y and R) and of T, then per internal node the factors at their stored ranks.
+struct CompactLayout {
+  std::vector<int> ranks;                       // r12, r21, rT (3 nn)
+  size_t header = 0, total = 0;                 // bytes
+  std::vector<CopyDesc> copies;                 // device -> staging, dst as an offset in bytes
+};
+
+static int compact_layout(hodlr_ctx* ctx, const hodlr_mat* A, CompactLayout* L) {
+  L->ranks.assign(3 * A->nn, 0);
+  HQ_CUDA_OK(cudaStreamSynchronize(ctx->s));
+  if (A->nn) HQ_CUDA_OK(cudaMemcpy(L->ranks.data(), A->devints, sizeof(int) * 3 * A->nn, cudaMemcpyDeviceToHost));
+  L->header = ((4 + (size_t)A->nleaf + 3 * (size_t)A->nn) * sizeof(int) + 7) & ~size_t(7);
+  size_t off = L->header;
+  L->copies.clear();
+  auto add = [&](const double* src, int lds, int rows, int cols) {
+    if (rows <= 0 || cols <= 0) return;
+    CopyDesc c = {};
+    c.src = src; c.lds = lds; c.dst = reinterpret_cast<double*>(off); c.ldd = rows;
+    c.rows = rows; c.rows_src = rows; c.rows_src_ref = -1; c.cols = cols; c.colsref = -1; c.alpha = 1.0;
+    L->copies.push_back(c);
+    off += (size_t)rows * cols * sizeof(double);
+  };
+  for (int pass = 0; pass < 2; ++pass)                      // leaves of A (Y, R), then of T
+    for (int j = 0; j < A->nleaf; ++j) {
+      const int w = A->leaf_sizes[j];
+      add((pass ? A->TD : A->D) + (size_t)j * A->ldl * A->ldl, A->ldl, w, w);
+    }
+  for (int v = 0; v < A->nn; ++v) {
+    const int a = A->hi[2 * v + 1] - A->lo[2 * v + 1], b = A->hi[2 * v + 2] - A->lo[2 * v + 2];
+    const int r12 = L->ranks[v], r21 = L->ranks[A->nn + v], rT = L->ranks[2 * A->nn + v];
+    add(A->U12[v], a, a, r12);
+    add(A->V12[v], b, b, r12);
+    add(A->U21[v], b, b, r21);
+    add(A->V21[v], a, a, r21);
+    add(A->TU[v], a, a, rT);
+    add(A->TV[v], b, b, rT);
+  }
+  L->total = off;
+  return HODLR_OK;
+}
+
+extern "C" {
+
+int hodlr_compact_bytes(hodlr_ctx* ctx, const hodlr_mat* A, size_t* bytes) {
+  if (!ctx || !A || !bytes) return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  CompactLayout L;
+  if (int rc = compact_layout(ctx, A, &L)) return rc;
+  *bytes = L.total;
+  return HODLR_OK;
+}
+
+int hodlr_download_compact(hodlr_ctx* ctx, const hodlr_mat* Ac, void* host, size_t bytes) {
+  hodlr_mat* A = const_cast<hodlr_mat*>(Ac);
+  if (!ctx || !A || !host) return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  CompactLayout L;
+  if (int rc = compact_layout(ctx, A, &L)) return rc;
+  if (bytes < L.total) return HODLR_EINVAL;
+  // header on the host
+  int* hh = static_cast<int*>(host);
+  hh[0] = A->n; hh[1] = A->nleaf; hh[2] = A->nn; hh[3] = 0;
+  for (int j = 0; j < A->nleaf; ++j) hh[4 + j] = A->leaf_sizes[j];
+  for (int i = 0; i < 3 * A->nn; ++i) hh[4 + A->nleaf + i] = L.ranks[i];
+  // pack the blocks into a device staging buffer (descriptors after the data), one copy back
+  const size_t data = L.total - L.header;
+  const size_t dbytes = L.copies.size() * sizeof(CopyDesc);
+  const size_t need = ((data + 255) & ~size_t(255)) + dbytes + 256;
+  if (need > A->pack_bytes) {
+    mat_free(A, A->pack);
+    A->pack = nullptr;
+    A->pack_bytes = 0;
+    if (int rc = mat_alloc(A, &A->pack, need)) return rc;
+    A->pack_bytes = need;
+  }
+  char* stage = A->pack;
+  CopyDesc* dd = reinterpret_cast<CopyDesc*>(stage + ((data + 255) & ~size_t(255)));
+  for (auto& c : L.copies) c.dst = reinterpret_cast<double*>(stage + (reinterpret_cast<size_t>(c.dst) - L.header));
+  if (!L.copies.empty()) {
+    HQ_CUDA_OK(cudaMemcpyAsync(dd, L.copies.data(), dbytes, cudaMemcpyHostToDevice, ctx->s));
+    HQ_CUDA_OK(launch_copy(L.copies.data(), (int)L.copies.size(), dd, ctx->s));
+    HQ_CUDA_OK(cudaMemcpyAsync(static_cast<char*>(host) + L.header, stage, data, cudaMemcpyDeviceToHost, ctx->s));
+  }
   HQ_CUDA_OK(cudaStreamSynchronize(ctx->s));
   return HODLR_OK;
 }

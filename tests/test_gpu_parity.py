@@ -401,3 +401,38 @@ def test_truncate_is_repeatable_and_accurate(nL, nR, K):
     k, Lg, Rg = outs[0]
     M = L @ Rt.T
     assert np.linalg.norm(M - Lg @ Rg.T, 2) <= 1e-12 * 1.01 + 1e-13 * np.linalg.norm(M, 2)
+
+
+def test_compact_download_reconstructs_factors():
+    """hodlr_download_compact: the factors at their stored ranks reassemble Y, R and T exactly
+    as hodlr_to_dense gives them, and the compact size is below the capacity storage."""
+    inp = W.random_hodlr(2048, 256, 10, seed=6, col_scale_decades=10.0)
+    M = U.gpu_qr(inp, 1e-12, anorm=0.0, rank_cap=128)
+    nb = M.compact_bytes()
+    assert 0 < nb < M.storage_bytes()
+    buf = np.zeros(nb, dtype=np.uint8)
+    M.download_compact(buf)
+    ls, rk, LA, LT, nodes = B.unpack_compact(buf.tobytes())
+    assert ls == list(inp.leaf_sizes)
+    r12, r21, rT = M.ranks()
+    assert np.array_equal(rk[0], r12) and np.array_equal(rk[1], r21) and np.array_equal(rk[2], rT)
+    n = inp.n
+    YR = np.zeros((n, n))
+    T = np.zeros((n, n))
+    rng = W.node_ranges(ls)
+    nleaf = len(ls)
+    for j in range(nleaf):
+        lo, hi = rng[nleaf - 1 + j]
+        YR[lo:hi, lo:hi] = LA[j]
+        T[lo:hi, lo:hi] = np.triu(LT[j])
+    for v, f in enumerate(nodes):
+        (a0, a1), (b0, b1) = rng[2 * v + 1], rng[2 * v + 2]
+        YR[a0:a1, b0:b1] = f["U12"] @ f["V12"].T
+        YR[b0:b1, a0:a1] = f["U21"] @ f["V21"].T
+        T[a0:a1, b0:b1] = f["TU"] @ f["TV"].T
+    Y = np.tril(YR, -1) + np.eye(n)
+    R = np.triu(YR)
+    Yd, Td, Rd = (x.cpu().numpy() for x in U.factors_dense(M))
+    np.testing.assert_allclose(Y, Yd, atol=1e-13)
+    np.testing.assert_allclose(R, Rd, atol=1e-13 * np.abs(Rd).max())
+    np.testing.assert_allclose(T, Td, atol=1e-13)
