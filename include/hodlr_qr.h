@@ -295,7 +295,8 @@ int hodlr_download_compact(hodlr_ctx* ctx, const hodlr_mat* A, void* host, size_
  * hodlr_dense_qr — Householder QR in compact WY form of one dense h x w device matrix
  * (Alg. 1; h >= 1, 1 <= w <= 1024): on return A holds R in its upper triangle and the
  * Householder vectors (unit diagonal implied) below it, T_dev (w x w, leading dimension ldt)
- * the upper-triangular T with Q = I - Y T Y^T.  LAPACK dlarfg sign convention.
+ * the upper-triangular T with Q = I - Y T Y^T.  LAPACK dlarfg sign convention.  The kernel form
+ * follows the context's cluster size and concurrency setting, like the factorization's QRs.
  */
 int hodlr_dense_qr(hodlr_ctx* ctx, int h, int w, double* A_dev, int lda, double* T_dev, int ldt);
 

@@ -759,6 +759,197 @@ __device__ __forceinline__ void qr_dsmem_impl(const QRDesc* __restrict__ descs, 
   qr_build_T(d, A, lda, h, kmax, C, crank, cl, SOLO);   // starts with a barrier
 }
 
+// Blocked Householder QR (Alg. 1 with panels of QNB columns: the reflectors of a panel are
+// formed one by one, then applied together to the columns to its right) of one h x w matrix
+// held in global memory (L2-resident), for matrices whose columns do not fit in the cluster's
+// shared memory.  Column block q (columns q QNB .. q QNB + QNB - 1) belongs to CTA q % C.  For
+// panel p its owner loads the panel into shared memory, factors it there with block barriers
+// only (reflector norms by block reductions, scaled when needed), writes it back and publishes
+// it with one cluster barrier.  Every CTA then holds the panel's reflectors in shared memory
+// (unit lower trapezoidal) and applies them in order to each of its own later columns, one warp
+// per column with the column in registers: a column is read and written once per panel, and
+// the cluster waits once per panel instead of once per column.  T is built afterwards from
+// G = Y^T Y as in the other forms.
+constexpr int QNB = 16;
+
+__host__ __device__ inline size_t qr_blocked_bytes(int h) { return (size_t)h * QNB * sizeof(double) + 64; }
+
+__device__ __forceinline__ void qr_blocked_impl(const QRDesc& d, int h, int w, double* flops, double* Ys) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int crank = (int)cl.block_rank();
+  const int kmax = min(h, w);
+  double* A = d.A;
+  const size_t lda = d.lda;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __shared__ double red[QW + 1];
+  __shared__ double ptau[QNB];
+
+  if (crank == 0 && tid == 0 && flops && kmax > 0) {
+    if (d.step >= 0) {
+      double f;
+      if (d.fmode == 0) {
+        f = 2.0 * h * (double)w * w - 2.0 * (double)w * w * w / 3.0 + (double)h * w * w - (double)w * w * w / 3.0;
+      } else {
+        const double q = kmax;
+        f = 4.0 * h * (double)w * q - 4.0 * q * q * q / 3.0;
+      }
+      atomicAdd(&flops[d.step], f);
+    }
+    const double q = kmax;
+    double g = 2.0 * h * (double)w * q - q * q * (double)w - q * q * q / 3.0 + (double)w * q * q / 3.0;
+    if (g < 0) g = 0;
+    if (d.T) g += (double)h * q * q - q * q * q / 3.0;
+    atomicAdd(&flops[kKindSlot + 2], g);
+  }
+
+  const int npanel = (kmax + QNB - 1) / QNB;
+  for (int p = 0; p < npanel; ++p) {
+    const int j0 = p * QNB, nbp = min(QNB, kmax - j0), rows = h - j0;
+    const int owner = p % C;
+    if (crank == owner) {
+      __syncthreads();                                   // own columns updated by all threads
+      for (int e = tid; e < rows * nbp; e += QT) {
+        const int i = j0 + e % rows, c = e / rows;
+        Ys[i + (size_t)c * h] = __ldcg(&A[i + (size_t)(j0 + c) * lda]);
+      }
+      __syncthreads();
+      for (int jj = 0; jj < nbp; ++jj) {
+        const int j = j0 + jj;
+        double* y = Ys + (size_t)jj * h;
+        double s = 0.0;
+        for (int i = j + 1 + tid; i < h; i += QT) s = fma(y[i], y[i], s);
+        s = block_sum(s, red);
+        const double alpha = y[j];
+        double hn = 0.0;
+        if (norm_needs_scaling(s, alpha)) {              // uniform over the CTA
+          bool xz = false;
+          hn = scaled_column_norm<false>(y, j + 1, h, alpha, red, &xz);
+          s = xz ? 0.0 : 1.0;
+        } else if (tid == 0) {
+          hn = sqrt(fma(alpha, alpha, s));
+        }
+        __syncthreads();                                 // every thread has read alpha and red
+        if (tid == 0) {
+          double tau = 0.0, scal = 0.0, beta = alpha;
+          if (s > 0.0) {
+            beta = -copysign(hn, alpha);
+            tau = (beta - alpha) / beta;
+            scal = 1.0 / (alpha - beta);
+          }
+          ptau[jj] = tau;
+          red[QW] = scal;
+          d.tau[j] = tau;
+          y[j] = beta;
+        }
+        __syncthreads();
+        const double scal = red[QW], tau = ptau[jj];
+        if (scal != 0.0)
+          for (int i = j + 1 + tid; i < h; i += QT) y[i] *= scal;
+        __syncthreads();
+        if (tau != 0.0) {
+          for (int c = jj + 1 + warp; c < nbp; c += QW) {  // the rest of the panel
+            double* a = Ys + (size_t)c * h;
+            double t0 = 0.0, t1 = 0.0;
+            int i = j + 1 + lane;
+            for (; i + 32 < h; i += 64) {
+              t0 = fma(y[i], a[i], t0);
+              t1 = fma(y[i + 32], a[i + 32], t1);
+            }
+            if (i < h) t0 = fma(y[i], a[i], t0);
+            const double wv = tau * (warp_sum2(t0 + t1) + a[j]);
+            for (int r = j + 1 + lane; r < h; r += 32) a[r] = fma(-wv, y[r], a[r]);
+            __syncwarp();
+            if (lane == 0) a[j] -= wv;
+          }
+        }
+        __syncthreads();
+      }
+      // the factored panel back to global memory (R above the diagonal, reflectors below)
+      for (int e = tid; e < rows * nbp; e += QT) {
+        const int i = j0 + e % rows, c = e / rows;
+        A[i + (size_t)(j0 + c) * lda] = Ys[i + (size_t)c * h];
+      }
+      __syncthreads();
+      // unit lower trapezoidal form of the reflectors for the update of later columns
+      for (int e = tid; e < nbp * nbp; e += QT) {
+        const int r = e % nbp, c = e / nbp;
+        if (r <= c) Ys[j0 + r + (size_t)c * h] = (r == c) ? 1.0 : 0.0;
+      }
+    }
+    cl.sync();                                           // panel p and its tau published
+    if (crank != owner) {
+      for (int e = tid; e < rows * nbp; e += QT) {
+        const int i = j0 + e % rows, c = e / rows;
+        const double v = __ldcg(&A[i + (size_t)(j0 + c) * lda]);
+        Ys[i + (size_t)c * h] = i < j0 + c ? 0.0 : (i == j0 + c ? 1.0 : v);
+      }
+      if (tid < nbp) ptau[tid] = __ldcg(&d.tau[j0 + tid]);
+    }
+    __syncthreads();
+    // apply the panel's reflectors in order to this CTA's columns beyond the panel
+    const int qfirst = p + 1 + ((crank - (p + 1) % C) + C) % C;   // first own block after p
+    const int nown = [&] {
+      int c = 0;
+      for (int q = qfirst; q * QNB < w; q += C) c += min(QNB, w - q * QNB);
+      return c;
+    }();
+    const int nq = (rows + 31) >> 5;
+    for (int idx = warp; idx < nown; idx += QW) {
+      const int q = qfirst + (idx / QNB) * C;             // blocks before the last are full
+      const int c = q * QNB + idx % QNB;
+      double* a = A + (size_t)c * lda;
+      if (nq <= kQRRegs) {
+        double r[kQRRegs];
+#pragma unroll
+        for (int u = 0; u < kQRRegs; ++u) {
+          const int i = j0 + lane + 32 * u;
+          r[u] = (u < nq && i < h) ? __ldcg(&a[i]) : 0.0;
+        }
+        for (int k = 0; k < nbp; ++k) {
+          const double tk = ptau[k];
+          if (tk == 0.0) continue;
+          const double* yk = Ys + (size_t)k * h;
+          double t0 = 0.0, t1 = 0.0;
+#pragma unroll
+          for (int u = 0; u < kQRRegs; ++u) {
+            const int i = j0 + lane + 32 * u;
+            if (u < nq && i < h) {
+              if (u & 1) t1 = fma(yk[i], r[u], t1);
+              else t0 = fma(yk[i], r[u], t0);
+            }
+          }
+          const double wv = tk * warp_sum2(t0 + t1);
+#pragma unroll
+          for (int u = 0; u < kQRRegs; ++u) {
+            const int i = j0 + lane + 32 * u;
+            if (u < nq && i < h) r[u] = fma(-wv, yk[i], r[u]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kQRRegs; ++u) {
+          const int i = j0 + lane + 32 * u;
+          if (u < nq && i < h) a[i] = r[u];
+        }
+      } else {
+        // long columns: each reflector streams the column from L2
+        for (int k = 0; k < nbp; ++k) {
+          const double tk = ptau[k];
+          if (tk == 0.0) continue;
+          const double* yk = Ys + (size_t)k * h;
+          double t = 0.0;
+          for (int i = j0 + k + lane; i < h; i += 32) t = fma(yk[i], __ldcg(&a[i]), t);
+          const double wv = tk * warp_sum2(t);
+          for (int i = j0 + k + lane; i < h; i += 32) a[i] = fma(-wv, yk[i], __ldcg(&a[i]));
+          __syncwarp();
+        }
+      }
+    }
+  }
+  // T from G = Y^T Y (starts with a cluster barrier: every column final everywhere)
+  qr_build_T(d, A, lda, h, kmax, C, crank, cl, false);
+}
+
 // Bytes of shared memory of the distributed form for an h x w matrix on C CTAs.
 __host__ __device__ inline size_t qr_dsmem_bytes(int h, int w, int cluster) {
   const size_t nloc = (w + cluster - 1) / cluster;
@@ -781,6 +972,8 @@ __global__ void __launch_bounds__(QT) qr_dsmem_kernel(const QRDesc* __restrict__
     qr_dsmem_impl<true>(descs, di, flops, h, w, qsm);
   } else if (qr_dsmem_bytes(h, w, C) <= (size_t)smem_bytes) {
     qr_dsmem_impl<false>(descs, di, flops, h, w, qsm);
+  } else if (w > QNB && qr_blocked_bytes(h) <= (size_t)smem_bytes) {
+    qr_blocked_impl(d, h, w, flops, qsm);
   } else {
     qr_global_impl(descs, di, flops, qsm, smem_bytes / (int)sizeof(double));
   }

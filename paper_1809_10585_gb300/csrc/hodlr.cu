@@ -2255,7 +2255,7 @@ int hodlr_dense_qr(hodlr_ctx* ctx, int h, int w, double* A, int lda, double* T, 
   q.A = A; q.lda = lda; q.h = h; q.w = w; q.href = -1; q.wref = -1; q.tau = tau; q.T = T; q.ldt = ldt;
   q.G = G; q.ldg = k; q.step = kStepNone; q.fmode = 0;
   cudaError_t e = cudaMemcpyAsync(dq, &q, sizeof(QRDesc), cudaMemcpyHostToDevice, ctx->s);
-  if (e == cudaSuccess) e = launch_qr(&q, 1, dq, ctx->cluster, (size_t)-1, ctx->s);
+  if (e == cudaSuccess) e = launch_qr(&q, 1, dq, ctx->cluster, smem_cap(ctx), ctx->s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->s);
   cudaFree(tau);
   cudaFree(G);

@@ -52,6 +52,44 @@ def test_dense_qr_matches_oracle(h, w, seed):
     np.testing.assert_allclose(np.triu(Tg), T, atol=1e-12)
 
 
+@pytest.mark.parametrize("h,w,cluster,conc", [(300, 256, 4, 2), (400, 250, 2, 1), (700, 300, 4, 1),
+                                              (1024, 512, 16, 1), (260, 47, 1, 2), (33, 100, 2, 2)])
+def test_dense_qr_blocked_form_matches_oracle(h, w, cluster, conc):
+    """Sizes whose columns do not fit in the cluster's shared memory take the blocked form
+    (panels of 16 columns, one cluster barrier per panel): column registers (h <= 512) and the
+    streamed path for longer columns, widths that are not a multiple of the panel width, the
+    shared-memory cap of concurrent factorizations (conc = 2), and a wide matrix (h < w)."""
+    rng = np.random.default_rng(h + w)
+    A = rng.standard_normal((h, w))
+    A[:, 5] *= 1e-8
+    k = min(h, w)
+    Yo, To, Ro = O.block_qr(A[:, :k])
+    c = U.ctx()
+    cmax, c0 = c.cluster, c.concurrency
+    c.cluster = min(cluster, cmax)
+    c.concurrency = conc
+    try:
+        ta, pa, lda = U.dev(A)
+        tt, pt, ldt = U.empty(k, k)
+        B.dense_qr(c, h, w, pa, lda, pt, ldt)
+        Ag = U.host(ta, h, w)
+        Tg = U.host(tt, k, k)
+    finally:
+        c.cluster = cmax
+        c.concurrency = c0
+    Rg = np.triu(Ag[:k, :k])
+    Yg = np.tril(Ag[:, :k], -1)
+    Yg[:k, :k] += np.eye(k)
+    sc = max(1.0, np.abs(A).max())
+    np.testing.assert_allclose(Rg, Ro, atol=1e-13 * sc * np.sqrt(h))
+    np.testing.assert_allclose(Yg, Yo, atol=1e-11)
+    np.testing.assert_allclose(np.triu(Tg), To, atol=1e-12)
+    if h < w:
+        # the columns beyond the first h are Q^T A(:, h:) = R(:, h:)
+        Q = np.eye(h) - Yo @ To @ Yo.T
+        np.testing.assert_allclose(Ag[:, k:], Q.T @ A[:, k:], atol=1e-12 * sc * np.sqrt(h))
+
+
 @pytest.mark.parametrize("cluster", [0, 1])
 @pytest.mark.parametrize("h,w,seed", [(100, 20, 21), (300, 64, 22), (500, 256, 23), (1024, 512, 24)])
 def test_dense_qr_extreme_column_scales(h, w, seed, cluster):
