@@ -463,6 +463,179 @@ def gpu_arm(args):
     return 0
 
 
+def batch256_arm(args):
+    """The cross-matrix batch workload: 256 independent matrices, n log-uniform in [2048, 32768]
+    rounded to nmin 2^l, nmin in {128, 256}, off-diagonal ranks uniform in [5, 20], every second
+    matrix column-scaled to condition ~1e10, tol 1e-12; all 256 factored per step by one CUDA
+    graph (merged launch schedules per group of matrices of one structure)."""
+    import torch
+    from paper_1809_10585_gb300 import binding as B
+    from paper_1809_10585_gb300 import build as BUILD
+    import workloads as W
+    BUILD.build()
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    count = args.batch if args.batch != 64 else 256
+    t_gen = time.perf_counter()
+    inps = W.batched_family(count=count, seed0=rank * count)
+    t_gen = time.perf_counter() - t_gen
+    ctx = B.Context(local)
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream.cuda_stream)
+    ctx.cluster = min(ctx.cluster, BATCH_CLUSTER) if args.cluster <= 0 else args.cluster
+    ctx.set_batch_group(args.group)
+    mats = [B.Matrix(ctx, x, rank_cap=args.rank_cap) for x in inps]
+    for m in mats:
+        m.snapshot()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 1)):
+            B.qr_batched(ctx, mats, TOL, 0.0, graph=True)
+    ctx.sync()
+    bad = [i for i, m in enumerate(mats) if m.status()[0] != 0]
+    if bad:
+        raise RuntimeError(f"factorization status != 0 for matrices {bad[:8]}")
+    flops = sum(m.flops()["total"] for m in mats)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            B.qr_batched(ctx, mats, TOL, 0.0, graph=True)
+            evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), "cuda")
+    ms_per_step = ms / args.steps
+    value = whole_job_rate(ws, count, args.steps, ms / 1e3)
+    rec = recorded_fp64_peak()
+    peak = rec[0] if rec else B.fp64_peak(local)["dfma"]
+    achieved = flops / (ms_per_step / 1e3) / 1e12
+    mem = ctx.memory_used()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batch256_n2048-32768_nmin128-256_k5-20_half-colscaled1e-10_tol1e-12",
+                       "matrices": count, "n_min": min(x.n for x in inps), "n_max": max(x.n for x in inps),
+                       "n_total": sum(x.n for x in inps), "rank_cap": args.rank_cap, "cluster": ctx.cluster,
+                       "group": args.group, "tol": TOL, "l2": "flushed (256 MiB write) between timed steps",
+                       "device_bytes": mem, "host_generation_s": t_gen},
+            "effective_gflops": flops / (ms_per_step / 1e3) / 1e9,
+            "algorithmic_gflop_per_step": flops / 1e9, "clocks": clk,
+            "roofline": {"bound": "alu", "kernel": f"batched hQR graph ({count} factorizations per launch)",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": None, "peak_source": PEAK_RECORD if rec else "measured in this run"}}
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle.core as O
+        sample = sorted(range(count), key=lambda i: inps[i].n)[:: max(1, count // 8)][:8]
+        t = 0.0
+        f_sample = 0.0
+        for i in sample:
+            t += time_oracle(inps[i])
+            f_sample += mats[i].flops()["total"]
+        # the oracle's rate in algorithmic flops, applied to the whole batch
+        rate = (f_sample / t) / (flops / count) if t > 0 else 0.0
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                                "sample": f"{len(sample)} matrices of the batch spread over n "
+                                          f"({min(inps[i].n for i in sample)}..{max(inps[i].n for i in sample)}), "
+                                          "timed whole; rate scaled by algorithmic flops to the batch's mean"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def served_sweep_requests(rate, count, pool, seed):
+    """A Poisson stream at `rate` requests/s: factorize+solve requests on matrices drawn from the
+    pool (each request factors its matrix anew), 1-64 right-hand sides N(0,1); a third are repeat
+    solves on factors kept resident by an earlier request."""
+    import workloads as W
+    from paper_1809_10585_gb300 import server as S
+    rng = np.random.default_rng(seed)
+    reqs, kept, t = [], [], 0.0
+    for i in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        nrhs = int(rng.integers(1, 65))
+        if kept and rng.uniform() < 1.0 / 3.0:
+            key, n = kept[int(rng.integers(len(kept)))]
+            reqs.append(S.Solve(key, W.rhs(n, nrhs, seed=seed + 1000 + i), arrival=t))
+            continue
+        inp = pool[int(rng.integers(len(pool)))]
+        keep = bool(rng.uniform() < 0.5)
+        key = f"r{i}" if keep else None
+        reqs.append(S.FactorSolve(inp, W.rhs(inp.n, nrhs, seed=seed + 2000 + i), TOL, keep, key, arrival=t))
+        if keep:
+            kept.append((key, inp.n))
+    return reqs
+
+
+def served_arm(args):
+    """The served factorize+solve stream at the shape of the serving workload: Poisson arrivals
+    of requests on matrices of the random (rank 5), column-scaled (rank 10, condition ~1e10),
+    kernel 1/(x - y) and symmetric banded (b = 8) families with n log-uniform over
+    {4096, ..., 131072}; 1-64 right-hand sides; factors kept resident for repeat solves; HBM
+    admission budget 120 GB.  The arrival rate is swept up to saturation; p50/p99 latency and
+    throughput are reported per rate."""
+    import torch
+    import workloads as W
+    from paper_1809_10585_gb300 import build as BUILD
+    from paper_1809_10585_gb300 import server as S
+    BUILD.build()
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    rng = np.random.default_rng(777)
+    sizes = [4096 << i for i in range(6)]                      # 4096 ... 131072
+    pool, t_gen = [], time.perf_counter()
+    for i in range(args.served_pool):
+        n = int(sizes[int(rng.integers(len(sizes)))])
+        fam = i % 4
+        if fam == 0:
+            pool.append(W.random_hodlr(n, 256, 5, seed=i))
+        elif fam == 1:
+            pool.append(W.scaled_config1(n, 256, 10, seed=i, decades=10.0))
+        elif fam == 2:
+            pool.append(W.kernel_hodlr(n, 256, 1e-12, seed=i, device="cuda"))
+        else:
+            pool.append(W.banded_hodlr(n, 8, 256, seed=i))
+    t_gen = time.perf_counter() - t_gen
+    torch.cuda.empty_cache()
+    rates = [float(x) for x in args.served_rates.split(",")]
+    points = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    for k, rate in enumerate(rates):
+        reqs = served_sweep_requests(rate, args.served_requests, pool, seed=99 + k)
+        srv = S.Server(local, slots=8, hbm_budget=120e9, rank_cap=args.rank_cap)
+        t0 = time.perf_counter()
+        out = srv.run(reqs)
+        wall = time.perf_counter() - t0
+        lat = srv.latencies()
+        srv.close()
+        nfac = sum(1 for r in reqs if isinstance(r, S.FactorSolve))
+        points.append({"rate_per_s": rate, "requests": len(out), "factorizations": nfac,
+                       "p50_s": lat["p50_s"], "p99_s": lat["p99_s"], "wall_s": wall,
+                       "requests_per_s": len(out) / wall, "factorizations_per_s": nfac / wall,
+                       "max_running": srv.max_running})
+    clk = clocks.stop()
+    best = max(points, key=lambda p: p["requests_per_s"])
+    line = {"metric": "served factorize+solve requests/s at saturation (FP64, tol 1e-12); p50/p99 per rate",
+            "value": best["requests_per_s"], "unit": "requests/s", "n_gpus": 1, "steps": len(rates),
+            "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "served_n4096-131072_random-colscaled-kernel-banded_tol1e-12",
+                       "pool": [{"n": x.n, "family": ["random k5", "colscaled k10", "kernel", "banded b8"][i % 4]}
+                                for i, x in enumerate(pool)],
+                       "slots": 8, "hbm_budget_gb": 120, "rank_cap": args.rank_cap,
+                       "arrivals": "Poisson, rates swept", "host_generation_s": t_gen},
+            "points": points, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def peaks_arm(args):
     """FP64 DFMA and DMMA (mma.sync.m8n8k4) throughput of this GPU, with the SM clocks sampled
     while the microbenchmark runs: the record behind the roofline denominator."""
@@ -502,6 +675,12 @@ def main():
                     help="skip the served request stream (p50/p99 latency)")
     ap.add_argument("--group", type=int, default=0,
                     help="most matrices per merged launch schedule (0: all matrices of the workload in one)")
+    ap.add_argument("--served-requests", type=int, default=24, help="requests per rate of the served sweep")
+    ap.add_argument("--served-rates", default="0.5,2,8,32", help="arrival rates (requests/s) of the served sweep")
+    ap.add_argument("--served-pool", type=int, default=12, help="distinct matrices the served sweep draws from")
+    ap.add_argument("--workload", default="n8192", choices=["n8192", "batch256", "served"],
+                    help="n8192: the ill-conditioned n = 8192 workload (default); batch256: 256 matrices of "
+                         "log-uniform n in [2048, 32768]")
     ap.add_argument("--peaks", action="store_true",
                     help="measure the FP64 DFMA / DMMA throughput of the GPU and exit")
     ap.add_argument("--cluster", type=int, default=0,
@@ -511,6 +690,10 @@ def main():
         return reference_arm(args)
     if args.peaks:
         return peaks_arm(args)
+    if args.workload == "batch256":
+        return batch256_arm(args)
+    if args.workload == "served":
+        return served_arm(args)
     return gpu_arm(args)
 
 

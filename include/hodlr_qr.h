@@ -335,6 +335,52 @@ int hodlr_dense_qr_noalloc(hodlr_ctx* ctx, int h, int w, double* A_dev, int lda,
                            int ldt);
 
 /*
+ * Continuously batched factorize/solve service (the serving workload of the benchmark; the
+ * paper has no service).  A server owns `slots` contexts on device `device`; every admitted
+ * request runs in a slot of its own, so requests that arrive while others are on the GPU start
+ * as soon as a slot and memory free up and their work overlaps on the device.
+ *   hbm_budget : device bytes that running requests and resident factors may hold.  A request
+ *                is charged its exact footprint (hodlr_footprint of build + factorization +
+ *                solve, plus its right-hand sides); least recently used resident factors that
+ *                no running request uses are evicted to make room; a request that cannot fit
+ *                even with nothing else on the device fails with HODLR_ENOMEM.
+ *   rank_cap   : rank capacity of every factorization (as in hodlr_build).
+ * Order: first come, first served, except that a solve whose factors are not ready (still being
+ * factored, busy with another request, or about to be replaced) lets later requests pass.
+ * Requests are progressed by every call on the server (submit, poll, stats); nothing blocks
+ * except the upload of a factorization's matrix when it starts.  Calls on one server must not
+ * overlap from several threads.
+ */
+typedef struct hodlr_server hodlr_server;
+int hodlr_server_create(int device, int slots, size_t hbm_budget, int rank_cap, hodlr_server** out);
+void hodlr_server_destroy(hodlr_server* S);
+/* Factorize + solve: A described as for hodlr_build (host arrays, copied by the call), hQR with
+ * truncation tolerance tol and ||A||_2 estimated on the device (Alg. 2), then x = R^{-1} Q^T b
+ * for nrhs right-hand sides B_host (n x nrhs, leading dimension ldb >= n, copied; 1..1024).
+ * keep_key >= 0 keeps the factors resident under that key for hodlr_server_submit_solve
+ * (replacing older factors under the same key); -1 frees them after the solve.  *request is
+ * the request's id.  HODLR_EINVAL for a bad partition or arguments. */
+int hodlr_server_submit(hodlr_server* S, int n, int nleaf, const int* leaf_sizes, const double* const* leaves,
+                        const double* const* U12, const double* const* V12, const int* r12,
+                        const double* const* U21, const double* const* V21, const int* r21, double tol,
+                        int nrhs, const double* B_host, int ldb, long long keep_key, long long* request);
+/* Solve with the resident factors under `key` (Sec. 1: x = R^{-1} Q^T b), nrhs right-hand sides
+ * (copied).  HODLR_ESTATE if no factorization was ever submitted under the key. */
+int hodlr_server_submit_solve(hodlr_server* S, long long key, int nrhs, const double* B_host, int ldb,
+                              long long* request);
+/* Progress the server without blocking and report request `request`: *state = 0 waiting,
+ * 1 on the GPU, 2 done, or -code when it failed (HODLR_ENOMEM: can never fit the budget,
+ * HODLR_ESTATE: its factors will never exist, HODLR_ERANK: rank capacity exceeded ...).
+ * *latency_s (may be NULL) is the time from submission to completion (to now while pending).
+ * When the request is done and X_host is not NULL, the solution (n x nrhs, leading dimension
+ * ldx >= n) is copied there and the request's record is released (HODLR_ESTATE if it was
+ * already taken); a failed request's record is released when reported. */
+int hodlr_server_poll(hodlr_server* S, long long request, int* state, double* X_host, int ldx, double* latency_s);
+/* Progress the server, then report the waiting and running requests, resident factorizations
+ * and the bytes charged against the budget (any pointer may be NULL). */
+int hodlr_server_stats(hodlr_server* S, int* waiting, int* running, int* resident, size_t* bytes_used);
+
+/*
  * hodlr_fp64_peak — measured FP64 throughput of device `device`, the roofline denominator for
  * the kernels above (they are bound by FP64 arithmetic).  Not part of the paper's method: a
  * measurement utility.  Two paths are timed with CUDA events, best of `reps` launches after one

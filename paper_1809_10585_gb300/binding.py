@@ -73,6 +73,13 @@ _SIGS = {
     "hodlr_truncate": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, _VP, _VP, C.c_double, C.c_int, _VP, _VP, _PI]),
     "hodlr_dense_qr_noalloc": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.c_int, _VP, C.c_int]),
     "hodlr_fp64_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, _PD, _PD]),
+    "hodlr_server_create": (C.c_int, [C.c_int, C.c_int, C.c_size_t, C.c_int, C.POINTER(_VP)]),
+    "hodlr_server_destroy": (None, [_VP]),
+    "hodlr_server_submit": (C.c_int, [_VP, C.c_int, C.c_int, _PI, _PPD, _PPD, _PPD, _PI, _PPD, _PPD, _PI,
+                                      C.c_double, C.c_int, _VP, C.c_int, C.c_longlong, C.POINTER(C.c_longlong)]),
+    "hodlr_server_submit_solve": (C.c_int, [_VP, C.c_longlong, C.c_int, _VP, C.c_int, C.POINTER(C.c_longlong)]),
+    "hodlr_server_poll": (C.c_int, [_VP, C.c_longlong, _PI, _VP, C.c_int, _PD]),
+    "hodlr_server_stats": (C.c_int, [_VP, _PI, _PI, _PI, C.POINTER(C.c_size_t)]),
     "hodlr_ctx_set_memory_limit": (C.c_int, [_VP, C.c_size_t]),
     "hodlr_ctx_memory_used": (C.c_int, [_VP, C.POINTER(C.c_size_t)]),
     "hodlr_device_bytes": (C.c_int, [_VP, C.POINTER(C.c_size_t)]),

@@ -1,0 +1,352 @@
+// The continuously batched factorize/solve service behind hodlr_server_* (include/hodlr_qr.h).
+// Scheduling policy: serve_sched.h.  Every slot is a library context with its own streams, so
+// the work of requests admitted while others run overlaps on the device.  Admission charges a
+// request with its exact device footprint (hodlr_footprint: storage, plans and scratch of
+// build + factorization + solve) plus its right-hand sides.  Completion is polled without
+// blocking (hodlr_ready).  Host-side code only: all numerics run in the library's kernels.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "../../include/hodlr_qr.h"
+#include "serve_sched.h"
+
+namespace hq {
+cudaStream_t ctx_stream(hodlr_ctx* ctx);
+}
+
+namespace {
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Job {
+  int kind = 0;
+  long long key = -1;
+  // factorize requests: a copy of the matrix description (hodlr_build's arguments)
+  int n = 0;
+  std::vector<int> leaf_sizes, r12, r21;
+  std::vector<std::vector<double>> leaves, U12, V12, U21, V21;
+  double tol = 0.0;
+  // right-hand sides (n x nrhs, packed) and, when done, the solution
+  int nrhs = 0;
+  std::vector<double> B, X;
+  bool taken = false;            // the solution was handed out
+  double t_submit = 0.0, t_done = 0.0;
+  // while on the device
+  hodlr_mat* M = nullptr;
+  double* dB = nullptr;
+};
+
+}  // namespace
+
+struct hodlr_server {
+  int dev = 0;
+  int rank_cap = 128;
+  std::vector<hodlr_ctx*> slots;
+  hq::ServeScheduler* sched = nullptr;
+  std::map<long long, Job> jobs;
+  std::map<long long, hodlr_mat*> resident;     // key -> factored matrix
+  std::vector<long long> slot_job;              // slot -> running request id (-1: free)
+};
+
+namespace {
+
+void evict(hodlr_server* S, long long key) {
+  auto it = S->resident.find(key);
+  if (it == S->resident.end()) return;
+  hodlr_free(it->second);
+  S->resident.erase(it);
+}
+
+int start(hodlr_server* S, const hq::ServeScheduler::Request& r) {
+  Job& j = S->jobs[r.id];
+  hodlr_ctx* ctx = S->slots[r.slot];
+  cudaStream_t st = hq::ctx_stream(ctx);
+  int rc = HODLR_OK;
+  hodlr_mat* M = nullptr;
+  if (r.kind == hq::ServeScheduler::kFactor) {
+    const int nleaf = (int)j.leaf_sizes.size(), nn = nleaf - 1;
+    std::vector<const double*> lv(nleaf), u12(std::max(1, nn)), v12(std::max(1, nn)), u21(std::max(1, nn)),
+        v21(std::max(1, nn));
+    for (int i = 0; i < nleaf; ++i) lv[i] = j.leaves[i].data();
+    for (int v = 0; v < nn; ++v) {
+      u12[v] = j.U12[v].empty() ? nullptr : j.U12[v].data();
+      v12[v] = j.V12[v].empty() ? nullptr : j.V12[v].data();
+      u21[v] = j.U21[v].empty() ? nullptr : j.U21[v].data();
+      v21[v] = j.V21[v].empty() ? nullptr : j.V21[v].data();
+    }
+    rc = hodlr_build(ctx, j.n, nleaf, j.leaf_sizes.data(), lv.data(), u12.data(), v12.data(),
+                     nn ? j.r12.data() : nullptr, u21.data(), v21.data(), nn ? j.r21.data() : nullptr,
+                     S->rank_cap, &M);
+    if (rc) return rc;
+    // the description is on the device now; keep only the right-hand sides
+    j.leaves.clear(); j.U12.clear(); j.V12.clear(); j.U21.clear(); j.V21.clear();
+    rc = hodlr_qr(ctx, M, j.tol, 0.0);
+  } else {
+    auto it = S->resident.find(r.key);
+    if (it == S->resident.end()) return HODLR_ESTATE;
+    M = it->second;
+  }
+  if (!rc && cudaMalloc(&j.dB, sizeof(double) * (size_t)j.n * j.nrhs) != cudaSuccess) {
+    cudaGetLastError();
+    j.dB = nullptr;
+    rc = HODLR_ENOMEM;
+  }
+  if (!rc && cudaMemcpyAsync(j.dB, j.B.data(), sizeof(double) * (size_t)j.n * j.nrhs, cudaMemcpyHostToDevice,
+                             st) != cudaSuccess)
+    rc = HODLR_ECUDA;
+  if (!rc) rc = hodlr_solve_async(ctx, M, j.nrhs, j.dB, j.n);
+  if (rc) {
+    cudaStreamSynchronize(st);
+    if (j.dB) cudaFree(j.dB);
+    j.dB = nullptr;
+    if (r.kind == hq::ServeScheduler::kFactor && M) hodlr_free(M);
+    return rc;
+  }
+  j.M = M;
+  S->slot_job[r.slot] = r.id;
+  return HODLR_OK;
+}
+
+// Complete finished requests (non-blocking), then admit waiting ones.
+int progress(hodlr_server* S) {
+  if (cudaSetDevice(S->dev) != cudaSuccess) return HODLR_ECUDA;
+  auto ev = [S](long long key) { evict(S, key); };
+  for (size_t s = 0; s < S->slots.size(); ++s) {
+    const long long id = S->slot_job[s];
+    if (id < 0) continue;
+    int ready = 0;
+    int rc = hodlr_ready(S->slots[s], &ready);
+    if (!rc && !ready) continue;
+    Job& j = S->jobs[id];
+    const hq::ServeScheduler::Request* r = S->sched->find(id);
+    int err = rc;
+    if (!err && r->kind == hq::ServeScheduler::kFactor) {
+      int st = 0;
+      err = hodlr_status(S->slots[s], j.M, &st, nullptr);
+      if (!err && st) err = st;
+    }
+    if (!err) {
+      j.X.resize((size_t)j.n * j.nrhs);
+      if (cudaMemcpy(j.X.data(), j.dB, sizeof(double) * j.X.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+        err = HODLR_ECUDA;
+    }
+    cudaFree(j.dB);
+    j.dB = nullptr;
+    j.t_done = now_s();
+    j.B.clear();
+    S->slot_job[s] = -1;
+    size_t held = 0;
+    if (r->kind == hq::ServeScheduler::kFactor) {
+      if (!err && r->key >= 0) {
+        hodlr_device_bytes(j.M, &held);
+        S->sched->finish(id, 0, held, ev);           // may evict older factors under the key
+        S->resident[r->key] = j.M;
+      } else {
+        hodlr_free(j.M);
+        S->sched->finish(id, err, 0, ev);
+      }
+    } else {
+      S->sched->finish(id, err, 0, ev);
+      if (S->resident.count(j.key)) {
+        hodlr_device_bytes(S->resident[j.key], &held);   // a solve plan may have grown
+        S->sched->resize_resident(j.key, held);
+      }
+    }
+    j.M = nullptr;
+  }
+  S->sched->admit([S](const hq::ServeScheduler::Request& r) { return start(S, r); }, ev);
+  return HODLR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hodlr_server_create(int device, int slots, size_t hbm_budget, int rank_cap, hodlr_server** out) {
+  if (!out || slots < 1 || slots > 256 || hbm_budget == 0 || rank_cap < 1 || rank_cap > 256) return HODLR_EINVAL;
+  hodlr_server* S = new (std::nothrow) hodlr_server();
+  if (!S) return HODLR_ENOMEM;
+  S->dev = device;
+  S->rank_cap = rank_cap;
+  for (int s = 0; s < slots; ++s) {
+    hodlr_ctx* c = nullptr;
+    int rc = hodlr_ctx_create(device, &c);
+    if (!rc) rc = hodlr_ctx_set_concurrency(c, slots);   // factorizations share the SMs
+    if (rc) {
+      if (c) hodlr_ctx_destroy(c);
+      hodlr_server_destroy(S);
+      return rc;
+    }
+    S->slots.push_back(c);
+  }
+  S->slot_job.assign(slots, -1);
+  S->sched = new (std::nothrow) hq::ServeScheduler(slots, hbm_budget);
+  if (!S->sched) {
+    hodlr_server_destroy(S);
+    return HODLR_ENOMEM;
+  }
+  *out = S;
+  return HODLR_OK;
+}
+
+void hodlr_server_destroy(hodlr_server* S) {
+  if (!S) return;
+  cudaSetDevice(S->dev);
+  for (auto* c : S->slots) hodlr_sync(c);
+  for (auto& kv : S->jobs) {
+    if (kv.second.dB) cudaFree(kv.second.dB);
+    if (kv.second.M && kv.second.kind == 0) hodlr_free(kv.second.M);
+  }
+  for (auto& kv : S->resident) hodlr_free(kv.second);
+  for (auto* c : S->slots) hodlr_ctx_destroy(c);
+  delete S->sched;
+  delete S;
+}
+
+int hodlr_server_submit(hodlr_server* S, int n, int nleaf, const int* leaf_sizes, const double* const* leaves,
+                        const double* const* U12, const double* const* V12, const int* r12,
+                        const double* const* U21, const double* const* V21, const int* r21, double tol,
+                        int nrhs, const double* B_host, int ldb, long long keep_key, long long* request) {
+  if (!S || !request || !leaves || !B_host || nrhs < 1 || nrhs > 1024 || ldb < n || !(tol >= 0) || keep_key < -1)
+    return HODLR_EINVAL;
+  size_t need = 0;
+  if (int rc = hodlr_footprint(n, nleaf, leaf_sizes, S->rank_cap, 1, 0, nrhs, &need)) return rc;
+  const int nn = nleaf - 1;
+  if (nn > 0 && (!r12 || !r21)) return HODLR_EINVAL;
+  Job j;
+  j.kind = 0;
+  j.key = keep_key;
+  j.n = n;
+  j.tol = tol;
+  j.nrhs = nrhs;
+  j.leaf_sizes.assign(leaf_sizes, leaf_sizes + nleaf);
+  std::vector<int> lo(2 * nleaf - 1), hi(2 * nleaf - 1);
+  int off = 0;
+  for (int i = 0; i < nleaf; ++i) {
+    lo[nleaf - 1 + i] = off;
+    off += leaf_sizes[i];
+    hi[nleaf - 1 + i] = off;
+    if (!leaves[i]) return HODLR_EINVAL;
+    j.leaves.emplace_back(leaves[i], leaves[i] + (size_t)leaf_sizes[i] * leaf_sizes[i]);
+  }
+  for (int v = nleaf - 2; v >= 0; --v) {
+    lo[v] = lo[2 * v + 1];
+    hi[v] = hi[2 * v + 2];
+  }
+  for (int v = 0; v < nn; ++v) {
+    const size_t a = hi[2 * v + 1] - lo[2 * v + 1], b = hi[2 * v + 2] - lo[2 * v + 2];
+    if (r12[v] < 0 || r21[v] < 0) return HODLR_EINVAL;
+    auto cp = [](const double* const* arr, int v, size_t cnt, std::vector<std::vector<double>>& dst) {
+      if (cnt == 0) {
+        dst.emplace_back();
+        return true;
+      }
+      if (!arr || !arr[v]) return false;
+      dst.emplace_back(arr[v], arr[v] + cnt);
+      return true;
+    };
+    if (!cp(U12, v, a * r12[v], j.U12) || !cp(V12, v, b * r12[v], j.V12) || !cp(U21, v, b * r21[v], j.U21) ||
+        !cp(V21, v, a * r21[v], j.V21))
+      return HODLR_EINVAL;
+    j.r12.push_back(r12[v]);
+    j.r21.push_back(r21[v]);
+  }
+  j.B.resize((size_t)n * nrhs);
+  for (int c = 0; c < nrhs; ++c) memcpy(j.B.data() + (size_t)c * n, B_host + (size_t)c * ldb, sizeof(double) * n);
+  j.t_submit = now_s();
+  need += sizeof(double) * (size_t)n * nrhs;
+  const long long id = S->sched->submit(hq::ServeScheduler::kFactor, keep_key, need);
+  S->jobs[id] = std::move(j);
+  *request = id;
+  return progress(S);
+}
+
+int hodlr_server_submit_solve(hodlr_server* S, long long key, int nrhs, const double* B_host, int ldb,
+                              long long* request) {
+  if (!S || !request || !B_host || key < 0 || nrhs < 1 || nrhs > 1024) return HODLR_EINVAL;
+  // the order n comes from the resident matrix or from the waiting factorization producing it
+  int n = -1;
+  std::vector<int> leaf_sizes;
+  for (auto& kv : S->jobs)
+    if (kv.second.kind == 0 && kv.second.key == key) {
+      n = kv.second.n;
+      leaf_sizes = kv.second.leaf_sizes;
+    }
+  if (n < 0) return HODLR_ESTATE;                    // no factors under key, none coming
+  if (ldb < n) return HODLR_EINVAL;
+  size_t with = 0, without = 0;
+  hodlr_footprint(n, (int)leaf_sizes.size(), leaf_sizes.data(), S->rank_cap, 1, 0, nrhs, &with);
+  hodlr_footprint(n, (int)leaf_sizes.size(), leaf_sizes.data(), S->rank_cap, 1, 0, 0, &without);
+  Job j;
+  j.kind = 1;
+  j.key = key;
+  j.n = n;
+  j.leaf_sizes = leaf_sizes;
+  j.nrhs = nrhs;
+  j.B.resize((size_t)n * nrhs);
+  for (int c = 0; c < nrhs; ++c) memcpy(j.B.data() + (size_t)c * n, B_host + (size_t)c * ldb, sizeof(double) * n);
+  j.t_submit = now_s();
+  // right-hand sides plus, at most, a solve plan of this width
+  const size_t need = sizeof(double) * (size_t)n * nrhs + (with - without);
+  const long long id = S->sched->submit(hq::ServeScheduler::kSolve, key, need);
+  S->jobs[id] = std::move(j);
+  *request = id;
+  return progress(S);
+}
+
+int hodlr_server_poll(hodlr_server* S, long long request, int* state, double* X_host, int ldx, double* latency_s) {
+  if (!S || !state) return HODLR_EINVAL;
+  if (int rc = progress(S)) return rc;
+  const hq::ServeScheduler::Request* r = S->sched->find(request);
+  auto it = S->jobs.find(request);
+  if (!r || it == S->jobs.end()) return HODLR_EINVAL;
+  Job& j = it->second;
+  if (r->state == hq::ServeScheduler::kFailed) {
+    *state = -r->error;
+  } else {
+    *state = r->state == hq::ServeScheduler::kDone ? 2 : r->state;
+  }
+  if (latency_s) *latency_s = (r->state == hq::ServeScheduler::kDone || r->state == hq::ServeScheduler::kFailed)
+                                  ? j.t_done - j.t_submit : now_s() - j.t_submit;
+  const bool finished = r->state == hq::ServeScheduler::kDone || r->state == hq::ServeScheduler::kFailed;
+  if (r->state == hq::ServeScheduler::kDone && X_host) {
+    if (ldx < j.n) return HODLR_EINVAL;
+    if (j.taken) return HODLR_ESTATE;              // handed out by an earlier poll
+    for (int c = 0; c < j.nrhs; ++c)
+      memcpy(X_host + (size_t)c * ldx, j.X.data() + (size_t)c * j.n, sizeof(double) * j.n);
+  }
+  // a finished request's record is released once its result was taken (or it failed), except
+  // that a factorization stays known while solves may still name its key
+  if (finished && (X_host || r->state == hq::ServeScheduler::kFailed)) {
+    const bool keep_record = j.kind == 0 && j.key >= 0 && S->sched->is_resident(j.key);
+    if (!keep_record) {
+      S->sched->forget(request);
+      S->jobs.erase(it);
+    } else if (X_host) {
+      j.taken = true;
+      j.X.clear();
+      j.X.shrink_to_fit();
+    }
+  }
+  return HODLR_OK;
+}
+
+int hodlr_server_stats(hodlr_server* S, int* waiting, int* running, int* resident, size_t* bytes_used) {
+  if (!S) return HODLR_EINVAL;
+  if (int rc = progress(S)) return rc;
+  if (waiting) *waiting = S->sched->waiting();
+  if (running) *running = S->sched->running();
+  if (resident) *resident = S->sched->resident_count();
+  if (bytes_used) *bytes_used = S->sched->used();
+  return HODLR_OK;
+}
+
+}  // extern "C"

@@ -1,25 +1,23 @@
-"""Continuously batched factorize/solve service on one GPU, over the C ABI.
+"""Continuously batched factorize/solve service on one GPU: a thin Python client of the C ABI
+server (hodlr_server_* in include/hodlr_qr.h; scheduling policy in csrc/serve_sched.h).
 
 Requests
-  * FactorSolve(inp, rhs, tol, keep): build the HODLR matrix on the device, hQR, solve with the
-    right-hand sides, return x; keep=True keeps the factors resident under `key` for later
+  * FactorSolve(inp, rhs, tol, keep, key): build the HODLR matrix on the device, hQR, solve with
+    the right-hand sides, return x; keep=True keeps the factors resident under `key` for later
     Solve requests (repeat right-hand sides hit resident factors).
   * Solve(key, rhs): solve with resident factors.
 
-Continuous batching: every admitted request gets a slot — a library context with its own
-streams — so work of requests that arrive while others are on the GPU overlaps on the device.
-Requests are admitted as soon as a slot is free and their estimated HBM footprint fits the
-budget (least recently used resident factors are evicted to make room).  Completion is
-polled without blocking (hodlr_ready).  Latency is measured from arrival to completion.
-
-Every numeric step runs in the CUDA library; this module only schedules.
+The server admits a request as soon as a slot is free and its exact device footprint
+(hodlr_footprint plus its right-hand sides) fits the HBM budget, evicting least recently used
+resident factors to make room; requests admitted while others run overlap on the device.
+Latency runs from submission to completion.  This module only marshals arguments and replays
+arrival times: scheduling and every numeric step run in the library.
 """
 from __future__ import annotations
 
+import ctypes as C
 import dataclasses
-import itertools
 import time
-from collections import OrderedDict, deque
 
 import numpy as np
 
@@ -52,67 +50,92 @@ class Result:
     n: int
 
 
-def footprint_bytes(n: int, nleaf: int, leaf: int, rank_cap: int, nrhs: int) -> int:
-    """HBM estimate of one factorization: storage of A/Y/R and T (leaves and rank_cap
-    factors on every level), planner scratch (about four times the factor storage at these
-    shapes) and the right-hand sides."""
-    levels = max(0, nleaf.bit_length() - 1)
-    leaves = 2 * nleaf * leaf * leaf * 8
-    factors = 3 * n * levels * rank_cap * 8
-    scratch = 4 * factors + 16 * n * rank_cap * 8
-    return int(leaves + factors + scratch + 3 * n * max(nrhs, 1) * 8)
+def footprint_bytes(inp, rank_cap: int, nrhs: int) -> int:
+    """Device bytes the server charges a FactorSolve request: the exact footprint of build +
+    factorization + solve (hodlr_footprint) plus its right-hand sides."""
+    return B.footprint(inp.n, inp.leaf_sizes, rank_cap, estimate_norm=True, nrhs=nrhs) + 8 * inp.n * nrhs
+
+
+def _rhs(a):
+    a = np.asarray(a, dtype=np.float64)
+    if a.ndim == 1:
+        a = a[:, None]
+    return np.asfortranarray(a)
 
 
 class Server:
     def __init__(self, device: int = 0, slots: int = 8, hbm_budget: float = 120e9, rank_cap: int = 256):
-        import torch
-        self.torch = torch
-        self.device = device
-        self.dev = f"cuda:{device}"      # where right-hand sides are staged
-        self.slots = [B.Context(device) for _ in range(slots)]
-        for c in self.slots:             # several factorizations share the SMs
-            c.concurrency = slots
-        self.free = deque(range(slots))
-        self.budget = float(hbm_budget)
-        self.used = 0.0
         self.rank_cap = rank_cap
-        self.waiting: deque = deque()
-        self.active = {}                 # slot -> (rid, req, matrix, rhs tensor, t_arrival, bytes, kind)
-        self.resident: OrderedDict = OrderedDict()   # key -> (matrix, bytes)
+        self.h = B._VP()
+        B.check(B.lib().hodlr_server_create(device, slots, C.c_size_t(int(hbm_budget)), rank_cap, C.byref(self.h)),
+                "hodlr_server_create")
+        self.keys: dict[str, int] = {}
         self.results: dict[int, Result] = {}
-        self.ids = itertools.count()
-        self.t0 = time.perf_counter()
+        self.pending: dict[int, tuple] = {}       # id -> (kind, n, nrhs)
+        self.max_running = 0
 
     # ------------------------------------------------------------------------------ API
-    def now(self) -> float:
-        return time.perf_counter() - self.t0
+    def _key(self, name):
+        if name not in self.keys:
+            self.keys[name] = len(self.keys)
+        return self.keys[name]
 
     def submit(self, req) -> int:
-        rid = next(self.ids)
-        self.waiting.append((rid, req, self.now() if req.arrival <= 0 else req.arrival))
-        return rid
+        rid = C.c_longlong()
+        rhs = _rhs(req.rhs)
+        nrhs = rhs.shape[1]
+        if isinstance(req, Solve):
+            if req.key not in self.keys:
+                raise KeyError(f"no factorization was submitted under {req.key!r}")
+            B.check(B.lib().hodlr_server_submit_solve(self.h, self.keys[req.key], nrhs, B._VP(rhs.ctypes.data),
+                                                      rhs.shape[0], C.byref(rid)), "hodlr_server_submit_solve")
+            self.pending[rid.value] = ("solve", rhs.shape[0], nrhs)
+        else:
+            sizes, leaves, U12, V12, r12, U21, V21, r21, keep = B._marshal(req.inp)
+            key = self._key(req.key) if (req.keep and req.key is not None) else -1
+            B.check(B.lib().hodlr_server_submit(self.h, req.inp.n, len(req.inp.leaf_sizes), sizes, leaves, U12, V12,
+                                                r12, U21, V21, r21, req.tol, nrhs, B._VP(rhs.ctypes.data),
+                                                rhs.shape[0], key, C.byref(rid)), "hodlr_server_submit")
+            self.pending[rid.value] = ("factor_solve", req.inp.n, nrhs)
+        return rid.value
+
+    def poll(self):
+        """Progress the server; collect finished requests into self.results."""
+        running = C.c_int()
+        B.check(B.lib().hodlr_server_stats(self.h, None, C.byref(running), None, None), "hodlr_server_stats")
+        self.max_running = max(self.max_running, running.value)
+        for rid in list(self.pending):
+            kind, n, nrhs = self.pending[rid]
+            st, lat = C.c_int(), C.c_double()
+            B.check(B.lib().hodlr_server_poll(self.h, rid, C.byref(st), None, n, C.byref(lat)), "hodlr_server_poll")
+            if st.value < 0:
+                del self.pending[rid]
+                raise B.HodlrError(-st.value, f"request {rid}")
+            if st.value == 2:
+                x = np.zeros((n, nrhs), order="F")
+                B.check(B.lib().hodlr_server_poll(self.h, rid, C.byref(st), B._VP(x.ctypes.data), n, C.byref(lat)),
+                        "hodlr_server_poll")
+                self.results[rid] = Result(rid, x, lat.value, kind, n)
+                del self.pending[rid]
 
     def run(self, requests, poll_sleep=2e-4):
         """Replay requests with their arrival times (seconds from now) and serve them all."""
-        pending = sorted(((r.arrival, i, r) for i, r in enumerate(requests)), key=lambda t: (t[0], t[1]))
-        self.t0 = time.perf_counter()
-        order = []
+        order_in = sorted(range(len(requests)), key=lambda i: (requests[i].arrival, i))
+        t0 = time.perf_counter()
+        ids = {}
         k = 0
-        while k < len(pending) or self.waiting or self.active:
-            now = self.now()
-            while k < len(pending) and pending[k][0] <= now:
-                order.append(self.submit(pending[k][2]))
+        while k < len(order_in) or self.pending:
+            now = time.perf_counter() - t0
+            while k < len(order_in) and requests[order_in[k]].arrival <= now:
+                i = order_in[k]
+                ids[i] = self.submit(requests[i])
                 k += 1
-            self.step()
-            if not self.active and not self.waiting and k < len(pending):
-                time.sleep(max(0.0, min(pending[k][0] - self.now(), 0.01)))
+            self.poll()
+            if not self.pending and k < len(order_in):
+                time.sleep(max(0.0, min(requests[order_in[k]].arrival - (time.perf_counter() - t0), 0.01)))
             else:
                 time.sleep(poll_sleep)
-        return [self.results[r] for r in order]
-
-    def step(self):
-        self._poll()
-        self._admit()
+        return [self.results[ids[i]] for i in range(len(requests))]
 
     def latencies(self):
         lat = np.array([r.latency_s for r in self.results.values()])
@@ -121,98 +144,20 @@ class Server:
         return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                 "count": int(lat.size)}
 
+    def stats(self):
+        w, r, res = C.c_int(), C.c_int(), C.c_int()
+        b = C.c_size_t()
+        B.check(B.lib().hodlr_server_stats(self.h, C.byref(w), C.byref(r), C.byref(res), C.byref(b)),
+                "hodlr_server_stats")
+        return {"waiting": w.value, "running": r.value, "resident": res.value, "bytes": int(b.value)}
+
     def close(self):
-        for _, (M, _) in list(self.resident.items()):
-            M.free()
-        self.resident.clear()
-        for c in self.slots:
-            c.close()
+        if self.h:
+            B.lib().hodlr_server_destroy(self.h)
+            self.h = B._VP()
 
-    # ------------------------------------------------------------------------- internals
-    def _bytes_of(self, req):
-        if isinstance(req, Solve):
-            return 3 * req.rhs.shape[0] * max(1, req.rhs.shape[1]) * 8
-        inp = req.inp
-        return footprint_bytes(inp.n, len(inp.leaf_sizes), max(inp.leaf_sizes), self.rank_cap,
-                               req.rhs.shape[1] if req.rhs.ndim > 1 else 1)
-
-    def _evict_for(self, need):
-        while self.used + need > self.budget and self.resident:
-            key, (M, b) = self.resident.popitem(last=False)
-            if any(a[2] is M for a in self.active.values()):
-                self.resident[key] = (M, b)     # in use: keep, stop evicting
-                self.resident.move_to_end(key, last=False)
-                break
-            M.free()
-            self.used -= b
-
-    def _producer_pending(self, key):
-        """A FactorSolve that will keep factors under `key` is waiting or running."""
-        if any(isinstance(r, FactorSolve) and r.keep and r.key == key for _, r, _ in self.waiting):
-            return True
-        return any(a[6] == "factor_solve" and a[1].keep and a[1].key == key for a in self.active.values())
-
-    def _admit(self):
-        torch = self.torch
-        # first come, first served, except that a solve whose factors are not ready yet (still
-        # being factored, or busy with another solve) lets later requests pass
-        for item in list(self.waiting):
-            if not self.free:
-                return
-            rid, req, t_arr = item
-            if isinstance(req, Solve):
-                if req.key not in self.resident:
-                    if self._producer_pending(req.key):
-                        continue
-                    raise KeyError(f"no resident factors under {req.key!r}")
-                if any(a[2] is self.resident[req.key][0] for a in self.active.values()):
-                    continue                     # one solve per resident matrix at a time
-            need = self._bytes_of(req)
-            self._evict_for(need)
-            if self.used + need > self.budget and self.active:
-                return                           # wait for memory to free up
-            self.waiting = deque(x for x in self.waiting if x[0] != rid)
-            slot = self.free.popleft()
-            ctx = self.slots[slot]
-            rhs = np.asarray(req.rhs, dtype=np.float64)
-            if rhs.ndim == 1:
-                rhs = rhs[:, None]
-            nrhs = rhs.shape[1]
-            bt = torch.from_numpy(np.ascontiguousarray(rhs.T)).to(self.dev)
-            if isinstance(req, Solve):
-                M, _ = self.resident[req.key]
-                self.resident.move_to_end(req.key)
-                M.solve_async(nrhs, bt.data_ptr(), rhs.shape[0], ctx=ctx)
-                kind = "solve"
-            else:
-                M = B.Matrix(ctx, req.inp, rank_cap=self.rank_cap)
-                M.qr(req.tol, 0.0)
-                M.solve_async(nrhs, bt.data_ptr(), rhs.shape[0])
-                kind = "factor_solve"
-            self.used += need
-            self.active[slot] = (rid, req, M, bt, t_arr, need, kind)
-
-    def _poll(self):
-        for slot in list(self.active):
-            ctx = self.slots[slot]
-            if not ctx.ready():
-                continue
-            rid, req, M, bt, t_arr, need, kind = self.active.pop(slot)
-            st, _ = (0, 0.0) if kind == "solve" else M.status()
-            if st not in (0,):
-                raise B.HodlrError(st, "factorization")
-            x = bt.cpu().numpy().T.copy()
-            self.results[rid] = Result(rid, x, self.now() - t_arr, kind, M.n)
-            self.used -= need
-            if kind == "factor_solve":
-                if req.keep and req.key:
-                    old = self.resident.pop(req.key, None)
-                    if old is not None and old[0] is not M:
-                        old[0].free()
-                        self.used -= old[1]
-                    fb = footprint_bytes(M.n, M.nleaf, 0, self.rank_cap, 0)
-                    self.resident[req.key] = (M, fb)
-                    self.used += fb
-                else:
-                    M.free()
-            self.free.append(slot)
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
