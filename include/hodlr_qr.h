@@ -348,7 +348,9 @@ int hodlr_dense_qr_noalloc(hodlr_ctx* ctx, int h, int w, double* A_dev, int lda,
  * Order: first come, first served, except that a solve whose factors are not ready (still being
  * factored, busy with another request, or about to be replaced) lets later requests pass.
  * Requests are progressed by every call on the server (submit, poll, stats); nothing blocks
- * except the upload of a factorization's matrix when it starts.  Calls on one server must not
+ * except the upload of a factorization's matrix when it starts.  Device memory of finished
+ * requests is freed while no request runs (cudaFree waits for the whole device), or at once
+ * when such retired memory exceeds a quarter of the budget.  Calls on one server must not
  * overlap from several threads.
  */
 typedef struct hodlr_server hodlr_server;

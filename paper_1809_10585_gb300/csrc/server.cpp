@@ -54,14 +54,40 @@ struct hodlr_server {
   std::map<long long, Job> jobs;
   std::map<long long, hodlr_mat*> resident;     // key -> factored matrix
   std::vector<long long> slot_job;              // slot -> running request id (-1: free)
+  // Right-hand-side buffers, one per slot, grown on demand and reused: cudaFree waits for the
+  // whole device, so nothing is freed while requests run.  Matrices released while others run
+  // (finished factorizations that are not kept, evicted factors) wait in `retired` until no
+  // request is on the device.
+  std::vector<double*> slot_buf;
+  std::vector<size_t> slot_buf_doubles;
+  std::vector<hodlr_mat*> retired;
+  size_t budget = 0;
 };
 
 namespace {
 
+// Free retired matrices once nothing runs on the device (their cudaFree would otherwise wait
+// for every running request).
+void release_retired(hodlr_server* S) {
+  if (S->retired.empty()) return;
+  bool idle = true;
+  for (long long id : S->slot_job) idle = idle && id < 0;
+  // under continuous load the device is never idle: past a quarter of the budget, free anyway
+  size_t bytes = 0;
+  for (auto* M : S->retired) {
+    size_t b = 0;
+    hodlr_device_bytes(M, &b);
+    bytes += b;
+  }
+  if (!idle && bytes <= S->budget / 4) return;
+  for (auto* M : S->retired) hodlr_free(M);
+  S->retired.clear();
+}
+
 void evict(hodlr_server* S, long long key) {
   auto it = S->resident.find(key);
   if (it == S->resident.end()) return;
-  hodlr_free(it->second);
+  S->retired.push_back(it->second);
   S->resident.erase(it);
 }
 
@@ -94,20 +120,29 @@ int start(hodlr_server* S, const hq::ServeScheduler::Request& r) {
     if (it == S->resident.end()) return HODLR_ESTATE;
     M = it->second;
   }
-  if (!rc && cudaMalloc(&j.dB, sizeof(double) * (size_t)j.n * j.nrhs) != cudaSuccess) {
-    cudaGetLastError();
-    j.dB = nullptr;
-    rc = HODLR_ENOMEM;
+  const size_t nb = (size_t)j.n * j.nrhs;
+  if (!rc && S->slot_buf_doubles[r.slot] < nb) {
+    // growing the slot's buffer frees the old one: only here, and the old one is idle
+    if (S->slot_buf[r.slot]) cudaFree(S->slot_buf[r.slot]);
+    S->slot_buf[r.slot] = nullptr;
+    S->slot_buf_doubles[r.slot] = 0;
+    if (cudaMalloc(&S->slot_buf[r.slot], sizeof(double) * nb) != cudaSuccess) {
+      cudaGetLastError();
+      S->slot_buf[r.slot] = nullptr;
+      rc = HODLR_ENOMEM;
+    } else {
+      S->slot_buf_doubles[r.slot] = nb;
+    }
   }
+  j.dB = rc ? nullptr : S->slot_buf[r.slot];
   if (!rc && cudaMemcpyAsync(j.dB, j.B.data(), sizeof(double) * (size_t)j.n * j.nrhs, cudaMemcpyHostToDevice,
                              st) != cudaSuccess)
     rc = HODLR_ECUDA;
   if (!rc) rc = hodlr_solve_async(ctx, M, j.nrhs, j.dB, j.n);
   if (rc) {
     cudaStreamSynchronize(st);
-    if (j.dB) cudaFree(j.dB);
     j.dB = nullptr;
-    if (r.kind == hq::ServeScheduler::kFactor && M) hodlr_free(M);
+    if (r.kind == hq::ServeScheduler::kFactor && M) S->retired.push_back(M);
     return rc;
   }
   j.M = M;
@@ -138,8 +173,7 @@ int progress(hodlr_server* S) {
       if (cudaMemcpy(j.X.data(), j.dB, sizeof(double) * j.X.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
         err = HODLR_ECUDA;
     }
-    cudaFree(j.dB);
-    j.dB = nullptr;
+    j.dB = nullptr;                                  // the slot's buffer, kept for reuse
     j.t_done = now_s();
     j.B.clear();
     S->slot_job[s] = -1;
@@ -150,7 +184,7 @@ int progress(hodlr_server* S) {
         S->sched->finish(id, 0, held, ev);           // may evict older factors under the key
         S->resident[r->key] = j.M;
       } else {
-        hodlr_free(j.M);
+        S->retired.push_back(j.M);
         S->sched->finish(id, err, 0, ev);
       }
     } else {
@@ -162,6 +196,7 @@ int progress(hodlr_server* S) {
     }
     j.M = nullptr;
   }
+  release_retired(S);
   S->sched->admit([S](const hq::ServeScheduler::Request& r) { return start(S, r); }, ev);
   return HODLR_OK;
 }
@@ -176,6 +211,7 @@ int hodlr_server_create(int device, int slots, size_t hbm_budget, int rank_cap, 
   if (!S) return HODLR_ENOMEM;
   S->dev = device;
   S->rank_cap = rank_cap;
+  S->budget = hbm_budget;
   for (int s = 0; s < slots; ++s) {
     hodlr_ctx* c = nullptr;
     int rc = hodlr_ctx_create(device, &c);
@@ -188,6 +224,8 @@ int hodlr_server_create(int device, int slots, size_t hbm_budget, int rank_cap, 
     S->slots.push_back(c);
   }
   S->slot_job.assign(slots, -1);
+  S->slot_buf.assign(slots, nullptr);
+  S->slot_buf_doubles.assign(slots, 0);
   S->sched = new (std::nothrow) hq::ServeScheduler(slots, hbm_budget);
   if (!S->sched) {
     hodlr_server_destroy(S);
@@ -201,11 +239,12 @@ void hodlr_server_destroy(hodlr_server* S) {
   if (!S) return;
   cudaSetDevice(S->dev);
   for (auto* c : S->slots) hodlr_sync(c);
-  for (auto& kv : S->jobs) {
-    if (kv.second.dB) cudaFree(kv.second.dB);
+  for (auto& kv : S->jobs)
     if (kv.second.M && kv.second.kind == 0) hodlr_free(kv.second.M);
-  }
   for (auto& kv : S->resident) hodlr_free(kv.second);
+  for (auto* M : S->retired) hodlr_free(M);
+  for (auto* p : S->slot_buf)
+    if (p) cudaFree(p);
   for (auto* c : S->slots) hodlr_ctx_destroy(c);
   delete S->sched;
   delete S;

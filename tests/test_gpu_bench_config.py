@@ -1,9 +1,9 @@
 """Parity of the configuration that bench.py times, against the CPU oracle.
 
 The bench factors independent seeded matrices of the n = 8192, nmin = 256, rank-10,
-column-scaled (condition ~1e14) workload at tol = 1e-12 as one batched CUDA graph, with 4-CTA
-clusters and several factorizations in flight: the QR and Jacobi kernels then take their
-shared-memory-capped, global-memory and one-CTA forms.  A batch of three matrices (different
+column-scaled (condition ~1e14) workload at tol = 1e-12 as one batched CUDA graph, with the
+bench's cluster size and several factorizations in flight: the QR and Jacobi kernels then take their
+shared-memory-capped, blocked and one-CTA forms.  A batch of three matrices (different
 seeds) puts the kernels in the same forms as the bench's larger batches.  Every matrix of the
 batch is compared with the oracle's hQR (Alg. 2) of the same seeded input:
 
@@ -26,7 +26,7 @@ from paper_1809_10585_gb300 import binding as B  # noqa: E402
 
 SEEDS = (0, 1, 2)
 TOL = 1e-12
-BENCH_CLUSTER = 4
+from bench import BATCH_CLUSTER as BENCH_CLUSTER  # noqa: E402  (the cluster size bench.py uses)
 
 
 def test_batched_graph_of_bench_workload_matches_oracle():
