@@ -590,7 +590,10 @@ def batch256_arm(args):
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": None, "peak_source": PEAK_RECORD if rec else "measured in this run"}}
     if rank == 0 and not args.no_cpu_baseline:
-        sample = sorted(range(count), key=lambda i: inps[i].n)[:: max(1, count // 6)][:6]
+        # a bounded sample (about half a minute of host work): matrices of n <= 8192 spread over
+        # the batch's sizes and ranks
+        small = [i for i in sorted(range(count), key=lambda i: inps[i].n) if inps[i].n <= 8192]
+        sample = small[:: max(1, len(small) // 5)][:5]
         t = 0.0
         n_flops = 0.0
         import oracle.core as O
@@ -603,6 +606,81 @@ def batch256_arm(args):
                                 "sample": f"{len(sample)} matrices of the batch spread over n "
                                           f"({min(inps[i].n for i in sample)}..{max(inps[i].n for i in sample)}), "
                                           "timed whole; rate scaled by algorithmic flops to the batch's mean"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def single_arm(args):
+    """One matrix of the n = 1024 workload (nmin 128, rank 5, tol 1e-10) or of the kernel-generated
+    n = 65536 workload (A_ij = 1/(x_i - y_j) + n delta_ij, off-diagonal blocks compressed at
+    1e-12, tol 1e-12), factored by the plain one-matrix path (one CUDA graph per factorization,
+    the device's largest cluster size), with the oracle on the host cores beside it."""
+    import torch
+    import workloads as W
+    from paper_1809_10585_gb300 import binding as B
+    from paper_1809_10585_gb300 import build as BUILD
+    BUILD.build()
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if args.workload == "n1024":
+        inp, tol, name = W.config0(seed=rank), 1e-10, "hodlr_qr_n1024_nmin128_k5_tol1e-10"
+        kc = 64
+    else:
+        t = time.perf_counter()
+        inp = W.kernel_hodlr(65536, 256, 1e-12, seed=rank, device="cuda")
+        t_gen = time.perf_counter() - t
+        tol, name, kc = 1e-12, "hodlr_qr_n65536_nmin256_kernel_1/(x-y)_tol1e-12", 256
+        torch.cuda.empty_cache()
+    ctx = B.Context(local)
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream.cuda_stream)
+    M = B.Matrix(ctx, inp, rank_cap=kc)
+    M.snapshot()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 1)):
+            M.qr_graph(tol, 0.0)
+    ctx.sync()
+    st, anorm = M.status()
+    if st != 0:
+        raise RuntimeError(f"factorization status {st}")
+    flops = M.flops()["total"]
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            M.qr_graph(tol, 0.0)
+            evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), "cuda") / args.steps
+    rec = recorded_fp64_peak()
+    peak = rec[0] if rec else B.fp64_peak(local)["dfma"]
+    achieved = flops / (ms / 1e3) / 1e12
+    stats = M.stats()
+    line = {"metric": METRIC, "value": 1e3 / ms * ws, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "n": inp.n, "nmin": max(inp.leaf_sizes), "tol": tol, "rank_cap": kc,
+                       "cluster": ctx.cluster, "anorm": anorm, "max_rank_Y": stats["max_rank_Y"],
+                       "max_rank_T": stats["max_rank_T"], "max_rank_R": stats["max_rank_R"],
+                       "l2": "flushed (256 MiB write) between timed steps"},
+            "effective_gflops": flops / (ms / 1e3) / 1e9, "algorithmic_gflop_per_step": flops / 1e9,
+            "clocks": clk,
+            "roofline": {"bound": "alu", "kernel": "one hQR factorization (CUDA graph)", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": PEAK_RECORD if rec else "measured in this run"}}
+    if args.workload == "n65536":
+        line["config"]["host_generation_s"] = t_gen
+    if rank == 0 and not args.no_cpu_baseline:
+        t = time_oracle(inp)
+        line["cpu_baseline"] = {"value": 1.0 / t, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                                "sample": f"one full factorization of the same n={inp.n} matrix"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -741,7 +819,7 @@ def main():
     ap.add_argument("--served-requests", type=int, default=24, help="requests per rate of the served sweep")
     ap.add_argument("--served-rates", default="0.5,2,8,32", help="arrival rates (requests/s) of the served sweep")
     ap.add_argument("--served-pool", type=int, default=12, help="distinct matrices the served sweep draws from")
-    ap.add_argument("--workload", default="n8192", choices=["n8192", "batch256", "served"],
+    ap.add_argument("--workload", default="n8192", choices=["n8192", "batch256", "served", "n1024", "n65536"],
                     help="n8192: the ill-conditioned n = 8192 workload (default); batch256: 256 matrices of "
                          "log-uniform n in [2048, 32768]")
     ap.add_argument("--peaks", action="store_true",
@@ -759,6 +837,8 @@ def main():
         return batch256_arm(args)
     if args.workload == "served":
         return served_arm(args)
+    if args.workload in ("n1024", "n65536"):
+        return single_arm(args)
     return gpu_arm(args)
 
 

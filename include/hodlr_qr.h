@@ -60,6 +60,13 @@ int hodlr_ctx_set_stream(hodlr_ctx* ctx, void* stream);
  * CTAs.  Graphs captured earlier are re-captured on their next call.  HODLR_EINVAL for a size
  * below 1 or above the device's maximum. */
 int hodlr_ctx_set_cluster(hodlr_ctx* ctx, int cluster);
+/* Cluster size for large problems: a QR whose columns fit neither the shared memory of the
+ * context's cluster nor, as one 16-column panel, that of one CTA, and a Jacobi core whose
+ * columns do not fit the cluster's shared memory, run on up to this many CTAs instead (so that
+ * they avoid the slower global-memory forms).  0 (the default) keeps every launch at the
+ * context's cluster size.  Results depend on it at the level of rounding only.  HODLR_EINVAL
+ * above the device's maximum. */
+int hodlr_ctx_set_cluster_large(hodlr_ctx* ctx, int cluster);
 int hodlr_ctx_get_cluster(hodlr_ctx* ctx, int* cluster);
 /* Number of factorizations the caller runs on the GPU at the same time through this and other
  * contexts (default 1).  Above 1, the QR and Jacobi kernels reserve less shared memory per CTA
@@ -90,6 +97,18 @@ int hodlr_sync(hodlr_ctx* ctx);
  */
 int hodlr_ctx_set_memory_limit(hodlr_ctx* ctx, size_t bytes);
 int hodlr_ctx_memory_used(hodlr_ctx* ctx, size_t* bytes);
+/* Reserve `bytes` of device memory once (one cudaMalloc) as the pool of the context's account:
+ * every later device allocation for matrices built through the context is carved from it on the
+ * host, and hodlr_free returns it to the pool, without any CUDA call.  cudaMalloc and cudaFree
+ * wait for the whole device, so a pool keeps work of other streams (other requests) running
+ * while matrices come and go.  With a pool, hodlr_free does not wait for the device: free a
+ * matrix only after its work has completed (hodlr_sync, hodlr_ready).  An allocation that does
+ * not fit the pool fails with HODLR_ENOMEM.  HODLR_ESTATE if the context already has a pool or
+ * holds memory.  The pool is released when the last context and matrix using it are gone. */
+int hodlr_ctx_set_memory_pool(hodlr_ctx* ctx, size_t bytes);
+/* Make `ctx` use the memory account (limit, pool) of `from` (same device; ctx must hold no
+ * memory yet, else HODLR_ESTATE). */
+int hodlr_ctx_share_memory(hodlr_ctx* ctx, hodlr_ctx* from);
 
 /*
  * hodlr_build — allocate a device-resident HODLR matrix and upload it (Sec. 2.1, Eq. (3)).
@@ -348,10 +367,10 @@ int hodlr_dense_qr_noalloc(hodlr_ctx* ctx, int h, int w, double* A_dev, int lda,
  * Order: first come, first served, except that a solve whose factors are not ready (still being
  * factored, busy with another request, or about to be replaced) lets later requests pass.
  * Requests are progressed by every call on the server (submit, poll, stats); nothing blocks
- * except the upload of a factorization's matrix when it starts.  Device memory of finished
- * requests is freed while no request runs (cudaFree waits for the whole device), or at once
- * when such retired memory exceeds a quarter of the budget.  Calls on one server must not
- * overlap from several threads.
+ * except the upload of a factorization's matrix when it starts.  All device memory of the
+ * server comes from one pool of hbm_budget + hbm_budget / 8 bytes reserved at creation
+ * (hodlr_ctx_set_memory_pool), so requests that come and go never wait for the device.  Calls
+ * on one server must not overlap from several threads.
  */
 typedef struct hodlr_server hodlr_server;
 int hodlr_server_create(int device, int slots, size_t hbm_budget, int rank_cap, hodlr_server** out);

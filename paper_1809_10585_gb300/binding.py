@@ -37,6 +37,7 @@ _SIGS = {
     "hodlr_ctx_set_stream": (C.c_int, [_VP, _VP]),
     "hodlr_ctx_set_cluster": (C.c_int, [_VP, C.c_int]),
     "hodlr_ctx_get_cluster": (C.c_int, [_VP, _PI]),
+    "hodlr_ctx_set_cluster_large": (C.c_int, [_VP, C.c_int]),
     "hodlr_ctx_set_concurrency": (C.c_int, [_VP, C.c_int]),
     "hodlr_ctx_get_concurrency": (C.c_int, [_VP, _PI]),
     "hodlr_ctx_set_batch_group": (C.c_int, [_VP, C.c_int]),
@@ -82,6 +83,8 @@ _SIGS = {
     "hodlr_server_stats": (C.c_int, [_VP, _PI, _PI, _PI, C.POINTER(C.c_size_t)]),
     "hodlr_ctx_set_memory_limit": (C.c_int, [_VP, C.c_size_t]),
     "hodlr_ctx_memory_used": (C.c_int, [_VP, C.POINTER(C.c_size_t)]),
+    "hodlr_ctx_set_memory_pool": (C.c_int, [_VP, C.c_size_t]),
+    "hodlr_ctx_share_memory": (C.c_int, [_VP, _VP]),
     "hodlr_device_bytes": (C.c_int, [_VP, C.POINTER(C.c_size_t)]),
     "hodlr_footprint": (C.c_int, [C.c_int, C.c_int, _PI, C.c_int, C.c_int, C.c_int, C.c_int,
                                   C.POINTER(C.c_size_t)]),
@@ -148,6 +151,9 @@ class Context:
     def cluster(self, size: int):
         check(lib().hodlr_ctx_set_cluster(self.h, int(size)), "hodlr_ctx_set_cluster")
 
+    def set_cluster_large(self, size: int):
+        check(lib().hodlr_ctx_set_cluster_large(self.h, int(size)), "hodlr_ctx_set_cluster_large")
+
     @property
     def concurrency(self) -> int:
         v = C.c_int()
@@ -166,6 +172,12 @@ class Context:
 
     def set_memory_limit(self, nbytes: int):
         check(lib().hodlr_ctx_set_memory_limit(self.h, int(nbytes)), "hodlr_ctx_set_memory_limit")
+
+    def set_memory_pool(self, nbytes: int):
+        check(lib().hodlr_ctx_set_memory_pool(self.h, int(nbytes)), "hodlr_ctx_set_memory_pool")
+
+    def share_memory(self, other: "Context"):
+        check(lib().hodlr_ctx_share_memory(self.h, other.h), "hodlr_ctx_share_memory")
 
     def memory_used(self) -> int:
         v = C.c_size_t()

@@ -194,8 +194,12 @@ cudaError_t launch_panel_scatter(const PanelDesc* h, int n, PanelDesc* d, cudaSt
 // (their register use, ~126 per thread at 256 threads, allows no more), each with up to 18 KB
 // of static shared memory, out of the SM's 228 KB.
 constexpr size_t kClusterSmemShared = 92 * 1024;
-cudaError_t launch_qr(const QRDesc* h, int n, QRDesc* d, int cluster, size_t smem_cap, cudaStream_t s);
-cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, int cluster, size_t smem_cap, cudaStream_t s);
+// cluster_large (<= the device maximum): the cluster size for problems whose capacity does not
+// fit the shared memory of `cluster` CTAs (0: no growth).
+cudaError_t launch_qr(const QRDesc* h, int n, QRDesc* d, int cluster, size_t smem_cap, cudaStream_t s,
+                      int cluster_large = 0);
+cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, int cluster, size_t smem_cap, cudaStream_t s,
+                          int cluster_large = 0);
 cudaError_t launch_select(const SelectDesc* h, int n, SelectDesc* d, cudaStream_t s);
 cudaError_t launch_copy(const CopyDesc* h, int n, CopyDesc* d, cudaStream_t s);
 // fills and identities (kinds 0-2) of one record; norms (kind 3) of one record

@@ -1019,7 +1019,8 @@ int qr_max_cluster() {
   return v;
 }
 
-cudaError_t launch_qr(const QRDesc* h, int n, QRDesc* d, int cluster, size_t smem_cap, cudaStream_t s) {
+cudaError_t launch_qr(const QRDesc* h, int n, QRDesc* d, int cluster, size_t smem_cap, cudaStream_t s,
+                      int cluster_large) {
   if (n <= 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cluster, n, 1);
@@ -1038,9 +1039,18 @@ cudaError_t launch_qr(const QRDesc* h, int n, QRDesc* d, int cluster, size_t sme
     hcap = max(hcap, h[i].h);
     wcap = max(wcap, h[i].w);
   }
+  // A matrix whose columns fit neither the cluster's shared memory nor, as one panel, a CTA's
+  // (a tall truncation or left-orthogonalization input) would take the level-2 global-memory
+  // form: it is large by nature, so it gets the context's cluster size for large problems.
+  const size_t cap = std::min(kQRSmemMax, smem_cap);
+  if (cluster_large > cluster && qr_dsmem_bytes(hcap, wcap, cluster) > cap && qr_blocked_bytes(hcap) > cap) {
+    cluster = cluster_large;
+    cfg.gridDim = dim3(cluster, n, 1);
+    attr[0].val.clusterDim.x = cluster;
+  }
   // shared memory for the capacities, up to the per-CTA limit; the kernel picks its form from
   // the actual sizes
-  const size_t smem = std::min(qr_dsmem_bytes(hcap, wcap, cluster), std::min(kQRSmemMax, smem_cap));
+  const size_t smem = std::min(qr_dsmem_bytes(hcap, wcap, cluster), cap);
   cfg.dynamicSmemBytes = smem;
   // matrices of at most this many columns are factored by one CTA of the cluster (the others
   // exit at once): no cluster barrier per column; more of them while other factorizations
@@ -1735,7 +1745,7 @@ __global__ void __launch_bounds__(QT, 2) jacobi_dsmem_kernel(const JacobiDesc* _
 
 
 cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, int cluster, size_t smem_cap,
-                          cudaStream_t s) {
+                          cudaStream_t s, int cluster_large) {
   if (n <= 0) return cudaSuccess;
   const int cluster_max = cluster;
   int q1cap = 0, q2cap = 0;
@@ -1751,7 +1761,12 @@ cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, int cluster
   const int ppw = q1cap <= 4 * kJacobiRegs ? 8 : (q1cap <= 8 * kJacobiRegs ? 4 : (q1cap <= 16 * kJacobiRegs ? 2 : 1));
   const int pairs = (q2cap + 1) / 2;
   cluster = max(1, min(cluster, (pairs + 2 * ppw - 1) / (2 * ppw)));
-  while (cluster < cluster_max && jacobi_dsmem_bytes(q1cap, q2cap, cluster) > kJacobiSmemMax) ++cluster;
+  // a core whose columns do not fit the context's cluster in distributed shared memory grows
+  // the cluster, up to the context's size for large problems, instead of falling back to the
+  // global-memory form; small actual cores still run on one CTA of it (the others exit)
+  const size_t jcap = std::min(kJacobiSmemMax, smem_cap);
+  const int jmax = std::max(cluster_max, cluster_large);
+  while (cluster < jmax && jacobi_dsmem_bytes(q1cap, q2cap, cluster) > jcap) ++cluster;
   const size_t smem = jacobi_dsmem_bytes(q1cap, q2cap, cluster);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cluster, n, 1);

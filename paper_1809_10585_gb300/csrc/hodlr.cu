@@ -12,6 +12,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -29,6 +31,8 @@ namespace hq {
 cudaStream_t ctx_stream(hodlr_ctx* ctx);
 int ctx_cluster(hodlr_ctx* ctx);
 int ctx_device(hodlr_ctx* ctx);
+void* ctx_alloc(hodlr_ctx* ctx, size_t bytes);
+void ctx_free(hodlr_ctx* ctx, void* p, size_t bytes);
 cudaError_t launch_gemm_reduce(const GemmDesc* d, const int* rd, int nred, int nblocks, cudaStream_t s);
 }
 
@@ -36,9 +40,58 @@ cudaError_t launch_gemm_reduce(const GemmDesc* d, const int* rd, int nred, int n
 // Device bytes held through one context (its matrices with their plans, arenas and snapshots),
 // against an optional limit set by the caller.  Matrices keep the account alive, so freeing a
 // matrix after its context is destroyed stays correct.
+// A device memory pool reserved once (one cudaMalloc) and carved up on the host: first fit
+// over a free list ordered by offset, 256-byte granules, neighbours merged on release.  Taking
+// and returning memory makes no CUDA call, so it never synchronizes the device.
+struct DevPool {
+  char* base = nullptr;
+  size_t size = 0;
+  std::map<size_t, size_t> free_;               // offset -> bytes
+  std::map<size_t, size_t> used_;               // offset -> bytes
+  std::mutex mu;
+  void* take(size_t bytes) {
+    bytes = (bytes + 255) & ~size_t(255);
+    std::lock_guard<std::mutex> g(mu);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < bytes) continue;
+      const size_t off = it->first, rest = it->second - bytes;
+      free_.erase(it);
+      if (rest) free_[off + bytes] = rest;
+      used_[off] = bytes;
+      return base + off;
+    }
+    return nullptr;
+  }
+  void give(void* p) {
+    std::lock_guard<std::mutex> g(mu);
+    auto u = used_.find((size_t)((char*)p - base));
+    if (u == used_.end()) return;
+    size_t off = u->first, bytes = u->second;
+    used_.erase(u);
+    auto next = free_.lower_bound(off);
+    if (next != free_.end() && off + bytes == next->first) {
+      bytes += next->second;
+      next = free_.erase(next);
+    }
+    if (next != free_.begin()) {
+      auto prev = std::prev(next);
+      if (prev->first + prev->second == off) {
+        prev->second += bytes;
+        return;
+      }
+    }
+    free_[off] = bytes;
+  }
+  bool owns(void* p) const { return base && (char*)p >= base && (char*)p < base + size; }
+};
+
 struct MemAcct {
   std::atomic<long long> used{0};
   std::atomic<long long> limit{0};   // 0: no limit
+  std::shared_ptr<DevPool> pool;     // set: every allocation of the account comes from it
+  ~MemAcct() {
+    if (pool && pool->base) cudaFree(pool->base);
+  }
 };
 
 struct BatchGroup;
@@ -50,6 +103,7 @@ struct hodlr_ctx {
   cudaStream_t s = nullptr;
   cudaStream_t side = nullptr;   // second stream for work off the critical path
   int cluster = 8;
+  int cluster_large = 0;         // cluster size for problems that do not fit `cluster` (0: none)
   // stream pairs of batched factorizations (one pair per matrix of a batch)
   std::vector<std::pair<cudaStream_t, cudaStream_t>> pool;
   // CUDA graph of the last batched factorization captured with hodlr_qr_batched_graph
@@ -164,6 +218,12 @@ struct hodlr_mat {
   bool factored = false;
 };
 
+// Return device memory: to the account's pool (no CUDA call), else cudaFree.
+static void release_device(MemAcct* a, void* p) {
+  if (a && a->pool && a->pool->owns(p)) a->pool->give(p);
+  else cudaFree(p);
+}
+
 // Device allocation on behalf of matrix M, charged to its context's account.  HODLR_ENOMEM when
 // the account's limit would be exceeded or cudaMalloc fails (*p is then nullptr).
 static int mat_malloc(hodlr_mat* M, void** p, size_t bytes) {
@@ -178,7 +238,13 @@ static int mat_malloc(hodlr_mat* M, void** p, size_t bytes) {
       return HODLR_ENOMEM;
     }
   }
-  if (cudaMalloc(p, bytes) != cudaSuccess) {
+  if (a && a->pool) {
+    *p = a->pool->take(bytes);
+    if (!*p) {
+      a->used.fetch_sub((long long)bytes);
+      return HODLR_ENOMEM;
+    }
+  } else if (cudaMalloc(p, bytes) != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
     if (a) a->used.fetch_sub((long long)bytes);
@@ -203,9 +269,29 @@ static void mat_free(hodlr_mat* M, void* p) {
     b = it->second;
     M->allocs.erase(it);
   }
-  cudaFree(p);
+  release_device(M->mem.get(), p);
   M->held -= (long long)b;
   if (M->mem) M->mem->used.fetch_sub((long long)b);
+}
+
+// Device buffers outside any matrix (the server's right-hand sides), from the context's
+// account: its pool when it has one.
+void* hq::ctx_alloc(hodlr_ctx* ctx, size_t bytes) {
+  MemAcct* a = ctx->mem.get();
+  void* p = nullptr;
+  if (a->pool) {
+    p = a->pool->take(bytes);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) a->used.fetch_add((long long)((bytes + 255) & ~size_t(255)));
+  return p;
+}
+void hq::ctx_free(hodlr_ctx* ctx, void* p, size_t bytes) {
+  if (!p) return;
+  release_device(ctx->mem.get(), p);
+  ctx->mem->used.fetch_sub((long long)((bytes + 255) & ~size_t(255)));
 }
 
 cudaStream_t hq::ctx_stream(hodlr_ctx* ctx) { return ctx->s; }
@@ -1024,10 +1110,11 @@ static int run_plan_on(hodlr_ctx* ctx, hodlr_mat* M, Plan& P, Profiler* prof, cu
       case R_GATHER: e = launch_panel_gather((const PanelDesc*)hb, r.n, (PanelDesc*)dp, s); break;
       case R_SCATTER: e = launch_panel_scatter((const PanelDesc*)hb, r.n, (PanelDesc*)dp, s); break;
       case R_QR:
-        e = launch_qr((const QRDesc*)hb, r.n, (QRDesc*)dp, ctx->cluster, smem_cap(ctx), s);
+        e = launch_qr((const QRDesc*)hb, r.n, (QRDesc*)dp, ctx->cluster, smem_cap(ctx), s, ctx->cluster_large);
         break;
       case R_JACOBI:
-        e = launch_jacobi((const JacobiDesc*)hb, r.n, (JacobiDesc*)dp, ctx->cluster, smem_cap(ctx), s);
+        e = launch_jacobi((const JacobiDesc*)hb, r.n, (JacobiDesc*)dp, ctx->cluster, smem_cap(ctx), s,
+                          ctx->cluster_large);
         break;
       case R_SELECT: e = launch_select((const SelectDesc*)hb, r.n, (SelectDesc*)dp, s); break;
       case R_COPY: e = launch_copy((const CopyDesc*)hb, r.n, (CopyDesc*)dp, s); break;
@@ -1252,6 +1339,14 @@ int hodlr_ctx_set_cluster(hodlr_ctx* ctx, int cluster) {
   return HODLR_OK;
 }
 
+int hodlr_ctx_set_cluster_large(hodlr_ctx* ctx, int cluster) {
+  if (!ctx) return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  if (cluster < 0 || cluster > qr_max_cluster()) return HODLR_EINVAL;
+  ctx->cluster_large = cluster;
+  return HODLR_OK;
+}
+
 int hodlr_ctx_get_cluster(hodlr_ctx* ctx, int* cluster) {
   if (!ctx || !cluster) return HODLR_EINVAL;
   *cluster = ctx->cluster;
@@ -1345,7 +1440,7 @@ void hodlr_free(hodlr_mat* M) {
   if (M->gexec) cudaGraphExecDestroy(M->gexec);
   free_plan(M, M->plan);
   free_plan(M, M->splan);
-  for (auto& kv : M->allocs) cudaFree(kv.first);   // storage, tables, snapshot, arenas, buffers
+  for (auto& kv : M->allocs) release_device(M->mem.get(), kv.first);   // storage, tables, arenas, buffers
   if (M->mem) M->mem->used.fetch_sub(M->held);
   M->allocs.clear();
   delete M;
@@ -1570,7 +1665,7 @@ int hodlr_qr_graph(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm) {
   HQ_CUDA_OK(cudaSetDevice(ctx->dev));
   int rc = ensure_plan(ctx, A, tol, anorm);
   if (rc) return rc;
-  if (!A->gexec || A->g_tol != tol || A->g_anorm != anorm || A->g_cluster != ctx->cluster ||
+  if (!A->gexec || A->g_tol != tol || A->g_anorm != anorm || A->g_cluster != ctx->cluster * 64 + ctx->cluster_large ||
       A->g_conc != ctx->concurrency) {
     if (A->gexec) cudaGraphExecDestroy(A->gexec);
     A->gexec = nullptr;
@@ -1586,7 +1681,7 @@ int hodlr_qr_graph(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm) {
     if (e != cudaSuccess) return cuda_fail(e, __FILE__, __LINE__);
     A->g_tol = tol;
     A->g_anorm = anorm;
-    A->g_cluster = ctx->cluster;
+    A->g_cluster = ctx->cluster * 64 + ctx->cluster_large;
     A->g_conc = ctx->concurrency;
   }
   HQ_CUDA_OK(cudaGraphLaunch(A->gexec, ctx->s));
@@ -1887,7 +1982,8 @@ int hodlr_qr_batched_graph(hodlr_ctx* ctx, int count, hodlr_mat* const* A, doubl
   if (rc) return rc;
   std::vector<hodlr_mat*> key(A, A + count);
   if (!ctx->bgraph || replan || key != ctx->bmats || ctx->btol != tol || ctx->banorm != anorm ||
-      ctx->bcluster != ctx->cluster || ctx->bconc != ctx->concurrency || ctx->bgroup != ctx->batch_group) {
+      ctx->bcluster != ctx->cluster * 64 + ctx->cluster_large || ctx->bconc != ctx->concurrency ||
+      ctx->bgroup != ctx->batch_group) {
     if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
     ctx->bgraph = nullptr;
     BatchSetup b;
@@ -1904,7 +2000,7 @@ int hodlr_qr_batched_graph(hodlr_ctx* ctx, int count, hodlr_mat* const* A, doubl
     ctx->bmats = key;
     ctx->btol = tol;
     ctx->banorm = anorm;
-    ctx->bcluster = ctx->cluster;
+    ctx->bcluster = ctx->cluster * 64 + ctx->cluster_large;
     ctx->bconc = ctx->concurrency;
     ctx->bgroup = ctx->batch_group;
   }
@@ -2306,7 +2402,7 @@ int hodlr_truncate(hodlr_ctx* ctx, int nL, int nR, int K, const double* L, const
     else if (st == HODLR_ERANK) rc = HODLR_ERANK;
   }
   free_plan(&M, P);
-  for (auto& kv : M.allocs) cudaFree(kv.first);    // tables and arenas of the shell
+  for (auto& kv : M.allocs) release_device(M.mem.get(), kv.first);    // tables and arenas of the shell
   if (M.mem) M.mem->used.fetch_sub(M.held);
   M.allocs.clear();
   return rc;
@@ -2336,6 +2432,28 @@ int hodlr_build_dense(hodlr_ctx* ctx, int n, int nleaf, const int* leaf_sizes, c
 int hodlr_ctx_set_memory_limit(hodlr_ctx* ctx, size_t bytes) {
   if (!ctx) return HODLR_EINVAL;
   ctx->mem->limit.store((long long)bytes);
+  return HODLR_OK;
+}
+
+int hodlr_ctx_set_memory_pool(hodlr_ctx* ctx, size_t bytes) {
+  if (!ctx || bytes == 0) return HODLR_EINVAL;
+  if (ctx->mem->pool || ctx->mem->used.load() != 0) return HODLR_ESTATE;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  auto pool = std::make_shared<DevPool>();
+  pool->size = (bytes + 255) & ~size_t(255);
+  if (cudaMalloc(&pool->base, pool->size) != cudaSuccess) {
+    cudaGetLastError();
+    return HODLR_ENOMEM;
+  }
+  pool->free_[0] = pool->size;
+  ctx->mem->pool = pool;
+  return HODLR_OK;
+}
+
+int hodlr_ctx_share_memory(hodlr_ctx* ctx, hodlr_ctx* from) {
+  if (!ctx || !from || ctx->dev != from->dev) return HODLR_EINVAL;
+  if (ctx->mem->used.load() != 0) return HODLR_ESTATE;
+  ctx->mem = from->mem;
   return HODLR_OK;
 }
 

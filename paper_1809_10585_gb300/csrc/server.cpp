@@ -17,6 +17,8 @@
 
 namespace hq {
 cudaStream_t ctx_stream(hodlr_ctx* ctx);
+void* ctx_alloc(hodlr_ctx* ctx, size_t bytes);
+void ctx_free(hodlr_ctx* ctx, void* p, size_t bytes);
 }
 
 namespace {
@@ -54,40 +56,21 @@ struct hodlr_server {
   std::map<long long, Job> jobs;
   std::map<long long, hodlr_mat*> resident;     // key -> factored matrix
   std::vector<long long> slot_job;              // slot -> running request id (-1: free)
-  // Right-hand-side buffers, one per slot, grown on demand and reused: cudaFree waits for the
-  // whole device, so nothing is freed while requests run.  Matrices released while others run
-  // (finished factorizations that are not kept, evicted factors) wait in `retired` until no
-  // request is on the device.
+  // All device memory of the server (matrices, plans, scratch, right-hand sides) comes from one
+  // pool reserved at creation and shared by the slots' contexts: cudaMalloc and cudaFree wait
+  // for the whole device, and would serialize the requests.  Right-hand-side buffers, one per
+  // slot, grow on demand and are reused.
   std::vector<double*> slot_buf;
   std::vector<size_t> slot_buf_doubles;
-  std::vector<hodlr_mat*> retired;
   size_t budget = 0;
 };
 
 namespace {
 
-// Free retired matrices once nothing runs on the device (their cudaFree would otherwise wait
-// for every running request).
-void release_retired(hodlr_server* S) {
-  if (S->retired.empty()) return;
-  bool idle = true;
-  for (long long id : S->slot_job) idle = idle && id < 0;
-  // under continuous load the device is never idle: past a quarter of the budget, free anyway
-  size_t bytes = 0;
-  for (auto* M : S->retired) {
-    size_t b = 0;
-    hodlr_device_bytes(M, &b);
-    bytes += b;
-  }
-  if (!idle && bytes <= S->budget / 4) return;
-  for (auto* M : S->retired) hodlr_free(M);
-  S->retired.clear();
-}
-
 void evict(hodlr_server* S, long long key) {
   auto it = S->resident.find(key);
   if (it == S->resident.end()) return;
-  S->retired.push_back(it->second);
+  hodlr_free(it->second);                          // back to the pool; nothing waits
   S->resident.erase(it);
 }
 
@@ -122,17 +105,11 @@ int start(hodlr_server* S, const hq::ServeScheduler::Request& r) {
   }
   const size_t nb = (size_t)j.n * j.nrhs;
   if (!rc && S->slot_buf_doubles[r.slot] < nb) {
-    // growing the slot's buffer frees the old one: only here, and the old one is idle
-    if (S->slot_buf[r.slot]) cudaFree(S->slot_buf[r.slot]);
-    S->slot_buf[r.slot] = nullptr;
-    S->slot_buf_doubles[r.slot] = 0;
-    if (cudaMalloc(&S->slot_buf[r.slot], sizeof(double) * nb) != cudaSuccess) {
-      cudaGetLastError();
-      S->slot_buf[r.slot] = nullptr;
-      rc = HODLR_ENOMEM;
-    } else {
-      S->slot_buf_doubles[r.slot] = nb;
-    }
+    // the slot's buffer grows (its old contents are not needed: the slot is idle)
+    hq::ctx_free(ctx, S->slot_buf[r.slot], sizeof(double) * S->slot_buf_doubles[r.slot]);
+    S->slot_buf[r.slot] = static_cast<double*>(hq::ctx_alloc(ctx, sizeof(double) * nb));
+    S->slot_buf_doubles[r.slot] = S->slot_buf[r.slot] ? nb : 0;
+    if (!S->slot_buf[r.slot]) rc = HODLR_ENOMEM;
   }
   j.dB = rc ? nullptr : S->slot_buf[r.slot];
   if (!rc && cudaMemcpyAsync(j.dB, j.B.data(), sizeof(double) * (size_t)j.n * j.nrhs, cudaMemcpyHostToDevice,
@@ -142,7 +119,7 @@ int start(hodlr_server* S, const hq::ServeScheduler::Request& r) {
   if (rc) {
     cudaStreamSynchronize(st);
     j.dB = nullptr;
-    if (r.kind == hq::ServeScheduler::kFactor && M) S->retired.push_back(M);
+    if (r.kind == hq::ServeScheduler::kFactor && M) hodlr_free(M);
     return rc;
   }
   j.M = M;
@@ -184,7 +161,7 @@ int progress(hodlr_server* S) {
         S->sched->finish(id, 0, held, ev);           // may evict older factors under the key
         S->resident[r->key] = j.M;
       } else {
-        S->retired.push_back(j.M);
+        hodlr_free(j.M);                              // back to the pool; nothing waits
         S->sched->finish(id, err, 0, ev);
       }
     } else {
@@ -196,7 +173,6 @@ int progress(hodlr_server* S) {
     }
     j.M = nullptr;
   }
-  release_retired(S);
   S->sched->admit([S](const hq::ServeScheduler::Request& r) { return start(S, r); }, ev);
   return HODLR_OK;
 }
@@ -216,6 +192,9 @@ int hodlr_server_create(int device, int slots, size_t hbm_budget, int rank_cap, 
     hodlr_ctx* c = nullptr;
     int rc = hodlr_ctx_create(device, &c);
     if (!rc) rc = hodlr_ctx_set_concurrency(c, slots);   // factorizations share the SMs
+    // one pool for all slots: the budget plus an eighth for fragmentation
+    if (!rc) rc = s == 0 ? hodlr_ctx_set_memory_pool(c, hbm_budget + hbm_budget / 8)
+                         : hodlr_ctx_share_memory(c, S->slots[0]);
     if (rc) {
       if (c) hodlr_ctx_destroy(c);
       hodlr_server_destroy(S);
@@ -242,9 +221,8 @@ void hodlr_server_destroy(hodlr_server* S) {
   for (auto& kv : S->jobs)
     if (kv.second.M && kv.second.kind == 0) hodlr_free(kv.second.M);
   for (auto& kv : S->resident) hodlr_free(kv.second);
-  for (auto* M : S->retired) hodlr_free(M);
-  for (auto* p : S->slot_buf)
-    if (p) cudaFree(p);
+  for (size_t s = 0; s < S->slot_buf.size(); ++s)
+    hq::ctx_free(S->slots[0], S->slot_buf[s], sizeof(double) * S->slot_buf_doubles[s]);
   for (auto* c : S->slots) hodlr_ctx_destroy(c);
   delete S->sched;
   delete S;

@@ -63,3 +63,40 @@ def test_batched_graph_of_bench_workload_matches_oracle():
             assert (dg - dgo).abs().max().item() <= 1e3 * TOL * an
     finally:
         c.cluster = cmax
+
+
+def test_sample_of_batch_family_matches_oracle():
+    """A sample of the 256-matrix batch family (n log-uniform, nmin 128 or 256, ranks 5-20,
+    every second matrix column-scaled to condition ~1e10), factored together as the batch bench
+    does (uploaded into device matrices, one batched call, merged schedules per partition, rank
+    capacity 256), each against the oracle's hQR of the same input: 2-norm errors within 10x of
+    the oracle's, the Frobenius errors at most 100 tol, and the diagonal of R."""
+    import workloads as W
+    fam = W.batched_family(count=64, seed0=0, n_lo=2048, n_hi=4096)
+    inps = [x for x in fam if x.n <= 4096][:5]
+    c = U.ctx()
+    cmax = c.cluster
+    c.cluster = min(cmax, BENCH_CLUSTER)
+    c.set_batch_group(4)
+    try:
+        mats = [B.Matrix(c, x, rank_cap=256) for x in inps]
+        B.qr_batched(c, mats, TOL, 0.0)
+        c.sync()
+        for inp, M in zip(inps, mats):
+            st, anorm = M.status()
+            assert st == 0
+            res = O.hqr(O.from_input(inp), TOL)
+            assert abs(anorm - res.anorm) <= 1e-10 * res.anorm
+            A = torch.from_numpy(W.to_dense(inp)).cuda()
+            an = U.norm2(A)
+            (eo, ea), (eoF, eaF) = U.errors_both(*U.factors_dense(M), A)
+            Yo, To, Ro = (torch.from_numpy(x).cuda() for x in (res.Y_dense(), res.T_dense(), res.R_dense()))
+            (eoo, eao), _ = U.errors_both(Yo, To, Ro, A)
+            floor = 1e-14 * np.sqrt(inp.n)
+            assert eoF <= 100 * TOL and eaF / an <= 100 * TOL, (inp.name, eoF, eaF / an)
+            assert eo <= 10 * eoo + floor and ea <= 10 * eao + floor * an, (inp.name, eo, eoo, ea, eao)
+            R = U.dense_of(M, 2).T
+            assert (torch.diagonal(R).abs() - torch.diagonal(Ro).abs()).abs().max().item() <= 1e3 * TOL * an
+    finally:
+        c.cluster = cmax
+        c.set_batch_group(0)

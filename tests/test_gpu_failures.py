@@ -117,3 +117,45 @@ def test_zero_column_gives_singular_solve():
     b = torch.randn(1, inp.n, dtype=torch.float64, device="cuda")
     rc = M.solve(1, b.data_ptr(), inp.n)
     assert rc == B.HODLR_ESINGULAR
+
+
+def test_memory_pool_serves_allocations_and_rejects_overflow():
+    """A context with a device memory pool takes every allocation of its matrices from the pool
+    (no cudaMalloc/cudaFree while matrices come and go): results equal those of a context
+    without a pool, the account returns to zero when the matrices are freed, a second context
+    sharing the pool draws from the same account, and a matrix larger than the pool fails with
+    HODLR_ENOMEM."""
+    inp = W.random_hodlr(2048, 256, 8, seed=7)
+    need = B.footprint(2048, inp.leaf_sizes, 64, estimate_norm=True)
+    ref = U.gpu_qr(inp, 1e-10, anorm=0.0, rank_cap=64)
+    Rref = U.dense_of(ref, 2).cpu().numpy()
+    ctx = _fresh_ctx()
+    ctx2 = B.Context(0)
+    try:
+        ctx.set_memory_pool(int(6 * need))
+        ctx2.share_memory(ctx)
+        with pytest.raises(B.HodlrError) as e:
+            ctx.set_memory_pool(need)                  # already has one
+        assert e.value.code == B.HODLR_ESTATE
+        for rep in range(3):                           # memory is reused across matrices
+            M = B.Matrix(ctx, inp, rank_cap=64)
+            M2 = B.Matrix(ctx2, inp, rank_cap=64)
+            M.qr(1e-10)
+            M2.qr(1e-10)
+            ctx.sync()
+            ctx2.sync()
+            assert ctx.memory_used() == 2 * need and ctx2.memory_used() == 2 * need
+            for X in (M, M2):
+                R = U.dense_of(X, 2).cpu().numpy()
+                np.testing.assert_allclose(R, Rref, rtol=0, atol=1e-12 * np.abs(Rref).max())
+            M.free()
+            M2.free()
+            assert ctx.memory_used() == 0
+        big = W.random_hodlr(8192, 256, 10, seed=8)
+        with pytest.raises(B.HodlrError) as e:
+            X = B.Matrix(ctx, big, rank_cap=128)
+            X.qr(1e-10)
+        assert e.value.code == B.HODLR_ENOMEM
+    finally:
+        ctx2.close()
+        ctx.close()
