@@ -278,11 +278,19 @@ def gpu_arm(args):
     cmax = ctx.cluster
     ccl = args.cluster if args.cluster > 0 else (cmax if nb == 1 else min(cmax, BATCH_CLUSTER))
     ctx.cluster = ccl
+    if args.cluster_large > 0:
+        ctx.set_cluster_large(args.cluster_large)
     ctx.set_batch_group(args.group)
     mats = [B.Matrix(ctx, x, rank_cap=args.rank_cap) for x in inps]
     M = mats[0]
     for m in mats:
         m.snapshot()
+    tuned = None
+    if nb > 1 and args.cluster <= 0 and args.group_given is False:
+        # launch shapes (cluster size, merged group size) chosen by timing this batch on this GPU
+        with torch.cuda.stream(stream):
+            tuned = B.autotune_batched(ctx, mats, TOL, 0.0, reps=2)
+        ccl = ctx.cluster
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def factor_all():
@@ -429,7 +437,8 @@ def gpu_arm(args):
                                    for k, v in prof.items()}}}
     # matrices of one structure share one merged schedule: a step launches one factorization's
     # kernels per group (each launch carrying the descriptors of every matrix of the group)
-    groups = 1 if nb == 1 else (-(-nb // args.group) if args.group > 0 else 1)
+    grp = tuned["group"] if tuned else args.group
+    groups = 1 if nb == 1 else (-(-nb // grp) if grp > 0 else 1)
     gpu_launches = sum(v["launches"] for v in prof.values()) * args.steps * groups
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -437,7 +446,9 @@ def gpu_arm(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N, "nmin": NMIN, "rank": K, "col_scale_decades": DECADES,
                        "tol": TOL, "rank_cap": args.rank_cap, "batch": nb, "cluster": ccl,
-                       "group": args.group,
+                       "group": tuned["group"] if tuned else args.group,
+                       "launch_shapes": "autotuned (hodlr_autotune_batched: cluster x group, best of 2 timed graphs "
+                                        "each)" if tuned else "given",
                        "batching": "independent seeded matrices of the workload factored together: one merged "
                                    "launch schedule per group of matrices (each launch carries every matrix's "
                                    "descriptors), one CUDA graph per step",
@@ -490,7 +501,9 @@ def batch256_arm(args):
     ctx = B.Context(local)
     stream = torch.cuda.Stream()
     ctx.set_stream(stream.cuda_stream)
-    ctx.cluster = min(ctx.cluster, BATCH_CLUSTER) if args.cluster <= 0 else args.cluster
+    cmax = ctx.cluster
+    ctx.cluster = min(cmax, BATCH_CLUSTER) if args.cluster <= 0 else args.cluster
+    ctx.set_cluster_large(cmax if args.cluster_large < 0 else args.cluster_large)
     ctx.set_batch_group(args.group)
     key = lambda x: (x.n, tuple(x.leaf_sizes))
     wave_idx = [[i for i in range(count) if i % waves == w] for w in range(waves)]
@@ -578,6 +591,7 @@ def batch256_arm(args):
                        "matrices": count, "waves": waves, "device_matrices": sum(need.values()),
                        "n_min": min(x.n for x in inps), "n_max": max(x.n for x in inps),
                        "n_total": sum(x.n for x in inps), "rank_cap": kc, "cluster": ctx.cluster,
+                       "cluster_large": cmax if args.cluster_large < 0 else args.cluster_large,
                        "group": args.group, "tol": TOL,
                        "l2": "inputs larger than L2 (each wave re-uploads its matrices before its timed region)",
                        "device_bytes": mem, "host_generation_s": t_gen},
@@ -816,6 +830,9 @@ def main():
                     help="most matrices per merged launch schedule (0: no limit; default: 1 for the n = 8192 "
                          "workload, 4 for the 256-matrix batch)")
     ap.add_argument("--waves", type=int, default=2, help="waves per step of the 256-matrix batch")
+    ap.add_argument("--cluster-large", type=int, default=-1,
+                    help="cluster size for QRs / Jacobi cores that do not fit the cluster's shared memory "
+                         "(0: none; default: none for the n = 8192 workload, the device maximum otherwise)")
     ap.add_argument("--served-requests", type=int, default=24, help="requests per rate of the served sweep")
     ap.add_argument("--served-rates", default="0.5,2,8,32", help="arrival rates (requests/s) of the served sweep")
     ap.add_argument("--served-pool", type=int, default=12, help="distinct matrices the served sweep draws from")
@@ -827,6 +844,7 @@ def main():
     ap.add_argument("--cluster", type=int, default=0,
                     help="CTAs per thread-block cluster of the QR/Jacobi kernels (0: automatic)")
     args = ap.parse_args()
+    args.group_given = args.group >= 0
     if args.group < 0:
         args.group = 4 if args.workload == "batch256" else 1
     if args.impl == "reference":

@@ -192,6 +192,19 @@ int hodlr_qr_profile(hodlr_ctx* ctx, hodlr_mat* A, double tol, double anorm, dou
 int hodlr_qr_batched(hodlr_ctx* ctx, int count, hodlr_mat* const* A, double tol, double anorm);
 int hodlr_qr_batched_graph(hodlr_ctx* ctx, int count, hodlr_mat* const* A, double tol, double anorm);
 
+/*
+ * hodlr_autotune_batched — choose the launch shapes of a batch by measurement: for each cluster
+ * size of the QR and Jacobi kernels in {2, 3, 4, 8, device maximum} and each batch group size in
+ * {1, 4} (merged schedules, hodlr_ctx_set_batch_group), hodlr_qr_batched_graph of the given
+ * matrices is recorded and timed `reps` times with CUDA events on the context's stream; the
+ * fastest pair is kept on the context and returned (*best_ms: its best time per batch).  The
+ * matrices need snapshots (each timed run restores them first); they end up factored.  The
+ * choice depends on the workload (sizes, ranks, how many matrices) and on the GPU, and results
+ * depend on it at the level of rounding only.  Synchronous.  Not in the paper.
+ */
+int hodlr_autotune_batched(hodlr_ctx* ctx, int count, hodlr_mat* const* A, double tol, double anorm, int reps,
+                           int* best_cluster, int* best_group, double* best_ms);
+
 /* Synchronize and return the status word of the last factorization in *status, and the
  * ||A||_2 used for the thresholds eps ||A||_2 of Alg. 2 (S~ and the update of the second block
  * column) in *anorm_used (either may be NULL).  The status is HODLR_OK, or HODLR_ERANK when a

@@ -55,6 +55,7 @@ _SIGS = {
     "hodlr_qr_batched": (C.c_int, [_VP, C.c_int, C.POINTER(_VP), C.c_double, C.c_double]),
     "hodlr_qr_batched_graph": (C.c_int, [_VP, C.c_int, C.POINTER(_VP), C.c_double, C.c_double]),
     "hodlr_qr_profile": (C.c_int, [_VP, _VP, C.c_double, C.c_double, _PD, _PI, _PD]),
+    "hodlr_autotune_batched": (C.c_int, [_VP, C.c_int, C.POINTER(_VP), C.c_double, C.c_double, C.c_int, _PI, _PI, _PD]),
     "hodlr_status": (C.c_int, [_VP, _VP, _PI, _PD]),
     "hodlr_ranks": (C.c_int, [_VP, _VP, _PI, _PI, _PI]),
     "hodlr_flops": (C.c_int, [_VP, _VP, _PD]),
@@ -353,6 +354,15 @@ def qr_batched(ctx: Context, mats, tol: float, anorm: float = 0.0, graph: bool =
     arr = (_VP * len(mats))(*[m.h for m in mats])
     fn = lib().hodlr_qr_batched_graph if graph else lib().hodlr_qr_batched
     check(fn(ctx.h, len(mats), arr, tol, anorm), "hodlr_qr_batched")
+
+
+def autotune_batched(ctx: Context, mats, tol: float, anorm: float = 0.0, reps: int = 2):
+    """Pick the cluster size and batch group of the context by timing the batched graph."""
+    arr = (_VP * len(mats))(*[m.h for m in mats])
+    c, g, ms = C.c_int(), C.c_int(), C.c_double()
+    check(lib().hodlr_autotune_batched(ctx.h, len(mats), arr, tol, anorm, reps, C.byref(c), C.byref(g), C.byref(ms)),
+          "hodlr_autotune_batched")
+    return {"cluster": c.value, "group": g.value, "ms": ms.value}
 
 
 def dense_qr(ctx: Context, h, w, A_ptr, lda, T_ptr, ldt):

@@ -2009,6 +2009,58 @@ int hodlr_qr_batched_graph(hodlr_ctx* ctx, int count, hodlr_mat* const* A, doubl
   return HODLR_OK;
 }
 
+int hodlr_autotune_batched(hodlr_ctx* ctx, int count, hodlr_mat* const* A, double tol, double anorm, int reps,
+                           int* best_cluster, int* best_group, double* best_ms) {
+  if (!ctx || !A || count < 1 || reps < 1) return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  const int cmax = qr_max_cluster();
+  std::vector<int> clusters;
+  for (int c : {2, 3, 4, 8, cmax})
+    if (c <= cmax && std::find(clusters.begin(), clusters.end(), c) == clusters.end()) clusters.push_back(c);
+  std::vector<int> groups = {1, 4};
+  const int c0 = ctx->cluster, g0 = ctx->batch_group;
+  cudaEvent_t e0, e1;
+  HQ_CUDA_OK(cudaEventCreate(&e0));
+  HQ_CUDA_OK(cudaEventCreate(&e1));
+  double best = -1.0;
+  int bc = c0, bg = g0, rc = HODLR_OK;
+  for (int c : clusters) {
+    for (int g : groups) {
+      if (g > 1 && count < 2 * g) continue;
+      ctx->cluster = c;
+      ctx->batch_group = g;
+      rc = hodlr_qr_batched_graph(ctx, count, A, tol, anorm);     // records the graph
+      if (!rc && cudaStreamSynchronize(ctx->s) != cudaSuccess) rc = HODLR_ECUDA;
+      double mn = -1.0;
+      for (int r = 0; r < reps && !rc; ++r) {
+        cudaEventRecord(e0, ctx->s);
+        rc = hodlr_qr_batched_graph(ctx, count, A, tol, anorm);
+        cudaEventRecord(e1, ctx->s);
+        if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = HODLR_ECUDA;
+        float ms = 0.0f;
+        if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+        if (!rc && (mn < 0 || ms < mn)) mn = ms;
+      }
+      if (rc) break;
+      if (best < 0 || mn < best) {
+        best = mn;
+        bc = c;
+        bg = g;
+      }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->cluster = rc ? c0 : bc;
+  ctx->batch_group = rc ? g0 : bg;
+  if (rc) return rc;
+  if (best_cluster) *best_cluster = bc;
+  if (best_group) *best_group = bg;
+  if (best_ms) *best_ms = best;
+  return HODLR_OK;
+}
+
 int hodlr_status(hodlr_ctx* ctx, hodlr_mat* A, int* status, double* anorm_used) {
   if (!ctx || !A) return HODLR_EINVAL;
   HQ_CUDA_OK(cudaStreamSynchronize(ctx->s));

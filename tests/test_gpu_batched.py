@@ -110,3 +110,34 @@ def test_merged_groups_equal_alone_and_graph_replays(group):
             assert M.flops()["total"] > 0
     finally:
         c.set_batch_group(0)
+
+
+def test_autotuner_picks_a_valid_shape_and_results_follow():
+    """hodlr_autotune_batched times the batched graph for each (cluster size, batch group)
+    candidate and keeps the fastest on the context; afterwards the batch factors to the same
+    results as with the default shapes, to rounding."""
+    from paper_1809_10585_gb300 import binding as B
+    tol = 1e-12
+    inps = [W.random_hodlr(1024, 128, 5, seed=s, col_scale_decades=6.0 * (s % 2)) for s in range(4)]
+    c = B.Context(0)
+    try:
+        ref = []
+        for inp in inps:
+            M = B.Matrix(c, inp, rank_cap=64)
+            M.qr(tol)
+            ref.append(U.dense_of(M, 2).cpu().numpy())
+            M.free()
+        mats = [B.Matrix(c, inp, rank_cap=64) for inp in inps]
+        for M in mats:
+            M.snapshot()
+        best = B.autotune_batched(c, mats, tol, 0.0, reps=1)
+        assert best["cluster"] in (2, 3, 4, 8, 16) and best["group"] in (1, 4) and best["ms"] > 0
+        assert c.cluster == best["cluster"]
+        B.qr_batched(c, mats, tol, 0.0, graph=True)
+        c.sync()
+        for M, R0 in zip(mats, ref):
+            assert M.status()[0] == 0
+            R = U.dense_of(M, 2).cpu().numpy()
+            assert np.max(np.abs(R - R0)) <= 1e-9 * max(1.0, np.max(np.abs(R0)))
+    finally:
+        c.close()

@@ -131,8 +131,9 @@ def test_memory_pool_serves_allocations_and_rejects_overflow():
     Rref = U.dense_of(ref, 2).cpu().numpy()
     ctx = _fresh_ctx()
     ctx2 = B.Context(0)
+    small = B.Context(0)
     try:
-        ctx.set_memory_pool(int(6 * need))
+        ctx.set_memory_pool(2 << 30)                   # room for the dense copies below too
         ctx2.share_memory(ctx)
         with pytest.raises(B.HodlrError) as e:
             ctx.set_memory_pool(need)                  # already has one
@@ -151,11 +152,12 @@ def test_memory_pool_serves_allocations_and_rejects_overflow():
             M.free()
             M2.free()
             assert ctx.memory_used() == 0
-        big = W.random_hodlr(8192, 256, 10, seed=8)
+        small.set_memory_pool(need // 4)               # smaller than one factorization
         with pytest.raises(B.HodlrError) as e:
-            X = B.Matrix(ctx, big, rank_cap=128)
+            X = B.Matrix(small, inp, rank_cap=64)
             X.qr(1e-10)
         assert e.value.code == B.HODLR_ENOMEM
     finally:
+        small.close()
         ctx2.close()
         ctx.close()
