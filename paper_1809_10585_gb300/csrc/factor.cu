@@ -983,11 +983,10 @@ constexpr size_t kQRSmemMax = 200 * 1024;
 constexpr int kQRSoloCols = 32;
 
 // Largest cluster size both cluster kernels can be launched with (16 needs the non-portable
-// attribute and enough SMs per GPC), probed once per process; attributes are set here, never
-// during stream capture.
-int qr_max_cluster() {
-  static int cached = -1;
-  if (cached > 0) return cached;
+// attribute and enough SMs per GPC), probed once per process (thread-safe: the first caller
+// runs the probe, concurrent callers wait for it); attributes are set here, never during stream
+// capture.
+static int probe_max_cluster() {
   int v = 8;
   bool ok = cudaFuncSetAttribute(qr_dsmem_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
             cudaFuncSetAttribute(qr_dsmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQRSmemMax) == cudaSuccess &&
@@ -1015,8 +1014,12 @@ int qr_max_cluster() {
   cudaFuncSetAttribute(jacobi_dsmem_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaFuncSetAttribute(jacobi_dsmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kJacobiSmemMax);
   cudaGetLastError();
-  cached = v;
   return v;
+}
+
+int qr_max_cluster() {
+  static const int cached = probe_max_cluster();
+  return cached;
 }
 
 cudaError_t launch_qr(const QRDesc* h, int n, QRDesc* d, int cluster, size_t smem_cap, cudaStream_t s,

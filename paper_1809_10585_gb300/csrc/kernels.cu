@@ -296,14 +296,16 @@ __global__ void gemm_reduce_kernel(const GemmDesc* __restrict__ descs, const int
   *c = v;
 }
 
+// SM count of the device, queried once per process (thread-safe static initialisation).
 static int device_sms() {
-  static int sms = 0;
-  if (sms <= 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      sms = 152;
+  static const int sms = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        v <= 0)
+      v = 152;
     cudaGetLastError();
-  }
+    return v;
+  }();
   return sms;
 }
 

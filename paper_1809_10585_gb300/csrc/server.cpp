@@ -1,15 +1,21 @@
 // The continuously batched factorize/solve service behind hodlr_server_* (include/hodlr_qr.h).
-// Scheduling policy: serve_sched.h.  Every slot is a library context with its own streams, so
-// the work of requests admitted while others run overlaps on the device.  Admission charges a
-// request with its exact device footprint (hodlr_footprint: storage, plans and scratch of
-// build + factorization + solve) plus its right-hand sides.  Completion is polled without
-// blocking (hodlr_ready).  Host-side code only: all numerics run in the library's kernels.
+// Scheduling policy: serve_sched.h.  Every slot is a library context with its own streams and a
+// host worker thread that issues the slot's requests, so the work of requests admitted while
+// others run overlaps on the device: issuing a factorization of thousands of launches can block
+// the issuing thread until the device has drained most of them, and with one issuing thread the
+// requests would run one after another.  Admission charges a request with its exact device
+// footprint (hodlr_footprint: storage, plans and scratch of build + factorization + solve) plus
+// its right-hand sides.  The caller's thread only submits, admits and collects (never waits for
+// the device).  Host-side code only: all numerics run in the library's kernels.
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <condition_variable>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/hodlr_qr.h"
@@ -41,28 +47,38 @@ struct Job {
   std::vector<double> B, X;
   bool taken = false;            // the solution was handed out
   double t_submit = 0.0, t_done = 0.0;
-  // while on the device
-  hodlr_mat* M = nullptr;
-  double* dB = nullptr;
 };
 
 }  // namespace
 
+// One slot: a library context, its reusable right-hand-side buffer and the worker thread that
+// runs the slot's requests.  Fields below `th` are guarded by hodlr_server::mu.
+struct Slot {
+  hodlr_ctx* ctx = nullptr;
+  double* buf = nullptr;           // n x nrhs staging of right-hand sides, grown on demand
+  size_t buf_doubles = 0;
+  std::thread th;
+  int state = 0;                   // 0 idle, 1 request assigned, 2 request finished (rc valid)
+  long long id = -1;
+  Job* job = nullptr;
+  hodlr_mat* M = nullptr;          // solve: the resident factors; factorization: set by the worker
+  int rc = 0;
+};
+
 struct hodlr_server {
   int dev = 0;
   int rank_cap = 128;
-  std::vector<hodlr_ctx*> slots;
+  std::vector<Slot> slots;
   hq::ServeScheduler* sched = nullptr;
   std::map<long long, Job> jobs;
   std::map<long long, hodlr_mat*> resident;     // key -> factored matrix
-  std::vector<long long> slot_job;              // slot -> running request id (-1: free)
   // All device memory of the server (matrices, plans, scratch, right-hand sides) comes from one
   // pool reserved at creation and shared by the slots' contexts: cudaMalloc and cudaFree wait
-  // for the whole device, and would serialize the requests.  Right-hand-side buffers, one per
-  // slot, grow on demand and are reused.
-  std::vector<double*> slot_buf;
-  std::vector<size_t> slot_buf_doubles;
+  // for the whole device, and would serialize the requests.
   size_t budget = 0;
+  std::mutex mu;                   // API calls and the workers' hand-offs
+  std::condition_variable work;    // a slot was given a request, or the server is closing
+  bool quit = false;
 };
 
 namespace {
@@ -74,13 +90,16 @@ void evict(hodlr_server* S, long long key) {
   S->resident.erase(it);
 }
 
-int start(hodlr_server* S, const hq::ServeScheduler::Request& r) {
-  Job& j = S->jobs[r.id];
-  hodlr_ctx* ctx = S->slots[r.slot];
+// Run one request on slot `slot` (the slot's worker thread, without the server lock): build and
+// factor, or take the resident factors; stage the right-hand sides, solve, wait for the slot's
+// stream and copy the solution back.
+int run_request(hodlr_server* S, Slot& sl, Job& j, hodlr_mat** Mout) {
+  hodlr_ctx* ctx = sl.ctx;
   cudaStream_t st = hq::ctx_stream(ctx);
+  if (cudaSetDevice(S->dev) != cudaSuccess) return HODLR_ECUDA;
   int rc = HODLR_OK;
-  hodlr_mat* M = nullptr;
-  if (r.kind == hq::ServeScheduler::kFactor) {
+  hodlr_mat* M = *Mout;
+  if (j.kind == 0) {
     const int nleaf = (int)j.leaf_sizes.size(), nn = nleaf - 1;
     std::vector<const double*> lv(nleaf), u12(std::max(1, nn)), v12(std::max(1, nn)), u21(std::max(1, nn)),
         v21(std::max(1, nn));
@@ -95,73 +114,99 @@ int start(hodlr_server* S, const hq::ServeScheduler::Request& r) {
                      nn ? j.r12.data() : nullptr, u21.data(), v21.data(), nn ? j.r21.data() : nullptr,
                      S->rank_cap, &M);
     if (rc) return rc;
-    // the description is on the device now; keep only the right-hand sides
-    j.leaves.clear(); j.U12.clear(); j.V12.clear(); j.U21.clear(); j.V21.clear();
+    *Mout = M;
     rc = hodlr_qr(ctx, M, j.tol, 0.0);
-  } else {
+  }
+  const size_t nb = (size_t)j.n * j.nrhs;
+  if (!rc && sl.buf_doubles < nb) {
+    // the slot's buffer grows (its old contents are not needed: the slot is idle)
+    hq::ctx_free(ctx, sl.buf, sizeof(double) * sl.buf_doubles);
+    sl.buf = static_cast<double*>(hq::ctx_alloc(ctx, sizeof(double) * nb));
+    sl.buf_doubles = sl.buf ? nb : 0;
+    if (!sl.buf) rc = HODLR_ENOMEM;
+  }
+  if (!rc && cudaMemcpyAsync(sl.buf, j.B.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    rc = HODLR_ECUDA;
+  if (!rc) rc = hodlr_solve_async(ctx, M, j.nrhs, sl.buf, j.n);
+  if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = HODLR_ECUDA;
+  if (!rc && j.kind == 0) {
+    int status = 0;
+    rc = hodlr_status(ctx, M, &status, nullptr);
+    if (!rc && status) rc = status;
+  }
+  if (!rc) {
+    j.X.resize(nb);
+    if (cudaMemcpy(j.X.data(), sl.buf, sizeof(double) * nb, cudaMemcpyDeviceToHost) != cudaSuccess) rc = HODLR_ECUDA;
+  }
+  return rc;
+}
+
+void worker(hodlr_server* S, int slot) {
+  Slot& sl = S->slots[slot];
+  std::unique_lock<std::mutex> lk(S->mu);
+  for (;;) {
+    S->work.wait(lk, [&] { return S->quit || sl.state == 1; });
+    if (sl.state != 1) return;                    // closing, nothing assigned
+    Job* j = sl.job;
+    hodlr_mat* M = sl.M;
+    lk.unlock();
+    const int rc = run_request(S, sl, *j, &M);
+    const double t = now_s();
+    lk.lock();
+    j->t_done = t;
+    sl.M = M;
+    sl.rc = rc;
+    sl.state = 2;
+  }
+}
+
+// Hand an admitted request to its slot's worker (server lock held).
+int start(hodlr_server* S, const hq::ServeScheduler::Request& r) {
+  Slot& sl = S->slots[r.slot];
+  Job& j = S->jobs[r.id];
+  hodlr_mat* M = nullptr;
+  if (r.kind == hq::ServeScheduler::kSolve) {
     auto it = S->resident.find(r.key);
     if (it == S->resident.end()) return HODLR_ESTATE;
     M = it->second;
   }
-  const size_t nb = (size_t)j.n * j.nrhs;
-  if (!rc && S->slot_buf_doubles[r.slot] < nb) {
-    // the slot's buffer grows (its old contents are not needed: the slot is idle)
-    hq::ctx_free(ctx, S->slot_buf[r.slot], sizeof(double) * S->slot_buf_doubles[r.slot]);
-    S->slot_buf[r.slot] = static_cast<double*>(hq::ctx_alloc(ctx, sizeof(double) * nb));
-    S->slot_buf_doubles[r.slot] = S->slot_buf[r.slot] ? nb : 0;
-    if (!S->slot_buf[r.slot]) rc = HODLR_ENOMEM;
-  }
-  j.dB = rc ? nullptr : S->slot_buf[r.slot];
-  if (!rc && cudaMemcpyAsync(j.dB, j.B.data(), sizeof(double) * (size_t)j.n * j.nrhs, cudaMemcpyHostToDevice,
-                             st) != cudaSuccess)
-    rc = HODLR_ECUDA;
-  if (!rc) rc = hodlr_solve_async(ctx, M, j.nrhs, j.dB, j.n);
-  if (rc) {
-    cudaStreamSynchronize(st);
-    j.dB = nullptr;
-    if (r.kind == hq::ServeScheduler::kFactor && M) hodlr_free(M);
-    return rc;
-  }
-  j.M = M;
-  S->slot_job[r.slot] = r.id;
+  sl.id = r.id;
+  sl.job = &j;
+  sl.M = M;
+  sl.rc = 0;
+  sl.state = 1;
+  S->work.notify_all();
   return HODLR_OK;
 }
 
-// Complete finished requests (non-blocking), then admit waiting ones.
+// Complete the requests the workers finished, then admit waiting ones (server lock held; never
+// waits for the device).
 int progress(hodlr_server* S) {
   if (cudaSetDevice(S->dev) != cudaSuccess) return HODLR_ECUDA;
   auto ev = [S](long long key) { evict(S, key); };
-  for (size_t s = 0; s < S->slots.size(); ++s) {
-    const long long id = S->slot_job[s];
-    if (id < 0) continue;
-    int ready = 0;
-    int rc = hodlr_ready(S->slots[s], &ready);
-    if (!rc && !ready) continue;
+  for (Slot& sl : S->slots) {
+    if (sl.state != 2) continue;
+    const long long id = sl.id;
     Job& j = S->jobs[id];
     const hq::ServeScheduler::Request* r = S->sched->find(id);
-    int err = rc;
-    if (!err && r->kind == hq::ServeScheduler::kFactor) {
-      int st = 0;
-      err = hodlr_status(S->slots[s], j.M, &st, nullptr);
-      if (!err && st) err = st;
-    }
-    if (!err) {
-      j.X.resize((size_t)j.n * j.nrhs);
-      if (cudaMemcpy(j.X.data(), j.dB, sizeof(double) * j.X.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
-        err = HODLR_ECUDA;
-    }
-    j.dB = nullptr;                                  // the slot's buffer, kept for reuse
-    j.t_done = now_s();
+    const int err = sl.rc;
+    hodlr_mat* M = sl.M;
+    sl.state = 0;
+    sl.id = -1;
+    sl.job = nullptr;
+    sl.M = nullptr;
+    // the description was uploaded; keep only the solution
+    j.leaves.clear(); j.U12.clear(); j.V12.clear(); j.U21.clear(); j.V21.clear();
     j.B.clear();
-    S->slot_job[s] = -1;
+    if (err) j.X.clear();
     size_t held = 0;
     if (r->kind == hq::ServeScheduler::kFactor) {
       if (!err && r->key >= 0) {
-        hodlr_device_bytes(j.M, &held);
+        hodlr_device_bytes(M, &held);
         S->sched->finish(id, 0, held, ev);           // may evict older factors under the key
-        S->resident[r->key] = j.M;
+        S->resident[r->key] = M;
       } else {
-        hodlr_free(j.M);                              // back to the pool; nothing waits
+        if (M) hodlr_free(M);                         // back to the pool; the slot's stream is idle
         S->sched->finish(id, err, 0, ev);
       }
     } else {
@@ -171,7 +216,6 @@ int progress(hodlr_server* S) {
         S->sched->resize_resident(j.key, held);
       }
     }
-    j.M = nullptr;
   }
   S->sched->admit([S](const hq::ServeScheduler::Request& r) { return start(S, r); }, ev);
   return HODLR_OK;
@@ -188,25 +232,29 @@ int hodlr_server_create(int device, int slots, size_t hbm_budget, int rank_cap, 
   S->dev = device;
   S->rank_cap = rank_cap;
   S->budget = hbm_budget;
+  S->slots.resize(slots);                          // fixed from here on: workers hold references
   for (int s = 0; s < slots; ++s) {
     hodlr_ctx* c = nullptr;
     int rc = hodlr_ctx_create(device, &c);
     if (!rc) rc = hodlr_ctx_set_concurrency(c, slots);   // factorizations share the SMs
     // one pool for all slots: the budget plus an eighth for fragmentation
     if (!rc) rc = s == 0 ? hodlr_ctx_set_memory_pool(c, hbm_budget + hbm_budget / 8)
-                         : hodlr_ctx_share_memory(c, S->slots[0]);
+                         : hodlr_ctx_share_memory(c, S->slots[0].ctx);
     if (rc) {
       if (c) hodlr_ctx_destroy(c);
       hodlr_server_destroy(S);
       return rc;
     }
-    S->slots.push_back(c);
+    S->slots[s].ctx = c;
   }
-  S->slot_job.assign(slots, -1);
-  S->slot_buf.assign(slots, nullptr);
-  S->slot_buf_doubles.assign(slots, 0);
   S->sched = new (std::nothrow) hq::ServeScheduler(slots, hbm_budget);
   if (!S->sched) {
+    hodlr_server_destroy(S);
+    return HODLR_ENOMEM;
+  }
+  try {
+    for (int s = 0; s < slots; ++s) S->slots[s].th = std::thread(worker, S, s);
+  } catch (...) {
     hodlr_server_destroy(S);
     return HODLR_ENOMEM;
   }
@@ -216,14 +264,24 @@ int hodlr_server_create(int device, int slots, size_t hbm_budget, int rank_cap, 
 
 void hodlr_server_destroy(hodlr_server* S) {
   if (!S) return;
+  {
+    std::lock_guard<std::mutex> g(S->mu);
+    S->quit = true;                                // workers finish the request they hold, then stop
+  }
+  S->work.notify_all();
+  for (Slot& sl : S->slots)
+    if (sl.th.joinable()) sl.th.join();
   cudaSetDevice(S->dev);
-  for (auto* c : S->slots) hodlr_sync(c);
-  for (auto& kv : S->jobs)
-    if (kv.second.M && kv.second.kind == 0) hodlr_free(kv.second.M);
+  for (Slot& sl : S->slots) {
+    if (!sl.ctx) continue;
+    hodlr_sync(sl.ctx);
+    if (sl.M && sl.job && sl.job->kind == 0) hodlr_free(sl.M);   // finished, never collected
+  }
   for (auto& kv : S->resident) hodlr_free(kv.second);
-  for (size_t s = 0; s < S->slot_buf.size(); ++s)
-    hq::ctx_free(S->slots[0], S->slot_buf[s], sizeof(double) * S->slot_buf_doubles[s]);
-  for (auto* c : S->slots) hodlr_ctx_destroy(c);
+  for (Slot& sl : S->slots)
+    if (sl.ctx) hq::ctx_free(sl.ctx, sl.buf, sizeof(double) * sl.buf_doubles);
+  for (Slot& sl : S->slots)
+    if (sl.ctx) hodlr_ctx_destroy(sl.ctx);
   delete S->sched;
   delete S;
 }
@@ -232,6 +290,8 @@ int hodlr_server_submit(hodlr_server* S, int n, int nleaf, const int* leaf_sizes
                         const double* const* U12, const double* const* V12, const int* r12,
                         const double* const* U21, const double* const* V21, const int* r21, double tol,
                         int nrhs, const double* B_host, int ldb, long long keep_key, long long* request) {
+  if (!S) return HODLR_EINVAL;
+  std::lock_guard<std::mutex> lock(S->mu);
   if (!S || !request || !leaves || !B_host || nrhs < 1 || nrhs > 1024 || ldb < n || !(tol >= 0) || keep_key < -1)
     return HODLR_EINVAL;
   size_t need = 0;
@@ -288,6 +348,8 @@ int hodlr_server_submit(hodlr_server* S, int n, int nleaf, const int* leaf_sizes
 
 int hodlr_server_submit_solve(hodlr_server* S, long long key, int nrhs, const double* B_host, int ldb,
                               long long* request) {
+  if (!S) return HODLR_EINVAL;
+  std::lock_guard<std::mutex> lock(S->mu);
   if (!S || !request || !B_host || key < 0 || nrhs < 1 || nrhs > 1024) return HODLR_EINVAL;
   // the order n comes from the resident matrix or from the waiting factorization producing it
   int n = -1;
@@ -320,6 +382,8 @@ int hodlr_server_submit_solve(hodlr_server* S, long long key, int nrhs, const do
 }
 
 int hodlr_server_poll(hodlr_server* S, long long request, int* state, double* X_host, int ldx, double* latency_s) {
+  if (!S) return HODLR_EINVAL;
+  std::lock_guard<std::mutex> lock(S->mu);
   if (!S || !state) return HODLR_EINVAL;
   if (int rc = progress(S)) return rc;
   const hq::ServeScheduler::Request* r = S->sched->find(request);
@@ -357,6 +421,8 @@ int hodlr_server_poll(hodlr_server* S, long long request, int* state, double* X_
 }
 
 int hodlr_server_stats(hodlr_server* S, int* waiting, int* running, int* resident, size_t* bytes_used) {
+  if (!S) return HODLR_EINVAL;
+  std::lock_guard<std::mutex> lock(S->mu);
   if (!S) return HODLR_EINVAL;
   if (int rc = progress(S)) return rc;
   if (waiting) *waiting = S->sched->waiting();
