@@ -352,3 +352,70 @@ def to_dense(h: HodlrInput) -> np.ndarray:
         A[lo1:hi1, lo2:hi2] = h.U12[v] @ h.V12[v].T
         A[lo2:hi2, lo1:hi1] = h.U21[v] @ h.V21[v].T
     return A
+
+
+@dataclasses.dataclass
+class RectHodlrInput:
+    """Rectangular HODLR input (Sec. 6): row partition ``m_sizes`` and column partition
+    ``n_sizes`` (equal length 2^l, m_j >= n_j); leaf j is the dense m_j x n_j block; for internal
+    node v with children c1, c2: ``U12[v]`` (rows of c1 x r), ``V12[v]`` (columns of c2 x r),
+    ``U21[v]`` (rows of c2 x r), ``V21[v]`` (columns of c1 x r)."""
+    m_sizes: list
+    n_sizes: list
+    leaves: list
+    U12: list
+    V12: list
+    U21: list
+    V21: list
+    name: str = ""
+
+    @property
+    def m(self):
+        return int(sum(self.m_sizes))
+
+    @property
+    def n(self):
+        return int(sum(self.n_sizes))
+
+
+def random_rect_hodlr(m, n, nmin, k, seed=0, name="") -> RectHodlrInput:
+    """Random rectangular HODLR matrix shaped like Example 6.2: the column partition is the
+    balanced partition of n with leaves of at most ``nmin`` columns, the row partition splits m
+    the same number of times (floor(m/2) first), every leaf is N(0,1) of size m_j x n_j and every
+    off-diagonal block is U V^T with N(0,1) factors of rank k."""
+    n_sizes = balanced_leaf_sizes(n, nmin)
+    L = len(n_sizes)
+    m_sizes = [m]
+    while len(m_sizes) < L:
+        m_sizes = [x for s in m_sizes for x in (s // 2, s - s // 2)]
+    if any(a < b for a, b in zip(m_sizes, n_sizes)):
+        raise ValueError("every leaf needs m_j >= n_j")
+    rng = np.random.default_rng(seed)
+    rr, cr = node_ranges(m_sizes), node_ranges(n_sizes)
+    leaves = [np.asfortranarray(rng.standard_normal((m_sizes[j], n_sizes[j]))) for j in range(L)]
+    U12, V12, U21, V21 = [], [], [], []
+    for v in range(L - 1):
+        a, b = 2 * v + 1, 2 * v + 2
+        ma, mb = rr[a][1] - rr[a][0], rr[b][1] - rr[b][0]
+        na, nb = cr[a][1] - cr[a][0], cr[b][1] - cr[b][0]
+        U12.append(np.asfortranarray(rng.standard_normal((ma, k))))
+        V12.append(np.asfortranarray(rng.standard_normal((nb, k))))
+        U21.append(np.asfortranarray(rng.standard_normal((mb, k))))
+        V21.append(np.asfortranarray(rng.standard_normal((na, k))))
+    return RectHodlrInput(m_sizes, n_sizes, leaves, U12, V12, U21, V21,
+                          name=name or f"rect_m{m}_n{n}_nmin{nmin}_k{k}")
+
+
+def rect_to_dense(h: RectHodlrInput) -> np.ndarray:
+    """Assemble the dense m x n matrix of a rectangular HODLR input (a plain layout step)."""
+    A = np.zeros((h.m, h.n))
+    rr, cr = node_ranges(h.m_sizes), node_ranges(h.n_sizes)
+    L = len(h.m_sizes)
+    for j in range(L):
+        v = L - 1 + j
+        A[rr[v][0]:rr[v][1], cr[v][0]:cr[v][1]] = h.leaves[j]
+    for v in range(L - 1):
+        a, b = 2 * v + 1, 2 * v + 2
+        A[rr[a][0]:rr[a][1], cr[b][0]:cr[b][1]] = h.U12[v] @ h.V12[v].T
+        A[rr[b][0]:rr[b][1], cr[a][0]:cr[a][1]] = h.U21[v] @ h.V21[v].T
+    return A
