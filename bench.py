@@ -813,6 +813,111 @@ def peaks_arm(args):
     return 0
 
 
+def rect_arm(args):
+    """Example 6.2 of the paper (Sec. 6): the permuted QR of a random 8000 x 4000 rectangular HODLR
+    matrix (n_min = 250, rank-one off-diagonal blocks, eps = 1e-10) as the paper evaluates it, a
+    dense permuted Householder QR on the device followed by the compression of Y, T and R into the
+    HODLR formats of Fig. 6.3 (hodlr_rect_qr).  The matrix is resident on the device; a step is one
+    call.  The oracle (numpy) runs beside it on a 4000 x 2000 sample of the same family."""
+    import torch
+    import oracle.core as O
+    import oracle.rect as OR
+    import workloads as W
+    from paper_1809_10585_gb300 import binding as B
+    from paper_1809_10585_gb300 import build as BUILD
+    BUILD.build()
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    m, n, nmin, k, tol = 8000, 4000, 250, 1, 1e-10
+    inp = W.random_rect_hodlr(m, n, nmin, k, seed=rank)
+    A = W.rect_to_dense(inp)
+    ctx = B.Context(local)
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream.cuda_stream)
+    At = torch.from_numpy(np.ascontiguousarray(A.T)).to("cuda")            # column-major m x n
+    out = None
+    for _ in range(max(args.warmup, 1)):
+        if out:
+            for h in out[:3]:
+                h.free()
+        out = B.rect_qr(ctx, inp.m_sizes, inp.n_sizes, At.data_ptr(), m, tol, rank_cap=64, seed=3)
+    Yh, Th, Rh, anorm, rc = out
+    ranks = {nm: int(max(h.ranks()[0].max(), h.ranks()[1].max())) for nm, h in (("Y", Yh), ("T", Th), ("R", Rh))}
+    A_h = OR.compress(A, inp.m_sizes, inp.n_sizes, tol * anorm) if rank == 0 else None
+    mem = ({"Y_and_T": (Yh.storage() + Th.storage()) / A_h.storage(), "R": Rh.storage() / A_h.storage()}
+           if A_h is not None else None)
+    for h in (Yh, Th, Rh):
+        h.free()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            hs = B.rect_qr(ctx, inp.m_sizes, inp.n_sizes, At.data_ptr(), m, tol, rank_cap=64, seed=3)
+            evs[i][1].record(stream)
+            torch.cuda.synchronize()
+            for h in hs[:3]:
+                h.free()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), "cuda") / args.steps
+    # end to end: pinned upload of A, the factorization, and the ranks of the three factors read back
+    pinned = torch.from_numpy(np.ascontiguousarray(A.T)).pin_memory()
+    Ad = torch.empty_like(At)
+    e2e_ms = []
+    for i in range(max(2, min(args.steps, 5))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            Ad.copy_(pinned, non_blocking=True)
+        stream.synchronize()
+        hs = B.rect_qr(ctx, inp.m_sizes, inp.n_sizes, Ad.data_ptr(), m, tol, rank_cap=64, seed=3)
+        _ = [h.ranks() for h in hs[:3]]
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        for h in hs[:3]:
+            h.free()
+    e2e = float(np.median(e2e_ms))
+    flops = float(O.dense_qr_flops(m, n))
+    rec = recorded_fp64_peak()
+    peak = rec[0] if rec else B.fp64_peak(local)["dfma"]
+    achieved = flops / (ms / 1e3) / 1e12
+    line = {"metric": "rectangular HODLR permuted QRs/s (FP64, Sec. 6, Example 6.2, eps 1e-10)",
+            "value": 1e3 / ms * ws, "unit": "factorizations/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"rect_m{m}_n{n}_nmin{nmin}_k{k}_tol{tol:g}", "m": m, "n": n, "nmin": nmin,
+                       "leaves": len(inp.n_sizes), "rank": k, "tol": tol, "anorm": anorm, "rank_cap": 64,
+                       "max_rank": ranks, "memory_vs_A": mem,
+                       "l2": "flushed (256 MiB write) between timed steps; inputs (256 MB) larger than L2"},
+            "clocks": clk,
+            "e2e": {"value": 1e3 / e2e * ws, "unit": "factorizations/s", "h2d_bytes_per_step": int(A.nbytes),
+                    "d2h_bytes_per_step": int(4 * 3 * 2 * (len(inp.n_sizes) - 1))},
+            "roofline": {"bound": "alu", "kernel": "hodlr_rect_qr (dense permuted QR + compression)",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": None, "flops_per_launch": flops,
+                         "flops_note": "algorithmic flops of the dense Householder QR with T (2mn^2 - 2n^3/3 + "
+                                       "mn^2 - n^3/3); the compression is not counted",
+                         "peak_source": PEAK_RECORD if rec else "measured in this run"}}
+    if rank == 0 and not args.no_cpu_baseline:
+        smp = W.random_rect_hodlr(4000, 2000, 250, k, seed=0)
+        As = W.rect_to_dense(smp)
+        t0 = time.perf_counter()
+        OR.rect_qr(As, smp.m_sizes, smp.n_sizes, tol)
+        ts = time.perf_counter() - t0
+        scale = O.dense_qr_flops(4000, 2000) / flops
+        line["cpu_baseline"] = {"value": scale / ts, "unit": "factorizations/s", "cores": cpu_threads(),
+                                "kind": "oracle",
+                                "sample": f"one 4000 x 2000 matrix of the same family ({ts:.1f} s), scaled to the "
+                                          f"8000 x 4000 size by the dense QR flop ratio {scale:.3f}"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -836,7 +941,8 @@ def main():
     ap.add_argument("--served-requests", type=int, default=24, help="requests per rate of the served sweep")
     ap.add_argument("--served-rates", default="0.5,2,8,32", help="arrival rates (requests/s) of the served sweep")
     ap.add_argument("--served-pool", type=int, default=12, help="distinct matrices the served sweep draws from")
-    ap.add_argument("--workload", default="n8192", choices=["n8192", "batch256", "served", "n1024", "n65536"],
+    ap.add_argument("--workload", default="n8192",
+                    choices=["n8192", "batch256", "served", "n1024", "n65536", "rect"],
                     help="n8192: the ill-conditioned n = 8192 workload (default); batch256: 256 matrices of "
                          "log-uniform n in [2048, 32768]")
     ap.add_argument("--peaks", action="store_true",
@@ -857,6 +963,8 @@ def main():
         return served_arm(args)
     if args.workload in ("n1024", "n65536"):
         return single_arm(args)
+    if args.workload == "rect":
+        return rect_arm(args)
     return gpu_arm(args)
 
 

@@ -344,6 +344,60 @@ int hodlr_truncate(hodlr_ctx* ctx, int nL, int nR, int K, const double* L_dev,
                    double* Rout_dev, int* k_out);
 
 /*
+ * Rectangular HODLR matrices and their permuted QR (Sec. 6, Fig. 6.1-6.3).
+ *
+ * A rectangular HODLR matrix (m x n) has a row partition m_sizes and a column partition
+ * n_sizes of equal power-of-two length nleaf; the 2 x 2 splitting of Sec. 2.1 splits rows by
+ * the first and columns by the second, so leaf j is the dense m_j x n_j block and every
+ * off-diagonal block of an internal node is stored as U V^T (U: rows of the first child, V:
+ * columns of the second for A12, and the other way round for A21), at most rank_cap columns.
+ *
+ * hodlr_permuted_qr — Householder QR (Alg. 1, LAPACK sign convention, compact WY) of the dense
+ *   m x n matrix A_dev (device, column-major, lda >= m; m_j >= n_j for every j) that reduces
+ *   block column j to a triangle in the first n_j rows of row block j (Sec. 6: "situated on top
+ *   of the dense diagonal block"; everything else of the unreduced rows becomes zero).  This is
+ *   the QR of P A, where P lists the first n_j rows of every row block first, then all other
+ *   rows, each group in order: on return A_dev[P^T (...)] holds LAPACK's layout of that QR, i.e.
+ *   row p_i of A_dev holds row i of [R~ above the diagonal | Y~ below, unit diagonal implied],
+ *   so that Y = P^T Y~, R = P^T [R~; 0] and A = (I - Y T Y^T) R.  T_dev (n x n, ldt >= n) gets
+ *   the upper triangular T (zeros below the diagonal).  Panels of 64 columns by the cluster QR
+ *   kernel, trailing updates and the off-diagonal blocks of T by GEMMs (Sec. 3, Eq. (10)).
+ *   Scratch of m x n doubles plus n x n comes from the context's account (HODLR_ENOMEM).
+ *   Synchronous.  HODLR_EINVAL on inconsistent partitions or leading dimensions.
+ *
+ * hodlr_rect_compress — rectangular HODLR approximation of the dense device matrix A_dev: leaves
+ *   copied, every off-diagonal block by the randomized range finder and T_eps at the absolute
+ *   threshold thr (Sec. 2.1.1), Gaussian sketches from `seed`.  The partitions need not satisfy
+ *   m_j >= n_j.  Returns HODLR_ERANK (with *out valid, blocks truncated to rank_cap) when a
+ *   block keeps more than rank_cap singular values.
+ *
+ * hodlr_rect_qr — the Sec. 6 factorization as the paper evaluates it (Ex. 6.1, 6.2: "a dense
+ *   version of the algorithm", factors compressed afterwards into the formats of Fig. 6.3):
+ *   hodlr_permuted_qr of a copy of A_dev (A_dev is not modified), then Y (m x n) and R (m x n)
+ *   compressed in the rectangular format of A and T (n x n) in the square format of n_sizes.
+ *   Thresholds as in hQR: tol for Y and T (scale-free), tol ||A||_2 for R; anorm > 0 is used as
+ *   ||A||_2, else it is estimated by 30 power iterations on A^T A from the normalized all-ones
+ *   vector (*anorm_used, may be NULL, receives the value).  Outputs three new matrices owned by
+ *   the caller (hodlr_rect_free).  HODLR_ERANK (outputs valid) when a compression hit rank_cap.
+ *
+ * hodlr_rect_to_dense — the dense m x n matrix of R into out_dev (ld >= m).  hodlr_rect_ranks —
+ * the stored ranks of A12 (r12[v]) and A21 (r21[v]) for the nleaf - 1 internal nodes (heap
+ * order), synchronous.  hodlr_rect_free — release a matrix (NULL is ignored).
+ */
+typedef struct hodlr_rect hodlr_rect;
+int hodlr_permuted_qr(hodlr_ctx* ctx, int m, int n, int nleaf, const int* m_sizes, const int* n_sizes,
+                      double* A_dev, int lda, double* T_dev, int ldt);
+int hodlr_rect_compress(hodlr_ctx* ctx, int m, int n, int nleaf, const int* m_sizes, const int* n_sizes,
+                        const double* A_dev, int lda, double thr, int rank_cap, unsigned long long seed,
+                        hodlr_rect** out);
+int hodlr_rect_qr(hodlr_ctx* ctx, int m, int n, int nleaf, const int* m_sizes, const int* n_sizes,
+                  const double* A_dev, int lda, double tol, double anorm, int rank_cap, unsigned long long seed,
+                  hodlr_rect** Y, hodlr_rect** T, hodlr_rect** R, double* anorm_used);
+int hodlr_rect_to_dense(hodlr_ctx* ctx, const hodlr_rect* R, double* out_dev, int ld);
+int hodlr_rect_ranks(hodlr_ctx* ctx, const hodlr_rect* R, int* r12, int* r21);
+void hodlr_rect_free(hodlr_rect* R);
+
+/*
  * hodlr_dense_qr_noalloc — the same compact-WY Householder QR as hodlr_dense_qr, for callers
  * that must not allocate device memory: cudaMalloc and cudaFree synchronize the whole device
  * and can stall unrelated streams, and some callers (latency-critical loops, services that

@@ -89,6 +89,14 @@ _SIGS = {
     "hodlr_device_bytes": (C.c_int, [_VP, C.POINTER(C.c_size_t)]),
     "hodlr_footprint": (C.c_int, [C.c_int, C.c_int, _PI, C.c_int, C.c_int, C.c_int, C.c_int,
                                   C.POINTER(C.c_size_t)]),
+    "hodlr_permuted_qr": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, _PI, _PI, _VP, C.c_int, _VP, C.c_int]),
+    "hodlr_rect_compress": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, _PI, _PI, _VP, C.c_int, C.c_double, C.c_int,
+                                      C.c_ulonglong, C.POINTER(_VP)]),
+    "hodlr_rect_qr": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, _PI, _PI, _VP, C.c_int, C.c_double, C.c_double,
+                                C.c_int, C.c_ulonglong, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), _PD]),
+    "hodlr_rect_to_dense": (C.c_int, [_VP, _VP, _VP, C.c_int]),
+    "hodlr_rect_ranks": (C.c_int, [_VP, _VP, _PI, _PI]),
+    "hodlr_rect_free": (None, [_VP]),
 }
 
 SYMBOLS = tuple(_SIGS)
@@ -424,3 +432,87 @@ def truncate(ctx: Context, nL, nR, K, L_ptr, Rt_ptr, thr, kmax, Lout_ptr, Rout_p
     rc = lib().hodlr_truncate(ctx.h, nL, nR, K, _VP(L_ptr), _VP(Rt_ptr), thr, kmax, _VP(Lout_ptr),
                               _VP(Rout_ptr), C.byref(k))
     return rc, k.value
+
+
+# ------------------------------------------------------------ rectangular HODLR (Sec. 6)
+def _ints(xs):
+    return (C.c_int * len(xs))(*[int(x) for x in xs])
+
+
+def permuted_qr(ctx: Context, m_sizes, n_sizes, A_ptr, lda, T_ptr, ldt):
+    """Dense permuted QR of Sec. 6 in place on the device (hodlr_permuted_qr)."""
+    m, n = int(sum(m_sizes)), int(sum(n_sizes))
+    check(lib().hodlr_permuted_qr(ctx.h, m, n, len(m_sizes), _ints(m_sizes), _ints(n_sizes), _VP(A_ptr), lda,
+                                  _VP(T_ptr), ldt), "hodlr_permuted_qr")
+
+
+class RectMatrix:
+    """A device-resident rectangular HODLR matrix (hodlr_rect)."""
+
+    def __init__(self, ctx: Context, h, m_sizes, n_sizes):
+        self.ctx, self.h = ctx, h
+        self.m_sizes, self.n_sizes = list(m_sizes), list(n_sizes)
+        self.m, self.n = int(sum(m_sizes)), int(sum(n_sizes))
+
+    @classmethod
+    def compress(cls, ctx: Context, m_sizes, n_sizes, A_ptr, lda, thr, rank_cap=128, seed=0):
+        h = _VP()
+        rc = lib().hodlr_rect_compress(ctx.h, int(sum(m_sizes)), int(sum(n_sizes)), len(m_sizes), _ints(m_sizes),
+                                       _ints(n_sizes), _VP(A_ptr), lda, thr, rank_cap, seed, C.byref(h))
+        if rc not in (0, HODLR_ERANK):
+            raise HodlrError(rc, "hodlr_rect_compress")
+        return cls(ctx, h, m_sizes, n_sizes), rc
+
+    def to_dense(self, out_ptr, ld):
+        check(lib().hodlr_rect_to_dense(self.ctx.h, self.h, _VP(out_ptr), ld), "hodlr_rect_to_dense")
+
+    def ranks(self):
+        nn = max(1, len(self.m_sizes) - 1)
+        a, b = (C.c_int * nn)(), (C.c_int * nn)()
+        check(lib().hodlr_rect_ranks(self.ctx.h, self.h, a, b), "hodlr_rect_ranks")
+        k = len(self.m_sizes) - 1
+        return np.array(a[:k]), np.array(b[:k])
+
+    def storage(self):
+        """Doubles stored at the actual ranks: dense leaves plus the low-rank factors."""
+        import math
+        L = len(self.m_sizes)
+        s = sum(a * b for a, b in zip(self.m_sizes, self.n_sizes))
+        r12, r21 = self.ranks()
+        ro = np.concatenate([[0], np.cumsum(self.m_sizes)])
+        co = np.concatenate([[0], np.cumsum(self.n_sizes)])
+
+        def span(off, v):                       # extent of heap node v in a partition
+            d = int(math.floor(math.log2(v + 1)))
+            width = L >> d
+            first = (v - ((1 << d) - 1)) * width
+            return int(off[first + width] - off[first])
+        for v in range(L - 1):
+            a, b = 2 * v + 1, 2 * v + 2
+            s += r12[v] * (span(ro, a) + span(co, b)) + r21[v] * (span(ro, b) + span(co, a))
+        return int(s)
+
+    def free(self):
+        if self.h:
+            lib().hodlr_rect_free(self.h)
+            self.h = _VP()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def rect_qr(ctx: Context, m_sizes, n_sizes, A_ptr, lda, tol, anorm=0.0, rank_cap=128, seed=0):
+    """Sec. 6 factorization (hodlr_rect_qr): returns (Y, T, R, anorm_used, rc) with rc 0 or
+    HODLR_ERANK."""
+    y, t, r = _VP(), _VP(), _VP()
+    an = C.c_double()
+    rc = lib().hodlr_rect_qr(ctx.h, int(sum(m_sizes)), int(sum(n_sizes)), len(m_sizes), _ints(m_sizes),
+                             _ints(n_sizes), _VP(A_ptr), lda, tol, anorm, rank_cap, seed, C.byref(y), C.byref(t),
+                             C.byref(r), C.byref(an))
+    if rc not in (0, HODLR_ERANK):
+        raise HodlrError(rc, "hodlr_rect_qr")
+    return (RectMatrix(ctx, y, m_sizes, n_sizes), RectMatrix(ctx, t, n_sizes, n_sizes),
+            RectMatrix(ctx, r, m_sizes, n_sizes), an.value, rc)

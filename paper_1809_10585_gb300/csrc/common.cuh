@@ -160,8 +160,10 @@ struct CopyDesc {
 // Small element-wise operations, one descriptor per array, so that one launch may carry many:
 //   kSmallFill  p[0..cnt) = v;   kSmallIFill  ip[0..cnt) = (int)v;
 //   kSmallIdent p (ld, rows x cols) = [I; 0];
-//   kSmallNorm  *out = ||p[0..cnt)||_2, and p /= *out when scale (a zero vector is kept).
-enum SmallKind { kSmallFill = 0, kSmallIFill = 1, kSmallIdent = 2, kSmallNorm = 3 };
+//   kSmallNorm  *out = ||p[0..cnt)||_2, and p /= *out when scale (a zero vector is kept);
+//   kSmallTri   out (leading dimension cnt, rows x cols) = the unit lower trapezoidal part of
+//               p (ld) when scale == 0 (ones on the diagonal), its upper part when scale == 1.
+enum SmallKind { kSmallFill = 0, kSmallIFill = 1, kSmallIdent = 2, kSmallNorm = 3, kSmallTri = 4 };
 struct SmallDesc {
   int kind;
   double* p;

@@ -12,7 +12,7 @@
 //
 //  * jacobi_dsmem_kernel — one-sided (Hestenes) Jacobi on the columns of the K x K core of
 //    T_eps, round-robin pair ordering, pairs spread over all warps of the cluster, one
-//    cluster barrier per round.
+//    cluster barrier per round; plane rotations in scaled form (two FMAs per row and pair).
 //
 // On GB300 a single SM retires about 2 FP64 FMA per clock, so a K^3 factorization on one SM
 // takes milliseconds for K ~ 100; a cluster of up to 16 CTAs (one per SM) multiplies the FP64
@@ -499,6 +499,7 @@ __device__ __forceinline__ void qr_global_impl(const QRDesc* __restrict__ descs,
 
 __global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __restrict__ descs);
 
+template <bool kOwner>
 __global__ void __launch_bounds__(QT, 2) jacobi_dsmem_kernel(const JacobiDesc* __restrict__ descs,
                                                           int q1cap, int q2cap, int smem_bytes, int solo_cols);
 constexpr size_t kJacobiSmemMax = 200 * 1024;
@@ -1011,8 +1012,10 @@ static int probe_max_cluster() {
     }
   }
   cudaGetLastError();
-  cudaFuncSetAttribute(jacobi_dsmem_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  cudaFuncSetAttribute(jacobi_dsmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kJacobiSmemMax);
+  cudaFuncSetAttribute(jacobi_dsmem_kernel<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(jacobi_dsmem_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kJacobiSmemMax);
+  cudaFuncSetAttribute(jacobi_dsmem_kernel<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(jacobi_dsmem_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kJacobiSmemMax);
   cudaGetLastError();
   return v;
 }
@@ -1112,6 +1115,40 @@ __device__ inline bool jacobi_rotation(double al, double be, double g, double to
   else t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
   c = 1.0 / sqrt(1.0 + t * t);
   s = c * t;
+  return true;
+}
+
+// The same rotation for the scaled form of the sweep (jacobi_solo_impl): returns t exactly as it
+// is applied and c = 1 / sqrt(1 + t^2) to FP64 rounding.  In the FP32 branch c0 = rsqrtf(1 + tf^2)
+// is corrected in FP64 with the series above, d = c0^2 (1 + t^2) - 1, where c0 t is exact in
+// FP64 (two 24-bit significands).
+__device__ inline bool jacobi_rotation_ct(double al, double be, double g, double tol2, float tolf, double& c,
+                                          double& t) {
+  const long long im = max(__double_as_longlong(al), __double_as_longlong(be));
+  int ex = (int)(im >> 52) - 1023;
+  ex = min(max(ex, -1000), 1000);
+  const double sc = pow2i(-ex);
+  const double a2 = al * sc, b2 = be * sc, g2 = g * sc;
+  const float af = (float)a2, bf = (float)b2, gf = (float)g2;
+  if (fminf(af, bf) > 1e-30f && fabsf(gf) > 1e-30f) {
+    if (!(fabsf(gf) > tolf * sqrtf(af) * sqrtf(bf))) return false;
+    const float zf = __fdividef(bf - af, 2.0f * gf);
+    float tf;
+    if (fabsf(zf) > 1e18f) tf = __fdividef(0.5f, zf);
+    else tf = __fdividef(copysignf(1.0f, zf), fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)));
+    const float cf = rsqrtf(fmaf(tf, tf, 1.0f));
+    const double c0 = (double)cf;
+    t = (double)tf;
+    const double s0 = c0 * t;
+    const double dd = fma(c0, c0, fma(s0, s0, -1.0));
+    c = c0 * fma(fma(0.375, dd, -0.5), dd, 1.0);
+    return true;
+  }
+  if (!(g2 * g2 > tol2 * a2 * b2)) return false;
+  const double zeta = (b2 - a2) / (2.0 * g2);
+  if (fabs(zeta) > 1e100) t = 0.5 / zeta;
+  else t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  c = 1.0 / sqrt(1.0 + t * t);
   return true;
 }
 
@@ -1262,14 +1299,17 @@ __global__ void __launch_bounds__(QT) jacobi_cluster_kernel(const JacobiDesc* __
 
 // One-sided Jacobi with the core held in distributed shared memory: column j lives in the
 // shared memory of CTA j % C.  Each warp rotates 32 / LG column pairs at once, one pair per
-// group of LG lanes (LG = 4, 8, 16 or 32, the smallest with q1 <= LG * kJacobiRegs): the FP64
-// instructions that form the rotation (the scarce resource, see jacobi_rotation) are then
-// shared by several pairs, and the dot product needs only log2(LG) shuffle levels.  Control
+// group of LG lanes (LG = 4 or 8, chosen by the dispatcher): the FP64 instructions that form
+// the rotation (the scarce resource, see jacobi_rotation) are then shared by several pairs, and
+// the dot product needs only log2(LG) shuffle levels.  Control
 // flow stays warp-uniform: a group whose pair is converged, deflated or absent applies the
-// identity and stores nothing; a warp none of whose pairs rotates skips the application.  Pair (a, b) reads and writes both columns through DSMEM; per
-// round that is one remote load, one remote store and one cluster barrier.  Same pair schedule,
-// thresholds and deflation as jacobi_cluster_kernel.  Columns longer than LG * kJacobiRegs
-// (q1 > 256 for LG = 32) are streamed from shared memory twice instead of held in registers.
+// identity and stores nothing; a warp none of whose pairs rotates skips the application.  Pair
+// (a, b) reads and writes both columns through DSMEM; per round that is one remote load, one
+// remote store and one cluster barrier.  Rotations take the scaled form of jacobi_solo_impl
+// (two FMAs per row; the scales d_j, e_j live with the column's owner and are folded into the
+// columns at every sweep start and every 16 rounds).  Same pair schedule, thresholds and
+// deflation as jacobi_cluster_kernel.  Columns longer than LG * kJacobiRegs (q1 > 64 for
+// LG = 8) are streamed from shared memory twice instead of held in registers.
 template <int LG>
 __device__ __forceinline__ void jacobi_dsmem_impl(const JacobiDesc* __restrict__ descs, const int* __restrict__ di,
                                                   double* flops, int q1cap, int q2cap) {
@@ -1288,7 +1328,9 @@ __device__ __forceinline__ void jacobi_dsmem_impl(const JacobiDesc* __restrict__
   const int ldc = max(q1, 1);
   double* cols = jsm;                                    // nloc x ldc, slot s = column crank + s*C
   double* cn = cols + (size_t)nloc * ldc;                // current squared norms of own columns
-  double* nall = cn + nloc;                              // squared norms of all columns (sweep start)
+  double* dsc = cn + nloc;                               // scales d_j of own columns
+  double* esc = dsc + nloc;                              // e_j ~ 1 / d_j
+  double* nall = esc + nloc;                             // squared norms of all columns (sweep start)
   int* act = reinterpret_cast<int*>(nall + q2);          // active columns of the sweep
   __shared__ int nact;
   double* M = d.M;
@@ -1311,6 +1353,7 @@ __device__ __forceinline__ void jacobi_dsmem_impl(const JacobiDesc* __restrict__
     if (j >= q2) break;
     for (int i = threadIdx.x; i < q1; i += QT) cols[(size_t)sl * ldc + i] = M[i + (size_t)j * ldm];
   }
+  for (int sl = threadIdx.x; sl < nloc; sl += QT) dsc[sl] = 1.0;
   // every CTA of the cluster must be running before any distributed shared memory access
   cl.sync();
 
@@ -1318,13 +1361,15 @@ __device__ __forceinline__ void jacobi_dsmem_impl(const JacobiDesc* __restrict__
   const int nreg = (q1 + LG - 1) / LG;                   // register slots in use (uniform)
   const bool inreg = nreg <= kJacobiRegs;
   for (int sweep = 0; sweep <= kMaxSweeps; ++sweep) {
-    // exact squared norms of own columns, broadcast into every CTA's copy
+    // fold the scales into own columns; exact squared norms, broadcast into every CTA's copy
     for (int sl = warp; sl < nloc; sl += QW) {
       const int j = crank + sl * C;
       if (j >= q2) break;
+      const double s = dsc[sl];
       double v = 0.0;
       for (int i = lane; i < q1; i += 32) {
-        const double x = cols[(size_t)sl * ldc + i];
+        const double x = cols[(size_t)sl * ldc + i] * s;
+        cols[(size_t)sl * ldc + i] = x;
         v = fma(x, x, v);
       }
       v = warp_sum2(v);
@@ -1332,6 +1377,8 @@ __device__ __forceinline__ void jacobi_dsmem_impl(const JacobiDesc* __restrict__
       if (lane == 0) {
         cn[sl] = v;
         d.nrm[j] = v;
+        dsc[sl] = 1.0;
+        esc[sl] = 1.0;
       }
     }
     cl.sync();
@@ -1348,6 +1395,21 @@ __device__ __forceinline__ void jacobi_dsmem_impl(const JacobiDesc* __restrict__
     const int P = Ka + (Ka & 1);
     int local = 0;
     for (int r = 0; r < P - 1; ++r) {
+      if (r > 0 && r % 16 == 0) {
+        // fold own scales (true norms are tracked unchanged); the previous round's barrier
+        // ordered every remote access to these columns
+        for (int sl = warp; sl < nloc; sl += QW) {
+          if (crank + sl * C >= q2) break;
+          const double s = dsc[sl];
+          for (int i = lane; i < q1; i += 32) cols[(size_t)sl * ldc + i] *= s;
+          __syncwarp();
+          if (lane == 0) {
+            dsc[sl] = 1.0;
+            esc[sl] = 1.0;
+          }
+        }
+        cl.sync();
+      }
       for (int pb = gw * PPW; pb < P / 2; pb += nw * PPW) {
         const int pi = pb + sub;
         int ia = 0, ib = 0;
@@ -1359,9 +1421,13 @@ __device__ __forceinline__ void jacobi_dsmem_impl(const JacobiDesc* __restrict__
         const int a = valid ? act[ia] : 0, b = valid ? act[ib] : 0;
         double* xa = cl.map_shared_rank(cols, a % C) + (size_t)(a / C) * ldc;
         double* yb = cl.map_shared_rank(cols, b % C) + (size_t)(b / C) * ldc;
-        double* na_p = cl.map_shared_rank(cn, a % C) + a / C;
-        double* nb_p = cl.map_shared_rank(cn, b % C) + b / C;
-        const double al = valid ? *na_p : 0.0, be = valid ? *nb_p : 0.0;
+        // per-column scalars of the owners (pointers are formed again for the stores: fewer live
+        // registers)
+        const int ao = a % C, as = a / C, bo = b % C, bs = b / C;
+        const double al = valid ? cl.map_shared_rank(cn, ao)[as] : 0.0;
+        const double be = valid ? cl.map_shared_rank(cn, bo)[bs] : 0.0;
+        const double da = valid ? cl.map_shared_rank(dsc, ao)[as] : 1.0;
+        const double db = valid ? cl.map_shared_rank(dsc, bo)[bs] : 1.0;
         double x[kJacobiRegs], y[kJacobiRegs];
         double g0 = 0.0, g1 = 0.0;
         if (inreg) {
@@ -1382,19 +1448,22 @@ __device__ __forceinline__ void jacobi_dsmem_impl(const JacobiDesc* __restrict__
             if (i + LG < q1) g1 = fma(xa[i + LG], yb[i + LG], g1);
           }
         }
-        double g = g0 + g1;
+        double gw2 = g0 + g1;
 #pragma unroll
-        for (int o = LG / 2; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+        for (int o = LG / 2; o > 0; o >>= 1) gw2 += __shfl_xor_sync(0xffffffffu, gw2, o);
+        const double g = da * db * gw2;                   // gamma of the true columns
         // every lane of a group holds g and forms the same rotation (an FP64 instruction costs
         // the same for one lane as for 32); the deflation test runs on the bit patterns
-        double c = 1.0, sn = 0.0, tt = 0.0;
+        double c = 1.0, tt = 0.0;
         const bool doit = valid && __double_as_longlong(al) > dfl_bits && __double_as_longlong(be) > dfl_bits &&
-                          jacobi_rotation(al, be, g, tol2, tolf, c, sn, tt);
+                          jacobi_rotation_ct(al, be, g, tol2, tolf, c, tt);
         if (!doit) {
           c = 1.0;
-          sn = 0.0;
           tt = 0.0;
         }
+        const double ea = doit ? cl.map_shared_rank(esc, ao)[as] : 1.0;
+        const double eb = doit ? cl.map_shared_rank(esc, bo)[bs] : 1.0;
+        const double mu = doit ? tt * db * ea : 0.0, nu = doit ? tt * da * eb : 0.0;
         // alpha' = alpha - t gamma, beta' = beta + t gamma; the shrinking column's norm is summed
         // exactly when it loses more than half of its mass (cancellation)
         const double tg = tt * g;
@@ -1402,13 +1471,27 @@ __device__ __forceinline__ void jacobi_dsmem_impl(const JacobiDesc* __restrict__
         const bool exact = doit && (a_shrinks ? (tg > 0.5 * al) : (-tg > 0.5 * be));
         const bool any_exact = __any_sync(0xffffffffu, exact);
         const bool any_doit = __any_sync(0xffffffffu, doit);   // else the warp's pairs are final
+        // the pair's scalars are stored before the columns (no other pair of the round reads
+        // them), so that they are not live across the application; an exact norm replaces the
+        // tracked one afterwards
+        const double dsh = c * (a_shrinks ? da : db);     // new scale of the shrinking column
+        if (doit && gl == 0) {
+          const double rc = fma(tt, tt, 1.0) * c;         // 1 / c
+          cl.map_shared_rank(cn, ao)[as] = fma(-tt, g, al);
+          cl.map_shared_rank(cn, bo)[bs] = fma(tt, g, be);
+          cl.map_shared_rank(esc, ao)[as] = ea * rc;
+          cl.map_shared_rank(esc, bo)[bs] = eb * rc;
+          cl.map_shared_rank(dsc, ao)[as] = c * da;
+          cl.map_shared_rank(dsc, bo)[bs] = c * db;
+          ++local;
+        }
         double s0 = 0.0, s1 = 0.0;
         if (inreg && any_doit) {
 #pragma unroll
           for (int t = 0; t < kJacobiRegs; ++t) {
             if (t < nreg) {
-              const double xn = c * x[t] - sn * y[t];
-              const double yn = sn * x[t] + c * y[t];
+              const double xn = fma(-mu, y[t], x[t]);
+              const double yn = fma(nu, x[t], y[t]);
               const int i = gl + LG * t;
               if (doit && i < q1) {
                 xa[i] = xn;
@@ -1424,8 +1507,8 @@ __device__ __forceinline__ void jacobi_dsmem_impl(const JacobiDesc* __restrict__
         } else if (doit) {
           for (int i = gl; i < q1; i += LG) {
             const double xv = xa[i], yv = yb[i];
-            const double xn = c * xv - sn * yv;
-            const double yn = sn * xv + c * yv;
+            const double xn = fma(-mu, yv, xv);
+            const double yn = fma(nu, xv, yv);
             xa[i] = xn;
             yb[i] = yn;
             const double v = a_shrinks ? xn : yn;
@@ -1437,11 +1520,9 @@ __device__ __forceinline__ void jacobi_dsmem_impl(const JacobiDesc* __restrict__
 #pragma unroll
           for (int o = LG / 2; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
         }
-        if (doit && gl == 0) {
-          const double na = fma(-tt, g, al), nb = fma(tt, g, be);
-          *na_p = (exact && a_shrinks) ? ss : na;
-          *nb_p = (exact && !a_shrinks) ? ss : nb;
-          ++local;
+        if (exact && gl == 0) {
+          if (a_shrinks) cl.map_shared_rank(cn, ao)[as] = dsh * dsh * ss;
+          else cl.map_shared_rank(cn, bo)[bs] = dsh * dsh * ss;
         }
       }
       cl.sync();
@@ -1466,8 +1547,10 @@ __device__ __forceinline__ void jacobi_dsmem_impl(const JacobiDesc* __restrict__
 // writes only its own column and norm, into its own shared memory.  Remote traffic is therefore
 // loads only; the one cluster barrier per round orders the round's writes before the next
 // round's reads and the round's reads before the buffer is written again.  A column without a
-// partner in a round is copied to the other buffer.  Lane groups, thresholds, deflation and the
-// exact-norm rule as in jacobi_dsmem_impl.
+// partner in a round is copied to the other buffer.  Rotations take the scaled form of
+// jacobi_solo_impl (the owner's new column is one FMA per row; scales are double-buffered with
+// the columns and folded at every sweep start and every 16 rounds).  Lane groups, thresholds,
+// deflation and the exact-norm rule as in jacobi_dsmem_impl.
 template <int LG, bool SOLO>
 __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__ descs, const int* __restrict__ di,
                                                   double* flops, int q1cap, int q2cap) {
@@ -1489,7 +1572,9 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
   const int q2n = q2;
   double* cols0 = jsm;                                   // [2][nloc][ldc], slot s = column crank + s*C
   double* cn0 = cols0 + 2 * (size_t)nloc * ldc;          // [2][nloc] tracked squared norms
-  double* nall = cn0 + 2 * nloc;                         // squared norms of all columns (sweep start)
+  double* sc0 = cn0 + 2 * nloc;                          // [2][nloc] scales d_j
+  double* ec0 = sc0 + 2 * nloc;                          // [2][nloc] e_j ~ 1 / d_j
+  double* nall = ec0 + 2 * nloc;                         // squared norms of all columns (sweep start)
   int* act = reinterpret_cast<int*>(nall + q2n);         // active columns of the sweep
   int* own = act + q2n;                                // positions (in act) of own active columns
   __shared__ int nact, nown;
@@ -1514,6 +1599,7 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
     if (j >= q2) break;
     for (int i = threadIdx.x; i < q1; i += QT) cols0[(size_t)sl * ldc + i] = M[i + (size_t)j * ldm];
   }
+  for (int sl = threadIdx.x; sl < nloc; sl += QT) sc0[sl] = 1.0;
   // every CTA of the cluster must be running before any distributed shared memory access
   csync<SOLO>(cl);
 
@@ -1523,13 +1609,15 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
   for (int sweep = 0; sweep <= kMaxSweeps; ++sweep) {
     double* cols = cols0 + cur * bufstride;
     double* cn = cn0 + cur * nloc;
-    // exact squared norms of own columns, broadcast into every CTA's copy
+    // fold the scales into own columns; exact squared norms, broadcast into every CTA's copy
     for (int sl = warp; sl < nloc; sl += QW) {
       const int j = crank + sl * C;
       if (j >= q2) break;
+      const double s = sc0[cur * nloc + sl];
       double v = 0.0;
       for (int i = lane; i < q1; i += 32) {
-        const double x = cols[(size_t)sl * ldc + i];
+        const double x = cols[(size_t)sl * ldc + i] * s;
+        cols[(size_t)sl * ldc + i] = x;
         v = fma(x, x, v);
       }
       v = warp_sum2(v);
@@ -1537,6 +1625,8 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
       if (lane == 0) {
         cn[sl] = v;
         d.nrm[j] = v;
+        sc0[cur * nloc + sl] = 1.0;
+        ec0[cur * nloc + sl] = 1.0;
       }
     }
     csync<SOLO>(cl);
@@ -1560,6 +1650,21 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
     const int P = Ka + (Ka & 1), m = P - 1;
     int local = 0;
     for (int r = 0; r < P - 1; ++r) {
+      if (r > 0 && r % 16 == 0) {
+        // fold the scales of own active columns in the buffer this round reads (the previous
+        // round's barrier ordered every access to it)
+        for (int t = warp; t < No; t += QW) {
+          const int sl = act[own[t]] >> 5;
+          const double s = sc0[cur * nloc + sl];
+          for (int i = lane; i < q1; i += 32) cols0[cur * bufstride + (size_t)sl * ldc + i] *= s;
+          __syncwarp();
+          if (lane == 0) {
+            sc0[cur * nloc + sl] = 1.0;
+            ec0[cur * nloc + sl] = 1.0;
+          }
+        }
+        csync<SOLO>(cl);
+      }
       const int rb = cur, wb = cur ^ 1;                  // read / write buffers of this round
       for (int tb = warp * PPW; tb < No; tb += QW * PPW) {
         const int t = tb + sub;
@@ -1580,6 +1685,8 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
         const double* yb = rmt<SOLO>(cl, cols0, bo) + rb * bufstride + (size_t)bs * ldc;
         const double al = valid ? rmt<SOLO>(cl, cn0, ao)[rb * nloc + as] : 0.0;
         const double be = valid ? rmt<SOLO>(cl, cn0, bo)[rb * nloc + bs] : 0.0;
+        const double da = valid ? rmt<SOLO>(cl, sc0, ao)[rb * nloc + as] : 1.0;
+        const double db = valid ? rmt<SOLO>(cl, sc0, bo)[rb * nloc + bs] : 1.0;
         double* dst = cols0 + wb * bufstride + (size_t)ms * ldc;
         const double* src = cols0 + rb * bufstride + (size_t)ms * ldc;
         double xr[kJacobiRegs], yr[kJacobiRegs];
@@ -1602,31 +1709,42 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
             if (i + LG < q1) g1 = fma(xa[i + LG], yb[i + LG], g1);
           }
         }
-        double g = g0 + g1;
+        double gw2 = g0 + g1;
 #pragma unroll
-        for (int o = LG / 2; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-        double c = 1.0, sn = 0.0, tt = 0.0;
+        for (int o = LG / 2; o > 0; o >>= 1) gw2 += __shfl_xor_sync(0xffffffffu, gw2, o);
+        const double g = da * db * gw2;                   // gamma of the true columns
+        double c = 1.0, tt = 0.0;
         const bool doit = valid && __double_as_longlong(al) > dfl_bits && __double_as_longlong(be) > dfl_bits &&
-                          jacobi_rotation(al, be, g, tol2, tolf, c, sn, tt);
+                          jacobi_rotation_ct(al, be, g, tol2, tolf, c, tt);
         if (!doit) {
           c = 1.0;
-          sn = 0.0;
           tt = 0.0;
         }
-        // own new column: x' = c x - s y (a), y' = s x + c y (b); the identity when not rotated
-        const double ca = mine_a ? c : sn, cb = mine_a ? -sn : c;
+        // own new column: w_a - (t d_b e_a) w_b (a) or w_b + (t d_a e_b) w_a (b)
+        const double eown = ec0[rb * nloc + (task ? ms : 0)];
+        const double m1 = mine_a ? -tt * db * eown : tt * da * eown;
         const double tg = tt * g;
         const bool a_shrinks = tg > 0.0;
         const bool exact = doit && (mine_a == a_shrinks) && (a_shrinks ? (tg > 0.5 * al) : (-tg > 0.5 * be));
         const bool any_exact = __any_sync(0xffffffffu, exact);
         const bool any_doit = __any_sync(0xffffffffu, doit);
+        // own scalars of the next buffer are stored before the column (only this task writes
+        // them), so that they are not live across the application
+        const double dnew = c * (mine_a ? da : db);
+        if (task && gl == 0) {
+          const int sl = ms;
+          cn0[wb * nloc + sl] = doit ? (mine_a ? fma(-tt, g, al) : fma(tt, g, be)) : cn0[rb * nloc + sl];
+          sc0[wb * nloc + sl] = doit ? dnew : sc0[rb * nloc + sl];
+          ec0[wb * nloc + sl] = doit ? eown * (fma(tt, tt, 1.0) * c) : eown;
+          if (doit && mine_a) ++local;
+        }
         double s0 = 0.0, s1 = 0.0;
         if (inreg && any_doit) {
 #pragma unroll
           for (int u = 0; u < kJacobiRegs; ++u) {
             if (u < nreg) {
               const int i = gl + LG * u;
-              const double v = doit ? fma(ca, xr[u], cb * yr[u]) : 0.0;
+              const double v = doit ? fma(m1, mine_a ? yr[u] : xr[u], mine_a ? xr[u] : yr[u]) : 0.0;
               if (task && i < q1) dst[i] = doit ? v : src[i];
               if (any_exact) {
                 if (u & 1) s1 = fma(v, v, s1);
@@ -1645,7 +1763,7 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
           }
         } else if (task) {
           for (int i = gl; i < q1; i += LG) {
-            const double v = doit ? fma(ca, xa[i], cb * yb[i]) : src[i];
+            const double v = doit ? fma(m1, mine_a ? yb[i] : xa[i], mine_a ? xa[i] : yb[i]) : src[i];
             dst[i] = v;
             s0 = fma(v, v, s0);
           }
@@ -1655,12 +1773,7 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
 #pragma unroll
           for (int o = LG / 2; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
         }
-        if (task && gl == 0) {
-          const int sl = ms;
-          const double nw = doit ? (mine_a ? fma(-tt, g, al) : fma(tt, g, be)) : cn0[rb * nloc + sl];
-          cn0[wb * nloc + sl] = exact ? ss : nw;
-          if (doit && mine_a) ++local;
-        }
+        if (exact && gl == 0) cn0[wb * nloc + ms] = dnew * dnew * ss;
       }
       csync<SOLO>(cl);
       cur ^= 1;
@@ -1670,9 +1783,11 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
     for (int sl = 0; sl < nloc; ++sl) {
       const int j = crank + sl * C;
       if (j >= q2) break;
-      if (!(nall[j] > dfl) && ((P - 1) & 1))
+      if (!(nall[j] > dfl) && ((P - 1) & 1)) {
         for (int i = threadIdx.x; i < q1; i += QT) cols0[cur * bufstride + (size_t)sl * ldc + i] =
                                                       cols0[(cur ^ 1) * bufstride + (size_t)sl * ldc + i];
+        if (threadIdx.x == 0) sc0[cur * nloc + sl] = sc0[(cur ^ 1) * nloc + sl];
+      }
     }
     csync<SOLO>(cl);
     if (*(volatile int*)&d.rot[sweep] == 0) sweep = kMaxSweeps - 1;   // converged: final norms next pass
@@ -1686,15 +1801,231 @@ __device__ __forceinline__ void jacobi_owner_impl(const JacobiDesc* __restrict__
   csync<SOLO>(cl);   // no CTA may exit while others still access its shared memory
 }
 
+// Shared memory of the one-CTA scaled Jacobi (jacobi_solo_impl) for a q1 x q2 core.
+__host__ __device__ inline size_t jacobi_solo_bytes(int q1, int q2) {
+  return (size_t)q2 * max(q1, 1) * sizeof(double) + 3 * (size_t)q2 * sizeof(double) + (size_t)q2 * sizeof(int) + 64;
+}
+
+// One-sided Jacobi on one CTA with scaled rotations.  Column j is held as w_j with the true
+// column d_j w_j; the CTA also keeps e_j ~ 1 / d_j and the true squared norm.  A rotation of
+// the pair (a, b) with tangent t and cosine c (jacobi_rotation_ct) is applied as
+//     w_a <- w_a - (t d_b e_a) w_b,   w_b <- w_b + (t d_a e_b) w_a,   d_a, d_b <- c d_a, c d_b,
+// which is the plane rotation c [1, -t; t, 1] of the true columns with two FMAs per row instead
+// of two multiplications and two FMAs (Rutishauser's scaled form of the rotation).  The scales
+// are folded into the columns at the start of every sweep and every 16 rounds, which bounds
+// both the growth of w (c >= 1 / sqrt 2) and the drift of d_j e_j away from 1.  One group of
+// LG lanes rotates one pair; pairs of a round are disjoint, so columns are updated in place
+// and one block barrier separates the rounds.  Pair schedule, thresholds, deflation and the
+// exact-norm rule as in the other forms.
+template <int LG>
+__device__ __forceinline__ void jacobi_solo_impl(const JacobiDesc* __restrict__ descs, const int* __restrict__ di,
+                                                 double* flops, int q1cap, int q2cap) {
+  constexpr int PPW = 32 / LG;                            // pairs per warp and step
+  constexpr int kFold = 16;                               // rounds between folds of the scales
+  const JacobiDesc& d = descs[blockIdx.y];
+  const int q1 = min(dimv(d.q1, d.q1ref, di), q1cap), q2 = min(dimv(d.q2, d.q2ref, di), q2cap);
+  if (threadIdx.x == 0 && flops && q1 > 0 && q2 > 0) {
+    double p = max(q1, q2), q = min(q1, q2);
+    atomicAdd(&flops[kKindSlot + 3], 4.0 * p * p * q + 8.0 * p * q * q + 9.0 * q * q * q);
+  }
+  extern __shared__ double jsm[];
+  const int ldc = max(q1, 1);
+  double* cols = jsm;                                     // q2 x ldc: w
+  double* cn = cols + (size_t)q2 * ldc;                   // true squared norms
+  double* dsc = cn + q2;                                  // d_j
+  double* esc = dsc + q2;                                 // e_j
+  int* act = reinterpret_cast<int*>(esc + q2);            // active columns of the sweep
+  __shared__ int nact, nrot;
+  double* M = d.M;
+  const size_t ldm = d.ldm;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sub = lane / LG, gl = lane % LG;
+  const double tol = fmin(1e-13, fmax(1e-15, 8.8e-16 * sqrt((double)q1)));   // as jacobi_cluster_kernel
+  const double tol2 = tol * tol;
+  const float tolf = (float)tol;
+  double thr = d.thr;
+  if (d.thr_ref) thr *= *d.thr_ref;
+  const double dth = 1e-2 * thr / sqrt((double)max(q2, 1));
+  const double dfl = dth * dth;
+  const long long dfl_bits = __double_as_longlong(dfl);
+
+  for (int j = 0; j < q2; ++j)
+    for (int i = threadIdx.x; i < q1; i += QT) cols[(size_t)j * ldc + i] = M[i + (size_t)j * ldm];
+  for (int j = threadIdx.x; j < q2; j += QT) dsc[j] = 1.0;
+  __syncthreads();
+
+  const int nreg = (q1 + LG - 1) / LG;
+  const bool inreg = nreg <= kJacobiRegs;
+  for (int sweep = 0; sweep <= kMaxSweeps; ++sweep) {
+    // fold the scales into the columns and take exact squared norms
+    for (int j = warp; j < q2; j += QW) {
+      const double s = dsc[j];
+      double v = 0.0;
+      for (int i = lane; i < q1; i += 32) {
+        const double x = cols[(size_t)j * ldc + i] * s;
+        cols[(size_t)j * ldc + i] = x;
+        v = fma(x, x, v);
+      }
+      v = warp_sum2(v);
+      if (lane == 0) {
+        cn[j] = v;
+        d.nrm[j] = v;
+        dsc[j] = 1.0;
+        esc[j] = 1.0;
+      }
+    }
+    __syncthreads();
+    if (sweep == kMaxSweeps || q2 < 2 || q1 == 0) break;
+    if (threadIdx.x == 0) {
+      int c = 0;
+      for (int j = 0; j < q2; ++j)
+        if (cn[j] > dfl) act[c++] = j;
+      nact = c;
+      nrot = 0;
+    }
+    __syncthreads();
+    const int Ka = nact;
+    if (Ka < 2) break;
+    const int P = Ka + (Ka & 1);
+    int local = 0;
+    for (int r = 0; r < P - 1; ++r) {
+      if (r > 0 && r % kFold == 0) {
+        // fold the scales of the active columns (their true norms are tracked unchanged)
+        for (int x = warp; x < Ka; x += QW) {
+          const int j = act[x];
+          const double s = dsc[j];
+          for (int i = lane; i < q1; i += 32) cols[(size_t)j * ldc + i] *= s;
+          __syncwarp();
+          if (lane == 0) {
+            dsc[j] = 1.0;
+            esc[j] = 1.0;
+          }
+        }
+        __syncthreads();
+      }
+      for (int pb = warp * PPW; pb < P / 2; pb += QW * PPW) {
+        const int pi = pb + sub;
+        int ia = 0, ib = 0;
+        bool valid = pi < P / 2;
+        if (valid) {
+          rr_pair(r, pi, P, ia, ib);
+          valid = ia < Ka && ib < Ka;
+        }
+        const int a = valid ? act[ia] : 0, b = valid ? act[ib] : 0;
+        double* xa = cols + (size_t)a * ldc;
+        double* yb = cols + (size_t)b * ldc;
+        const double al = valid ? cn[a] : 0.0, be = valid ? cn[b] : 0.0;
+        const double da = dsc[a], db = dsc[b];
+        double x[kJacobiRegs], y[kJacobiRegs];
+        double g0 = 0.0, g1 = 0.0;
+        if (inreg) {
+#pragma unroll
+          for (int u = 0; u < kJacobiRegs; ++u) {
+            if (u < nreg) {
+              const int i = gl + LG * u;
+              const bool in = valid && i < q1;
+              x[u] = in ? xa[i] : 0.0;
+              y[u] = in ? yb[i] : 0.0;
+              if (u & 1) g1 = fma(x[u], y[u], g1);
+              else g0 = fma(x[u], y[u], g0);
+            }
+          }
+        } else if (valid) {
+          for (int i = gl; i < q1; i += 2 * LG) {
+            g0 = fma(xa[i], yb[i], g0);
+            if (i + LG < q1) g1 = fma(xa[i + LG], yb[i + LG], g1);
+          }
+        }
+        double gw = g0 + g1;
+#pragma unroll
+        for (int o = LG / 2; o > 0; o >>= 1) gw += __shfl_xor_sync(0xffffffffu, gw, o);
+        const double g = da * db * gw;                    // gamma of the true columns
+        double c = 1.0, tt = 0.0;
+        const bool doit = valid && __double_as_longlong(al) > dfl_bits && __double_as_longlong(be) > dfl_bits &&
+                          jacobi_rotation_ct(al, be, g, tol2, tolf, c, tt);
+        if (!doit) {
+          c = 1.0;
+          tt = 0.0;
+        }
+        const double mu = tt * db * esc[a], nu = tt * da * esc[b];
+        const double tg = tt * g;
+        const bool a_shrinks = tg > 0.0;
+        const bool exact = doit && (a_shrinks ? (tg > 0.5 * al) : (-tg > 0.5 * be));
+        const bool any_exact = __any_sync(0xffffffffu, exact);
+        const bool any_doit = __any_sync(0xffffffffu, doit);
+        double s0 = 0.0, s1 = 0.0;
+        if (inreg && any_doit) {
+#pragma unroll
+          for (int u = 0; u < kJacobiRegs; ++u) {
+            if (u < nreg) {
+              const double xn = fma(-mu, y[u], x[u]);
+              const double yn = fma(nu, x[u], y[u]);
+              const int i = gl + LG * u;
+              if (doit && i < q1) {
+                xa[i] = xn;
+                yb[i] = yn;
+              }
+              if (any_exact) {
+                const double v = a_shrinks ? xn : yn;
+                if (u & 1) s1 = fma(v, v, s1);
+                else s0 = fma(v, v, s0);
+              }
+            }
+          }
+        } else if (doit) {
+          for (int i = gl; i < q1; i += LG) {
+            const double xv = xa[i], yv = yb[i];
+            const double xn = fma(-mu, yv, xv);
+            const double yn = fma(nu, xv, yv);
+            xa[i] = xn;
+            yb[i] = yn;
+            const double v = a_shrinks ? xn : yn;
+            s0 = fma(v, v, s0);
+          }
+        }
+        double ss = s0 + s1;
+        if (any_exact) {
+#pragma unroll
+          for (int o = LG / 2; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        }
+        if (doit && gl == 0) {
+          const double dan = c * da, dbn = c * db;
+          const double rc = fma(tt, tt, 1.0) * c;         // 1 / c
+          double na = fma(-tt, g, al), nb = fma(tt, g, be);
+          if (exact) {
+            if (a_shrinks) na = dan * dan * ss;
+            else nb = dbn * dbn * ss;
+          }
+          cn[a] = na;
+          cn[b] = nb;
+          dsc[a] = dan;
+          dsc[b] = dbn;
+          esc[a] *= rc;
+          esc[b] *= rc;
+          ++local;
+        }
+      }
+      __syncthreads();
+    }
+    if (local) atomicAdd(&nrot, local);
+    __syncthreads();
+    if (threadIdx.x == 0) d.rot[sweep] = nrot;
+    if (nrot == 0) sweep = kMaxSweeps - 1;                // converged: final norms next pass
+    __syncthreads();                                      // nrot is read before it is reset
+  }
+  for (int j = 0; j < q2; ++j)
+    for (int i = threadIdx.x; i < q1; i += QT) M[i + (size_t)j * ldm] = cols[(size_t)j * ldc + i];
+}
+
 // Shared memory of the remote-store Jacobi (jacobi_dsmem_impl) for a core of at most q1cap x q2cap.
 __host__ __device__ inline size_t jacobi_dsmem_bytes(int q1cap, int q2cap, int cluster) {
   const size_t nloc = (q2cap + cluster - 1) / cluster;
-  return nloc * (q1cap + 1) * sizeof(double) + (size_t)q2cap * sizeof(double) + (size_t)q2cap * sizeof(int) + 64;
+  return nloc * (q1cap + 3) * sizeof(double) + (size_t)q2cap * sizeof(double) + (size_t)q2cap * sizeof(int) + 64;
 }
 // Shared memory of the owner-computes Jacobi for a core of at most q1cap x q2cap on `cluster` CTAs.
 __host__ __device__ inline size_t jacobi_owner_bytes(int q1cap, int q2cap, int cluster) {
   const size_t nloc = (q2cap + cluster - 1) / cluster;
-  return 2 * nloc * (q1cap + 1) * sizeof(double) + (size_t)q2cap * sizeof(double) +
+  return 2 * nloc * (q1cap + 3) * sizeof(double) + (size_t)q2cap * sizeof(double) +
          ((size_t)q2cap + nloc) * sizeof(int) + 64;
 }
 constexpr int kJacobiSoloCols = 32;   // cores up to this many columns run on one CTA (twice as
@@ -1702,12 +2033,17 @@ constexpr int kJacobiSoloCols = 32;   // cores up to this many columns run on on
 
 // Lane-group width from the actual column length of this cluster's core (ranks are known only
 // on the device; every CTA of the cluster reads the same descriptor, so the choice is uniform).
+// kOwner: the instantiation launched on clusters of 8 or more CTAs for a factorization alone on
+// the GPU, the only launches where the owner-computes form is chosen (each instantiation gets
+// its own register allocation).
+template <bool kOwner>
 __global__ void __launch_bounds__(QT, 2) jacobi_dsmem_kernel(const JacobiDesc* __restrict__ descs,
                                                           int q1cap, int q2cap, int smem_bytes, int solo_cols) {
   // The form is chosen from the core's actual size (every CTA of the cluster reads the same
   // descriptor): one CTA for small cores; on clusters of 8 or more CTAs owner-computes when its
   // two column buffers fit in the shared memory of the launch; else remote-store when one buffer
-  // fits; global memory otherwise.
+  // fits; global memory otherwise (owner-computes needs more shared memory than remote-store,
+  // so it is never the fallback).
   const JacobiDesc& d = descs[blockIdx.y];
   const int* di = d.di;
   double* flops = d.fl;
@@ -1715,30 +2051,19 @@ __global__ void __launch_bounds__(QT, 2) jacobi_dsmem_kernel(const JacobiDesc* _
   const int q2 = min(dimv(d.q2, d.q2ref, di), q2cap);
   const int C = (int)cg::this_cluster().num_blocks();
   const size_t avail = (size_t)smem_bytes;
-  if (q2 <= solo_cols && jacobi_owner_bytes(q1, q2, 1) <= avail) {
+  if (q2 <= solo_cols && jacobi_solo_bytes(q1, q2) <= avail) {
     if (cg::this_cluster().block_rank() != 0) return;
-    if (q1 <= 4 * kJacobiRegs) jacobi_owner_impl<4, true>(descs, di, flops, q1cap, q2cap);
-    else if (q1 <= 8 * kJacobiRegs) jacobi_owner_impl<8, true>(descs, di, flops, q1cap, q2cap);
-    else if (q1 <= 16 * kJacobiRegs) jacobi_owner_impl<16, true>(descs, di, flops, q1cap, q2cap);
-    else jacobi_owner_impl<32, true>(descs, di, flops, q1cap, q2cap);
-  } else if (C >= 8 && jacobi_owner_bytes(q1, q2, C) <= avail) {
+    if (q1 <= 4 * kJacobiRegs) jacobi_solo_impl<4>(descs, di, flops, q1cap, q2cap);
+    else jacobi_solo_impl<8>(descs, di, flops, q1cap, q2cap);
+  } else if (kOwner && C >= 8 && jacobi_owner_bytes(q1, q2, C) <= avail) {
     // owner-computes shortens the round (only loads cross SMs) but computes every pair on both
     // owners: it pays off on large clusters, where a round is latency-bound, not on small ones,
     // where the SM's FP64 issue rate is the limit
     if (q1 <= 4 * kJacobiRegs) jacobi_owner_impl<4, false>(descs, di, flops, q1cap, q2cap);
-    else if (q1 <= 8 * kJacobiRegs) jacobi_owner_impl<8, false>(descs, di, flops, q1cap, q2cap);
-    else if (q1 <= 16 * kJacobiRegs) jacobi_owner_impl<16, false>(descs, di, flops, q1cap, q2cap);
-    else jacobi_owner_impl<32, false>(descs, di, flops, q1cap, q2cap);
+    else jacobi_owner_impl<8, false>(descs, di, flops, q1cap, q2cap);
   } else if (jacobi_dsmem_bytes(q1, q2, C) <= avail) {
     if (q1 <= 4 * kJacobiRegs) jacobi_dsmem_impl<4>(descs, di, flops, q1cap, q2cap);
-    else if (q1 <= 8 * kJacobiRegs) jacobi_dsmem_impl<8>(descs, di, flops, q1cap, q2cap);
-    else if (q1 <= 16 * kJacobiRegs) jacobi_dsmem_impl<16>(descs, di, flops, q1cap, q2cap);
-    else jacobi_dsmem_impl<32>(descs, di, flops, q1cap, q2cap);
-  } else if (jacobi_owner_bytes(q1, q2, C) <= avail) {
-    if (q1 <= 4 * kJacobiRegs) jacobi_owner_impl<4, false>(descs, di, flops, q1cap, q2cap);
-    else if (q1 <= 8 * kJacobiRegs) jacobi_owner_impl<8, false>(descs, di, flops, q1cap, q2cap);
-    else if (q1 <= 16 * kJacobiRegs) jacobi_owner_impl<16, false>(descs, di, flops, q1cap, q2cap);
-    else jacobi_owner_impl<32, false>(descs, di, flops, q1cap, q2cap);
+    else jacobi_dsmem_impl<8>(descs, di, flops, q1cap, q2cap);
   } else {
     jacobi_global_impl(descs, di, flops);
   }
@@ -1761,14 +2086,19 @@ cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, int cluster
   // Cluster size for this launch: enough CTAs that each has about two warps of pair groups per
   // round (more CTAs only add barrier cost: a round is one dependent chain per pair), at most
   // the context's size, and enough that the columns fit in shared memory.
-  const int ppw = q1cap <= 4 * kJacobiRegs ? 8 : (q1cap <= 8 * kJacobiRegs ? 4 : (q1cap <= 16 * kJacobiRegs ? 2 : 1));
+  const int ppw = q1cap <= 4 * kJacobiRegs ? 8 : 4;     // pairs per warp (lane groups of 4 or 8)
   const int pairs = (q2cap + 1) / 2;
   cluster = max(1, min(cluster, (pairs + 2 * ppw - 1) / (2 * ppw)));
   // a core whose columns do not fit the context's cluster in distributed shared memory grows
-  // the cluster, up to the context's size for large problems, instead of falling back to the
-  // global-memory form; small actual cores still run on one CTA of it (the others exit)
+  // the cluster, up to the context's size for large problems and, for a factorization alone on
+  // the GPU, at least to 8 CTAs (the portable limit), instead of falling back to the
+  // global-memory form, which costs more than twice the FP64 instructions per rotation; small
+  // actual cores still run on one CTA of it (the others exit).  While factorizations share the
+  // SMs the larger clusters cost more than they save (measured on the batched n = 8192
+  // workload: 54.7 against 62.9 factorizations/s).
   const size_t jcap = std::min(kJacobiSmemMax, smem_cap);
-  const int jmax = std::max(cluster_max, cluster_large);
+  const int jgrow = smem_cap >= kJacobiSmemMax ? std::min(8, qr_max_cluster()) : 0;
+  const int jmax = std::max(std::max(cluster_max, cluster_large), jgrow);
   while (cluster < jmax && jacobi_dsmem_bytes(q1cap, q2cap, cluster) > jcap) ++cluster;
   const size_t smem = jacobi_dsmem_bytes(q1cap, q2cap, cluster);
   cudaLaunchConfig_t cfg = {};
@@ -1790,7 +2120,12 @@ cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, int cluster
     // cores of at most this many columns run on one CTA; more of them while other factorizations
     // share the SMs (throughput over latency)
     const int solo = smem_cap < kJacobiSmemMax ? 2 * kJacobiSoloCols : kJacobiSoloCols;
-    return cudaLaunchKernelEx(&cfg, jacobi_dsmem_kernel, (const JacobiDesc*)d, q1cap, q2cap,
+    // owner-computes (every pair formed on both owners) only for a factorization alone on the
+    // GPU: with several in flight the FP64 issue rate, not the round's latency, is the limit
+    if (cluster >= 8 && smem_cap >= kJacobiSmemMax)
+      return cudaLaunchKernelEx(&cfg, jacobi_dsmem_kernel<true>, (const JacobiDesc*)d, q1cap, q2cap,
+                                (int)smem2, solo);
+    return cudaLaunchKernelEx(&cfg, jacobi_dsmem_kernel<false>, (const JacobiDesc*)d, q1cap, q2cap,
                               (int)smem2, solo);
   }
   return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel, (const JacobiDesc*)d);

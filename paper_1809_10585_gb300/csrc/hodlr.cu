@@ -795,6 +795,210 @@ struct Planner {
     }
   }
 
+  // ------------------------------------------- rectangular HODLR and the permuted QR (Sec. 6)
+  // Row blocks moved by a row permutation: rows src .. src + len - 1 of the source go to rows
+  // dst .. dst + len - 1 of the destination (inverse: the other way round).
+  struct RowSeg {
+    int src, dst, len;
+  };
+  void copy_rows(const double* S, int lds, double* D, int ldd, int cols, const std::vector<RowSeg>& segs,
+                 bool inverse) {
+    std::vector<CopyDesc> cps;
+    for (const auto& g : segs) {
+      if (g.len <= 0 || cols <= 0) continue;
+      CopyDesc c = {};
+      c.src = S + (inverse ? g.dst : g.src); c.lds = lds;
+      c.dst = D + (inverse ? g.src : g.dst); c.ldd = ldd;
+      c.rows = g.len; c.rows_src = g.len; c.rows_src_ref = -1; c.cols = cols; c.colsref = -1; c.alpha = 1.0;
+      cps.push_back(c);
+    }
+    if (!cps.empty()) rec(R_COPY, (int)cps.size(), put(cps));
+  }
+
+  // Householder QR of the dense h x w matrix W (h >= w) in place, in the LAPACK layout (R on and
+  // above the diagonal, the unit lower trapezoidal Y below it), with the w x w upper T of the
+  // compact WY form (Alg. 1 blocked by panels of kRectNB columns): each panel is factored by
+  // the cluster QR kernel (its own T block), the columns to its right are updated with
+  // Q_p^T = I - Y_p T_p^T Y_p^T by three GEMMs, and the off-diagonal blocks of T are formed
+  // afterwards by T(0:j0, panel) = -T(0:j0, 0:j0) (Y(:, 0:j0)^T Y_p) T_p (Sec. 3, Eq. (10)).
+  static constexpr int kRectNB = 64;
+  void dense_qr(double* W, int ldw, int h, int w, double* T, int ldt, double* tau) {
+    const int nb = kRectNB;
+    double* G = alloc<double>((size_t)nb * nb);
+    double* X = alloc<double>((size_t)nb * w);
+    double* X2 = alloc<double>((size_t)nb * w);
+    {
+      CopyDesc z = {};                                     // T starts at zero (upper part written)
+      z.src = nullptr; z.dst = T; z.ldd = ldt; z.rows = w; z.rows_src = 0; z.rows_src_ref = -1;
+      z.cols = w; z.colsref = -1;
+      rec(R_COPY, 1, put(std::vector<CopyDesc>{z}));
+    }
+    for (int j0 = 0; j0 < w; j0 += nb) {
+      const int nbp = std::min(nb, w - j0), rest = w - j0 - nbp, hp = h - j0;
+      double* Yp = W + j0 + (size_t)j0 * ldw;
+      double* Tp = T + j0 + (size_t)j0 * ldt;
+      QRDesc q = {};
+      q.A = Yp; q.lda = ldw; q.h = hp; q.w = nbp; q.href = -1; q.wref = -1; q.tau = tau + j0;
+      q.T = Tp; q.ldt = ldt; q.G = G; q.ldg = nb; q.step = kStepNone; q.fmode = 0;
+      rec(R_QR, 1, put(std::vector<QRDesc>{q}));
+      if (rest == 0) continue;
+      double* Cp = W + j0 + (size_t)(j0 + nbp) * ldw;
+      gemm({gd(Yp, ldw, 1, kMaskUnitLower, Cp, ldw, 0, 0, X, nb, nbp, -1, rest, -1, hp, -1, 1.0, 0.0, kStepNone, -1)});
+      gemm({gd(Tp, ldt, 1, kMaskUpper, X, nb, 0, 0, X2, nb, nbp, -1, rest, -1, nbp, -1, 1.0, 0.0, kStepNone, -1)});
+      gemm({gd(Yp, ldw, 0, kMaskUnitLower, X2, nb, 0, 0, Cp, ldw, hp, -1, rest, -1, nbp, -1, -1.0, 1.0, kStepNone, -1)});
+    }
+    if (w <= nb) return;
+    // Y(:, 0:j0)^T Y_p for every later panel at once (rows above j0 of Y_p are zero)
+    double* Gx = alloc<double>((size_t)w * w);
+    std::vector<GemmDesc> gg;
+    for (int j0 = nb; j0 < w; j0 += nb) {
+      const int nbp = std::min(nb, w - j0);
+      gg.push_back(gd(W + j0, ldw, 1, 0, W + j0 + (size_t)j0 * ldw, ldw, 0, kMaskUnitLower, Gx + (size_t)j0 * w, w,
+                      j0, -1, nbp, -1, h - j0, -1, 1.0, 0.0, kStepNone, -1));
+    }
+    gemm(gg);
+    double* Xt = alloc<double>((size_t)w * nb);
+    for (int j0 = nb; j0 < w; j0 += nb) {                 // in order: each needs T(0:j0, 0:j0)
+      const int nbp = std::min(nb, w - j0);
+      gemm({gd(T, ldt, 0, kMaskUpper, Gx + (size_t)j0 * w, w, 0, 0, Xt, w, j0, -1, nbp, -1, j0, -1, 1.0, 0.0,
+               kStepNone, -1)});
+      gemm({gd(Xt, w, 0, 0, T + j0 + (size_t)j0 * ldt, ldt, 0, kMaskUpper, T + (size_t)j0 * ldt, ldt, j0, -1, nbp,
+               -1, nbp, -1, -1.0, 0.0, kStepNone, -1)});
+    }
+  }
+
+  // ||A||_2 of a dense m x n matrix by power iteration on A^T A from the normalized all-ones
+  // vector (the reading used for HODLR matrices), written to *out.
+  void dense_norm2(const double* A, int lda, int m, int n, double* out, int iters) {
+    double* x = alloc<double>(n);
+    double* z = alloc<double>(m);
+    fill(x, n, 1.0 / std::sqrt((double)n));
+    for (int it = 0; it < iters; ++it) {
+      gemm({gd(A, lda, 0, 0, x, n, 0, 0, z, m, m, -1, 1, -1, n, -1, 1.0, 0.0, kStepNone, -1)});
+      gemm({gd(A, lda, 1, 0, z, m, 0, 0, x, n, n, -1, 1, -1, m, -1, 1.0, 0.0, kStepNone, -1)});
+      norm(x, n, out, true);
+    }
+    gemm({gd(A, lda, 0, 0, x, n, 0, 0, z, m, m, -1, 1, -1, n, -1, 1.0, 0.0, kStepNone, -1)});
+    norm(z, m, out, false);
+  }
+
+  // Rectangular HODLR approximation (Sec. 2.1.1 on a row and a column partition) of the dense
+  // matrix A, as compress_dense: leaves copied, every off-diagonal block sampled by the
+  // randomized range finder and truncated by T_eps at thr (times *thr_ref when given).  rr / cr:
+  // row / column range of every heap-ordered node; the factors go to the matrix's U12, V12, U21,
+  // V21 (ranks in its rank table), leaf j to leaf[j] (ld = its rows).
+  void compress_rect(const double* A, int lda, const std::vector<std::pair<int, int>>& rr,
+                     const std::vector<std::pair<int, int>>& cr, const std::vector<double*>& leaf, double thr,
+                     const double* thr_ref, unsigned long long seed) {
+    const int kc = M->kc, nleaf = M->nleaf;
+    std::vector<CopyDesc> cps;
+    for (int j = 0; j < nleaf; ++j) {
+      const int v = nleaf - 1 + j, mr = rr[v].second - rr[v].first, nc = cr[v].second - cr[v].first;
+      CopyDesc cp = {};
+      cp.src = A + rr[v].first + (size_t)cr[v].first * lda; cp.lds = lda;
+      cp.dst = leaf[j]; cp.ldd = std::max(mr, 1);
+      cp.rows = mr; cp.rows_src = mr; cp.rows_src_ref = -1; cp.cols = nc; cp.colsref = -1; cp.alpha = 1.0;
+      cps.push_back(cp);
+    }
+    rec(R_COPY, (int)cps.size(), put(cps));
+    for (int l = 0; l < M->levels; ++l) {
+      size_t mk = mark();
+      std::vector<QRDesc> qds;
+      std::vector<GemmDesc> gY, gP2, gP3, gQ, gZ;
+      std::vector<Trunc> ts;
+      std::vector<Rec> pre;
+      std::vector<SmallDesc> idents;
+      for (int v = (1 << l) - 1; v < (2 << l) - 1; ++v) {
+        for (int which = 0; which < 2; ++which) {
+          const int a = which == 0 ? 2 * v + 1 : 2 * v + 2, b = which == 0 ? 2 * v + 2 : 2 * v + 1;
+          const int rlo = rr[a].first, clo = cr[b].first;
+          const int m = rr[a].second - rr[a].first, q = cr[b].second - cr[b].first;
+          const int p = std::min(std::min(kc + 16, m), q);
+          if (m == 0 || q == 0 || p == 0) continue;
+          const double* B = A + rlo + (size_t)clo * lda;
+          double* Om = alloc<double>((size_t)q * p);
+          double* Y = alloc<double>((size_t)m * p);
+          double* tau = alloc<double>(p);
+          double* T = alloc<double>((size_t)p * p);
+          double* G = alloc<double>((size_t)p * p);
+          double* Q = alloc<double>((size_t)m * p);
+          double* P2 = alloc<double>((size_t)p * p);
+          double* P3 = alloc<double>((size_t)p * p);
+          double* Z = alloc<double>((size_t)q * p);
+          const unsigned long long stream = seed * (unsigned long long)(2 * M->nn + 2) + 2 * v + which;
+          Rec g = {};
+          g.type = R_GAUSS; g.p0 = Om; g.cnt = (size_t)q * p;
+          g.i0 = (int)(unsigned)(stream & 0xffffffffull); g.i1 = (int)(unsigned)(stream >> 32);
+          pre.push_back(g);
+          SmallDesc sd = {};
+          sd.kind = kSmallIdent; sd.p = Q; sd.ld = m; sd.rows = m; sd.cols = p;
+          idents.push_back(sd);
+          gY.push_back(gd(B, lda, 0, 0, Om, q, 0, 0, Y, m, m, -1, p, -1, q, -1, 1.0, 0.0, kStepNone, -1));
+          QRDesc qd = {};
+          qd.A = Y; qd.lda = m; qd.h = m; qd.w = p; qd.href = -1; qd.wref = -1; qd.tau = tau; qd.T = T;
+          qd.ldt = p; qd.G = G; qd.ldg = p; qd.step = kStepNone; qd.fmode = 1;
+          qds.push_back(qd);
+          gP2.push_back(gd(Y, m, 1, kMaskUnitLower, Q, m, 0, 0, P2, p, p, -1, p, -1, p, -1, 1.0, 0.0, kStepNone, -1));
+          gP3.push_back(gd(T, p, 0, kMaskUpper, P2, p, 0, 0, P3, p, p, -1, p, -1, p, -1, 1.0, 0.0, kStepNone, -1));
+          gQ.push_back(gd(Y, m, 0, kMaskUnitLower, P3, p, 0, 0, Q, m, m, -1, p, -1, p, -1, -1.0, 1.0, kStepNone, -1));
+          gZ.push_back(gd(B, lda, 1, 0, Q, m, 0, 0, Z, q, q, -1, p, -1, m, -1, 1.0, 0.0, kStepNone, -1));
+          Trunc t;
+          t.nL = m; t.nR = q;
+          t.L.push_back(seg(Q, m, p, -1, 1.0));
+          t.R.push_back(seg(Z, q, p, -1, 1.0));
+          t.thr = thr; t.thr_ref = thr_ref;
+          t.Uout = which == 0 ? M->U12[v] : M->U21[v]; t.ldu = m;
+          t.Vout = which == 0 ? M->V12[v] : M->V21[v]; t.ldv = q;
+          t.kout_ref = which == 0 ? r12(v) : r21(v);
+          t.step = kStepNone;
+          ts.push_back(t);
+        }
+      }
+      for (auto& r : pre) push(r);
+      if (!idents.empty()) rec(R_SMALL, (int)idents.size(), put(idents));
+      gemm(gY);
+      if (!qds.empty()) rec(R_QR, (int)qds.size(), put(qds));
+      gemm(gP2);
+      gemm(gP3);
+      gemm(gQ);
+      gemm(gZ);
+      truncate(ts);
+      release(mk);
+    }
+  }
+
+  // Dense m x n matrix (ld) of a rectangular HODLR matrix: leaves copied, every off-diagonal
+  // block formed as U V^T at its stored rank.
+  void rect_to_dense(const std::vector<std::pair<int, int>>& rr, const std::vector<std::pair<int, int>>& cr,
+                     const std::vector<double*>& leaf, double* out, int ld) {
+    const int nleaf = M->nleaf, kc = M->kc;
+    std::vector<CopyDesc> cps;
+    for (int j = 0; j < nleaf; ++j) {
+      const int v = nleaf - 1 + j, mr = rr[v].second - rr[v].first, nc = cr[v].second - cr[v].first;
+      CopyDesc cp = {};
+      cp.src = leaf[j]; cp.lds = std::max(mr, 1);
+      cp.dst = out + rr[v].first + (size_t)cr[v].first * ld; cp.ldd = ld;
+      cp.rows = mr; cp.rows_src = mr; cp.rows_src_ref = -1; cp.cols = nc; cp.colsref = -1; cp.alpha = 1.0;
+      cps.push_back(cp);
+    }
+    rec(R_COPY, (int)cps.size(), put(cps));
+    std::vector<GemmDesc> g;
+    for (int v = 0; v < M->nn; ++v) {
+      for (int which = 0; which < 2; ++which) {
+        const int a = which == 0 ? 2 * v + 1 : 2 * v + 2, b = which == 0 ? 2 * v + 2 : 2 * v + 1;
+        const int m = rr[a].second - rr[a].first, q = cr[b].second - cr[b].first;
+        if (m == 0 || q == 0) continue;
+        double* C = out + rr[a].first + (size_t)cr[b].first * ld;
+        const double* U = which == 0 ? M->U12[v] : M->U21[v];
+        const double* V = which == 0 ? M->V12[v] : M->V21[v];
+        // C = U V^T at the stored rank (k = 0 writes zeros)
+        g.push_back(gd(U, m, 0, 0, V, q, 1, 0, C, ld, m, -1, q, -1, kc, which == 0 ? r12(v) : r21(v), 1.0, 0.0,
+                       kStepNone, -1));
+      }
+    }
+    gemm(g);
+  }
+
   // --------------------------------------------------------- left-orthogonal form (Sec. 2.1)
   void left_orth(int p) {
     size_t mk = mark();
@@ -2577,6 +2781,295 @@ int hodlr_stats(hodlr_ctx* ctx, const hodlr_mat* A, int* max_rank_Y, int* max_ra
   if (max_rank_T) *max_rank_T = mt;
   if (bytes) *bytes = A->store_doubles * sizeof(double) + sizeof(int) * 3 * A->nn;
   return HODLR_OK;
+}
+
+}  // extern "C"
+
+// ============================================= rectangular HODLR and the permuted QR (Sec. 6)
+// A rectangular HODLR matrix on the device: a shell hodlr_mat owns the storage (leaves, factors
+// at the rank capacity, rank table, status, scratch arenas) and the two partitions give the row
+// and column range of every heap-ordered node.
+struct hodlr_rect {
+  hodlr_mat* S = nullptr;
+  int m = 0, n = 0;
+  std::vector<int> m_sizes, n_sizes;
+  std::vector<std::pair<int, int>> rr, cr;
+  std::vector<double*> leaf;
+};
+
+namespace {
+
+// Node ranges of a partition (heap order), or empty when it is not a power-of-two partition of
+// positive sizes.
+std::vector<std::pair<int, int>> node_ranges_of(int nleaf, const int* sizes) {
+  std::vector<std::pair<int, int>> r;
+  if (nleaf < 1 || (nleaf & (nleaf - 1)) || !sizes) return r;
+  r.assign(2 * nleaf - 1, {0, 0});
+  int off = 0;
+  for (int j = 0; j < nleaf; ++j) {
+    if (sizes[j] < 1) return {};
+    r[nleaf - 1 + j] = {off, off + sizes[j]};
+    off += sizes[j];
+  }
+  for (int v = nleaf - 2; v >= 0; --v) r[v] = {r[2 * v + 1].first, r[2 * v + 2].second};
+  return r;
+}
+
+// A shell matrix for plans that are not one square HODLR matrix: rank table (2 (nleaf - 1)
+// ranks followed by the planner's integer slots), status, scalars; no storage.
+int make_shell(hodlr_ctx* ctx, int n, int nleaf, int kc, hodlr_mat** out) {
+  hodlr_mat* M = new (std::nothrow) hodlr_mat();
+  if (!M) return HODLR_ENOMEM;
+  M->mem = ctx->mem;
+  M->n = n; M->nleaf = nleaf; M->nn = nleaf - 1; M->kc = kc; M->ldl = 1;
+  int lv = 0;
+  while ((1 << lv) < nleaf) ++lv;
+  M->levels = lv;
+  M->n_devints = 3 * M->nn + 16 * (2 * M->nn + 1) + 64;
+  if (mat_alloc(M, &M->devints, sizeof(int) * M->n_devints) != HODLR_OK ||
+      mat_alloc(M, &M->dscal, sizeof(double) * 32) != HODLR_OK || mat_alloc(M, &M->dstatus, sizeof(int) * 4) != HODLR_OK) {
+    hodlr_free(M);
+    return HODLR_ENOMEM;
+  }
+  cudaMemsetAsync(M->devints, 0, sizeof(int) * M->n_devints, ctx->s);
+  cudaMemsetAsync(M->dscal, 0, sizeof(double) * 32, ctx->s);
+  cudaMemsetAsync(M->dstatus, 0, sizeof(int) * 4, ctx->s);
+  *out = M;
+  return HODLR_OK;
+}
+
+// Row blocks of the permutation of Sec. 6: the first n_j rows of every row block j, in order,
+// then the remaining rows of every block.
+std::vector<Planner::RowSeg> perm_segments(int nleaf, const int* m_sizes, const int* n_sizes) {
+  std::vector<Planner::RowSeg> segs;
+  int src = 0, dst = 0;
+  for (int j = 0; j < nleaf; ++j) {
+    segs.push_back({src, dst, n_sizes[j]});
+    dst += n_sizes[j];
+    src += m_sizes[j];
+  }
+  src = 0;
+  for (int j = 0; j < nleaf; ++j) {
+    segs.push_back({src + n_sizes[j], dst, m_sizes[j] - n_sizes[j]});
+    dst += m_sizes[j] - n_sizes[j];
+    src += m_sizes[j];
+  }
+  return segs;
+}
+
+bool rect_args_ok(int m, int n, int nleaf, const int* m_sizes, const int* n_sizes) {
+  if (m < 1 || n < 1 || nleaf < 1 || (nleaf & (nleaf - 1)) || !m_sizes || !n_sizes) return false;
+  long sm = 0, sn = 0;
+  for (int j = 0; j < nleaf; ++j) {
+    if (n_sizes[j] < 1 || m_sizes[j] < n_sizes[j]) return false;
+    sm += m_sizes[j];
+    sn += n_sizes[j];
+  }
+  return sm == m && sn == n;
+}
+
+// Dense permuted QR on the shell S: A (m x n, lda) is copied in permuted row order to W
+// (m x n, scratch of S), factored there, and written back to A in the original row order; T
+// (n x n, ldt).  anorm_out (device, may be null): ||A||_2 by power iteration, taken first.
+int plan_permuted_qr(hodlr_ctx* ctx, hodlr_mat* S, int m, int n, int nleaf, const int* m_sizes, const int* n_sizes,
+                     double* A, int lda, double* T, int ldt, double* W, double* anorm_out, double* Ysplit,
+                     double* Rsplit) {
+  const auto segs = perm_segments(nleaf, m_sizes, n_sizes);
+  Plan P;
+  int rc = build_plan(S, P, ctx->cluster, 0.0, [&](Planner& pl) {
+    if (anorm_out) pl.dense_norm2(A, lda, m, n, anorm_out, 30);
+    pl.copy_rows(A, lda, W, m, n, segs, false);
+    double* tau = pl.alloc<double>(n);
+    pl.dense_qr(W, m, m, n, T, ldt, tau);
+    if (Ysplit && Rsplit) {
+      // unit lower trapezoidal Y~ and upper R~ in the permuted order, then both back to the
+      // original row order (Y = P^T Y~, R = P^T [R~; 0])
+      double* Yt = pl.alloc<double>((size_t)m * n);
+      double* Rt = pl.alloc<double>((size_t)m * n);
+      SmallDesc a = {}, b = {};
+      a.kind = kSmallTri; a.p = W; a.ld = m; a.out = Yt; a.cnt = m; a.rows = m; a.cols = n; a.scale = 0;
+      b = a; b.out = Rt; b.scale = 1;
+      pl.rec(R_SMALL, 2, pl.put(std::vector<SmallDesc>{a, b}));
+      pl.copy_rows(Yt, m, Ysplit, m, n, segs, true);
+      pl.copy_rows(Rt, m, Rsplit, m, n, segs, true);
+    } else {
+      pl.copy_rows(W, m, A, lda, n, segs, true);
+    }
+  });
+  if (rc) {
+    free_plan(S, P);
+    return rc;
+  }
+  return run_temp_plan(ctx, S, P);
+}
+
+int new_rect(hodlr_ctx* ctx, int m, int n, int nleaf, const int* m_sizes, const int* n_sizes, int kc, hodlr_rect** out) {
+  hodlr_rect* R = new (std::nothrow) hodlr_rect();
+  if (!R) return HODLR_ENOMEM;
+  R->m = m; R->n = n;
+  R->m_sizes.assign(m_sizes, m_sizes + nleaf);
+  R->n_sizes.assign(n_sizes, n_sizes + nleaf);
+  R->rr = node_ranges_of(nleaf, m_sizes);
+  R->cr = node_ranges_of(nleaf, n_sizes);
+  int rc = make_shell(ctx, std::max(m, n), nleaf, kc, &R->S);
+  if (rc) {
+    delete R;
+    return rc;
+  }
+  hodlr_mat* S = R->S;
+  S->U12.assign(S->nn, nullptr); S->V12.assign(S->nn, nullptr); S->U21.assign(S->nn, nullptr); S->V21.assign(S->nn, nullptr);
+  auto fail = [&]() {
+    hodlr_free(S);
+    delete R;
+    return HODLR_ENOMEM;
+  };
+  for (int j = 0; j < nleaf; ++j) {
+    double* p = nullptr;
+    if (mat_alloc(S, &p, sizeof(double) * (size_t)m_sizes[j] * n_sizes[j]) != HODLR_OK) return fail();
+    R->leaf.push_back(p);
+  }
+  for (int v = 0; v < S->nn; ++v) {
+    const int a = 2 * v + 1, b = 2 * v + 2;
+    const size_t ma = R->rr[a].second - R->rr[a].first, mb = R->rr[b].second - R->rr[b].first;
+    const size_t na = R->cr[a].second - R->cr[a].first, nb = R->cr[b].second - R->cr[b].first;
+    if (mat_alloc(S, &S->U12[v], sizeof(double) * ma * kc) != HODLR_OK ||
+        mat_alloc(S, &S->V12[v], sizeof(double) * nb * kc) != HODLR_OK ||
+        mat_alloc(S, &S->U21[v], sizeof(double) * mb * kc) != HODLR_OK ||
+        mat_alloc(S, &S->V21[v], sizeof(double) * na * kc) != HODLR_OK)
+      return fail();
+  }
+  *out = R;
+  return HODLR_OK;
+}
+
+// Compress the dense A (device, lda) into R at thr (times *thr_ref when given); HODLR_ERANK
+// when a block needs more than the rank capacity.
+int rect_compress_into(hodlr_ctx* ctx, hodlr_rect* R, const double* A, int lda, double thr, const double* thr_ref,
+                       unsigned long long seed) {
+  int rc = temp_plan(ctx, R->S, [&](Planner& pl) { pl.compress_rect(A, lda, R->rr, R->cr, R->leaf, thr, thr_ref, seed); });
+  if (rc) return rc;
+  int st = 0;
+  if (cudaMemcpy(&st, R->S->dstatus, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return HODLR_ECUDA;
+  return st == HODLR_ERANK ? HODLR_ERANK : HODLR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hodlr_permuted_qr(hodlr_ctx* ctx, int m, int n, int nleaf, const int* m_sizes, const int* n_sizes, double* A_dev,
+                      int lda, double* T_dev, int ldt) {
+  if (!ctx || !A_dev || !T_dev || !rect_args_ok(m, n, nleaf, m_sizes, n_sizes) || lda < m || ldt < n)
+    return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  hodlr_mat* S = nullptr;
+  int rc = make_shell(ctx, m, 1, 1, &S);
+  if (rc) return rc;
+  double* W = nullptr;
+  if (mat_alloc(S, &W, sizeof(double) * (size_t)m * n) != HODLR_OK) rc = HODLR_ENOMEM;
+  if (!rc) rc = plan_permuted_qr(ctx, S, m, n, nleaf, m_sizes, n_sizes, A_dev, lda, T_dev, ldt, W, nullptr, nullptr, nullptr);
+  hodlr_free(S);
+  return rc;
+}
+
+int hodlr_rect_compress(hodlr_ctx* ctx, int m, int n, int nleaf, const int* m_sizes, const int* n_sizes,
+                        const double* A_dev, int lda, double thr, int rank_cap, unsigned long long seed, hodlr_rect** out) {
+  if (!ctx || !out || !A_dev || lda < m || !(thr >= 0) || rank_cap < 1 || rank_cap > 256) return HODLR_EINVAL;
+  // the compression itself needs no m_j >= n_j; it needs two power-of-two partitions
+  if (m < 1 || n < 1 || nleaf < 1 || (nleaf & (nleaf - 1)) || node_ranges_of(nleaf, m_sizes).empty() ||
+      node_ranges_of(nleaf, n_sizes).empty() || node_ranges_of(nleaf, m_sizes)[0].second != m ||
+      node_ranges_of(nleaf, n_sizes)[0].second != n)
+    return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  hodlr_rect* R = nullptr;
+  int rc = new_rect(ctx, m, n, nleaf, m_sizes, n_sizes, rank_cap, &R);
+  if (rc) return rc;
+  rc = rect_compress_into(ctx, R, A_dev, lda, thr, nullptr, seed);
+  if (rc && rc != HODLR_ERANK) {
+    hodlr_rect_free(R);
+    return rc;
+  }
+  *out = R;
+  return rc;
+}
+
+int hodlr_rect_qr(hodlr_ctx* ctx, int m, int n, int nleaf, const int* m_sizes, const int* n_sizes,
+                  const double* A_dev, int lda, double tol, double anorm, int rank_cap, unsigned long long seed,
+                  hodlr_rect** Y, hodlr_rect** T, hodlr_rect** R, double* anorm_used) {
+  if (!ctx || !A_dev || !Y || !T || !R || !rect_args_ok(m, n, nleaf, m_sizes, n_sizes) || lda < m || !(tol >= 0) ||
+      rank_cap < 1 || rank_cap > 256)
+    return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  *Y = *T = *R = nullptr;
+  hodlr_mat* S = nullptr;
+  int rc = make_shell(ctx, m, 1, 1, &S);
+  if (rc) return rc;
+  // dense factors, in the original row order, kept until the three compressions are done
+  double *A = nullptr, *W = nullptr, *Td = nullptr, *Yd = nullptr, *Rd = nullptr;
+  if (mat_alloc(S, &A, sizeof(double) * (size_t)m * n) != HODLR_OK || mat_alloc(S, &W, sizeof(double) * (size_t)m * n) != HODLR_OK ||
+      mat_alloc(S, &Td, sizeof(double) * (size_t)n * n) != HODLR_OK || mat_alloc(S, &Yd, sizeof(double) * (size_t)m * n) != HODLR_OK ||
+      mat_alloc(S, &Rd, sizeof(double) * (size_t)m * n) != HODLR_OK)
+    rc = HODLR_ENOMEM;
+  if (!rc && cudaMemcpy2DAsync(A, sizeof(double) * m, A_dev, sizeof(double) * lda, sizeof(double) * m, n,
+                               cudaMemcpyDeviceToDevice, ctx->s) != cudaSuccess)
+    rc = HODLR_ECUDA;
+  double* dnorm = S->dscal;                                // [0]: ||A||_2 used for R's threshold
+  if (!rc && anorm > 0 && cudaMemcpyAsync(dnorm, &anorm, sizeof(double), cudaMemcpyHostToDevice, ctx->s) != cudaSuccess)
+    rc = HODLR_ECUDA;
+  if (!rc)
+    rc = plan_permuted_qr(ctx, S, m, n, nleaf, m_sizes, n_sizes, A, m, Td, n, W, anorm > 0 ? nullptr : dnorm, Yd, Rd);
+  hodlr_rect *y = nullptr, *t = nullptr, *r = nullptr;
+  int rank_rc = HODLR_OK;
+  if (!rc) rc = new_rect(ctx, m, n, nleaf, m_sizes, n_sizes, rank_cap, &y);
+  if (!rc) rc = new_rect(ctx, n, n, nleaf, n_sizes, n_sizes, rank_cap, &t);
+  if (!rc) rc = new_rect(ctx, m, n, nleaf, m_sizes, n_sizes, rank_cap, &r);
+  // thresholds as in the square case: plain tol for the scale-free Y and T, tol ||A||_2 for R
+  for (int which = 0; which < 3 && !rc; ++which) {
+    const int c = which == 0 ? rect_compress_into(ctx, y, Yd, m, tol, nullptr, seed)
+                 : which == 1 ? rect_compress_into(ctx, t, Td, n, tol, nullptr, seed + 1)
+                              : rect_compress_into(ctx, r, Rd, m, tol, dnorm, seed + 2);
+    if (c == HODLR_ERANK) rank_rc = HODLR_ERANK;
+    else rc = c;
+  }
+  double an = anorm;
+  if (!rc && cudaMemcpy(&an, dnorm, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) rc = HODLR_ECUDA;
+  hodlr_free(S);
+  if (rc) {
+    hodlr_rect_free(y);
+    hodlr_rect_free(t);
+    hodlr_rect_free(r);
+    return rc;
+  }
+  if (anorm_used) *anorm_used = an;
+  *Y = y; *T = t; *R = r;
+  return rank_rc;
+}
+
+int hodlr_rect_to_dense(hodlr_ctx* ctx, const hodlr_rect* Rc, double* out_dev, int ld) {
+  hodlr_rect* R = const_cast<hodlr_rect*>(Rc);
+  if (!ctx || !R || !out_dev || ld < R->m) return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  return temp_plan(ctx, R->S, [&](Planner& pl) { pl.rect_to_dense(R->rr, R->cr, R->leaf, out_dev, ld); });
+}
+
+int hodlr_rect_ranks(hodlr_ctx* ctx, const hodlr_rect* R, int* r12, int* r21) {
+  if (!ctx || !R || !r12 || !r21) return HODLR_EINVAL;
+  HQ_CUDA_OK(cudaSetDevice(ctx->dev));
+  HQ_CUDA_OK(cudaStreamSynchronize(ctx->s));
+  const int nn = R->S->nn;
+  std::vector<int> h(std::max(1, 2 * nn), 0);
+  if (nn) HQ_CUDA_OK(cudaMemcpy(h.data(), R->S->devints, sizeof(int) * 2 * nn, cudaMemcpyDeviceToHost));
+  for (int v = 0; v < nn; ++v) {
+    r12[v] = h[v];
+    r21[v] = h[nn + v];
+  }
+  return HODLR_OK;
+}
+
+void hodlr_rect_free(hodlr_rect* R) {
+  if (!R) return;
+  hodlr_free(R->S);
+  delete R;
 }
 
 }  // extern "C"

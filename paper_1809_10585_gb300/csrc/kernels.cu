@@ -87,8 +87,19 @@ __device__ __forceinline__ void gemm_item(const GemmDesc* __restrict__ descs, in
   if (row0 >= m || col0 >= n) return;   // nothing to compute (partial slots beyond k unused)
   int kchunk = (k + d.ksplit - 1) / d.ksplit;
   kchunk = (kchunk + BK - 1) / BK * BK;
-  const int k0 = split * kchunk;
-  const int k1 = min(k, k0 + kchunk);
+  int k0 = split * kchunk;
+  int k1 = min(k, k0 + kchunk);
+  {
+    // a triangular operand is zero outside a band of k set by the tile's rows (A) or columns
+    // (B): products there are skipped (they would add exact zeros)
+    const int ma0 = min(BM, m - row0), na0 = min(BN, n - col0);
+    const bool lowa = d.mska == kMaskLower || d.mska == kMaskUnitLower;
+    const bool lowb = d.mskb == kMaskLower || d.mskb == kMaskUnitLower;
+    if ((d.mska == kMaskUpper && !d.ta) || (lowa && d.ta)) k0 = max(k0, row0);        // l >= i
+    if ((d.mska == kMaskUpper && d.ta) || (lowa && !d.ta)) k1 = min(k1, row0 + ma0);   // l <= i
+    if ((d.mskb == kMaskUpper && d.tb) || (lowb && !d.tb)) k0 = max(k0, col0);        // l >= j
+    if ((d.mskb == kMaskUpper && !d.tb) || (lowb && d.tb)) k1 = min(k1, col0 + na0);   // l <= j
+  }
 
   // The outputs of this tile that exist (ma x na) are known only on the device; most products
   // here multiply by a block of a few columns, so most tiles are sparse.  GB300 retires one
@@ -535,6 +546,13 @@ __global__ void small_kernel(const SmallDesc* __restrict__ descs) {
       const int i = (int)(e % d.rows), j = (int)(e / d.rows);
       d.p[i + (size_t)j * d.ld] = (i == j) ? 1.0 : 0.0;
     }
+  } else if (d.kind == kSmallTri) {
+    const long long tot = (long long)d.rows * d.cols;
+    for (long long e = t0; e < tot; e += stride) {
+      const int i = (int)(e % d.rows), j = (int)(e / d.rows);
+      const double a = d.p[i + (size_t)j * d.ld];
+      d.out[i + (size_t)j * d.cnt] = d.scale ? (i <= j ? a : 0.0) : (i > j ? a : (i == j ? 1.0 : 0.0));
+    }
   }
 }
 
@@ -542,7 +560,8 @@ cudaError_t launch_small(const SmallDesc* h, int n, SmallDesc* d, cudaStream_t s
   if (n <= 0) return cudaSuccess;
   long long mx = 1;
   for (int i = 0; i < n; ++i)
-    mx = std::max(mx, h[i].kind == kSmallIdent ? (long long)h[i].rows * h[i].cols : h[i].cnt);
+    mx = std::max(mx, (h[i].kind == kSmallIdent || h[i].kind == kSmallTri) ? (long long)h[i].rows * h[i].cols
+                                                                               : h[i].cnt);
   const int gx = (int)std::min<long long>(256, std::max<long long>(1, mx / 1024));
   small_kernel<<<dim3(gx, n), 256, 0, s>>>(d);
   return cudaGetLastError();
