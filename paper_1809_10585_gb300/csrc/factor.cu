@@ -122,14 +122,72 @@ __device__ __forceinline__ T* rmt(cg::cluster_group& cl, T* p, int rank) {
   return SOLO ? p : cl.map_shared_rank(p, rank);
 }
 
+// Sums of acc[0..15] over the 32 lanes of a warp by halving exchanges (after the step with
+// offset o a lane keeps half of its values, summed with the partner's): 16 additions per lane
+// instead of 16 x 5.  Lane l returns the sum of value l >> 1.
+__device__ __forceinline__ double halving_sum16(double acc[16], int lane) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const bool hi = lane & 16;
+    const double send = hi ? acc[q] : acc[q + 8];
+    const double keep = hi ? acc[q + 8] : acc[q];
+    acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const bool hi = lane & 8;
+    const double send = hi ? acc[q] : acc[q + 4];
+    const double keep = hi ? acc[q + 4] : acc[q];
+    acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const bool hi = lane & 4;
+    const double send = hi ? acc[q] : acc[q + 2];
+    const double keep = hi ? acc[q + 2] : acc[q];
+    acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  {
+    const bool hi = lane & 2;
+    const double send = hi ? acc[0] : acc[1];
+    const double keep = hi ? acc[1] : acc[0];
+    acc[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  return acc[0] + __shfl_xor_sync(0xffffffffu, acc[0], 1);
+}
+
+// One TNB x TNB diagonal block of T by the column recurrence of the compact WY form
+// T(0:c, c) = -tau_c T(0:c, 0:c) G(0:c, c), T(c, c) = tau_c (Sec. 3), one warp: g holds
+// G(q, c) = y_q^T y_c for q < c (zeros for columns beyond the block's), tl is tau of column
+// `lane` (0 beyond the block), and lane l receives row l of the block in trow (zeros below the
+// diagonal).  The block's rows stay in registers, so the dependent chain touches no memory.
+__device__ __forceinline__ void t_block_rows(const double (*g)[TNB + 1], double tl, int lane, double trow[TNB]) {
+#pragma unroll
+  for (int c = 0; c < TNB; ++c) trow[c] = 0.0;
+#pragma unroll
+  for (int c = 0; c < TNB; ++c) {
+    const double tc = __shfl_sync(0xffffffffu, tl, c);
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int q = 0; q < c; ++q) {
+      if (q & 1) s1 = fma(trow[q], g[q][c], s1);
+      else s0 = fma(trow[q], g[q][c], s0);
+    }
+    trow[c] = lane < c ? -tc * (s0 + s1) : (lane == c ? tc : 0.0);
+  }
+}
+
 // T of the compact WY form from the Householder vectors stored below the diagonal of A
 // (unit diagonal implied): G = Y^T Y (strictly upper part), 16 x 16 diagonal blocks by the
 // column recurrence T(0:i,i) = -tau_i T(0:i,0:i) G(0:i,i), then T12 = -T1 G12 T2 (Sec. 3, Eq. (10))
 // for blocks of doubling size.  A and tau must be final and visible to every CTA of the cluster.
-// `solo`: one CTA alone (block barriers instead of cluster barriers).  Not a template, so that
-// both forms share the one static staging area.
+// `solo`: one CTA alone (block barriers instead of cluster barriers).  `diag_done`: the
+// diagonal blocks of T are already stored (the blocked form builds them panel by panel), so
+// only G's off-diagonal blocks and the merges remain.  Not a template, so that all forms share
+// the one static staging area.
 __device__ void qr_build_T(const QRDesc& d, const double* A, const size_t lda, const int h, const int kmax,
-                           const int C, const int crank, cg::cluster_group& cl, const bool solo) {
+                           const int C, const int crank, cg::cluster_group& cl, const bool solo,
+                           const bool diag_done = false) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // staging area: 16 x 16 blocks of G per warp for the diagonal blocks, then the two 16 x 32
   // operand tiles of the merges
@@ -156,6 +214,7 @@ __device__ void qr_build_T(const QRDesc& d, const double* A, const size_t lda, c
       while ((long)J * (J + 1) / 2 > p) --J;
       while ((long)(J + 1) * (J + 2) / 2 <= p) ++J;
       const int I = (int)(p - (long)J * (J + 1) / 2);
+      if (diag_done && (I >> 2) == (J >> 2)) continue;   // inside a diagonal block: not needed
       const int i0 = 4 * I, j0 = 4 * J;
       double acc[16];
 #pragma unroll
@@ -174,39 +233,10 @@ __device__ void qr_build_T(const QRDesc& d, const double* A, const size_t lda, c
 #pragma unroll
           for (int v = 0; v < 4; ++v) acc[4 * u + v] = fma(yi[u], yj[v], acc[4 * u + v]);
       }
-      // halving exchanges: after the step with offset o a lane keeps half of its values, summed
-      // with the partner's; at the end lane l holds value (l >> 1) summed over all lanes
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const bool hi = lane & 16;
-        const double send = hi ? acc[q] : acc[q + 8];
-        const double keep = hi ? acc[q + 8] : acc[q];
-        acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const bool hi = lane & 8;
-        const double send = hi ? acc[q] : acc[q + 4];
-        const double keep = hi ? acc[q + 4] : acc[q];
-        acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-      }
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const bool hi = lane & 4;
-        const double send = hi ? acc[q] : acc[q + 2];
-        const double keep = hi ? acc[q + 2] : acc[q];
-        acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-      }
-      {
-        const bool hi = lane & 2;
-        const double send = hi ? acc[0] : acc[1];
-        const double keep = hi ? acc[1] : acc[0];
-        acc[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-      }
-      acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
-      const int q = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+      const double v = halving_sum16(acc, lane);        // lane l: value l >> 1
+      const int q = lane >> 1;
       const int i = i0 + q / 4, jj = j0 + q % 4;
-      if ((lane & 1) == 0 && i < jj && jj < kmax) G[i + (size_t)jj * ldg] = acc[0];
+      if ((lane & 1) == 0 && i < jj && jj < kmax) G[i + (size_t)jj * ldg] = v;
     }
     // zero T's strictly lower part, then diagonal blocks by the column recurrence
     for (long e = (long)crank * QT + threadIdx.x; e < (long)kmax * kmax; e += (long)C * QT) {
@@ -215,7 +245,7 @@ __device__ void qr_build_T(const QRDesc& d, const double* A, const size_t lda, c
     }
   }
   if (solo) __syncthreads(); else cl.sync();
-  {
+  if (!diag_done) {
     // Diagonal 16 x 16 blocks, one warp per block: the block of G is staged in shared memory and
     // lane l keeps row l of the block of T in registers, so the column recurrence runs without
     // global memory in its dependent chain.
@@ -230,20 +260,7 @@ __device__ void qr_build_T(const QRDesc& d, const double* A, const size_t lda, c
       const double tl = lane < nbk ? __ldcg(&d.tau[b0 + lane]) : 0.0;
       __syncwarp();
       double trow[TNB];
-#pragma unroll
-      for (int c = 0; c < TNB; ++c) trow[c] = 0.0;
-#pragma unroll
-      for (int c = 0; c < TNB; ++c) {
-        // T(l, c) = -tau_c sum_{l <= q < c} T(l, q) G(q, c), T(c, c) = tau_c
-        const double tc = __shfl_sync(0xffffffffu, tl, c);
-        double s0 = 0.0, s1 = 0.0;
-#pragma unroll
-        for (int q = 0; q < c; ++q) {
-          if (q & 1) s1 = fma(trow[q], gsm[warp][q][c], s1);
-          else s0 = fma(trow[q], gsm[warp][q][c], s0);
-        }
-        trow[c] = lane < c ? -tc * (s0 + s1) : (lane == c ? tc : 0.0);
-      }
+      t_block_rows(gsm[warp], tl, lane, trow);
       if (lane < nbk) {
 #pragma unroll
         for (int c = 0; c < TNB; ++c)
@@ -767,13 +784,71 @@ __device__ __forceinline__ void qr_dsmem_impl(const QRDesc* __restrict__ descs, 
 // panel p its owner loads the panel into shared memory, factors it there with block barriers
 // only (reflector norms by block reductions, scaled when needed), writes it back and publishes
 // it with one cluster barrier.  Every CTA then holds the panel's reflectors in shared memory
-// (unit lower trapezoidal) and applies them in order to each of its own later columns, one warp
-// per column with the column in registers: a column is read and written once per panel, and
-// the cluster waits once per panel instead of once per column.  T is built afterwards from
-// G = Y^T Y as in the other forms.
+// (unit lower trapezoidal), together with the panel's diagonal block T_p of T (built by the
+// owner from the panel's block of G = Y^T Y before the barrier), and applies
+// Q_p^T = I - Y_p T_p^T Y_p^T to each of its own later columns (Sec. 3, Eq. (10)), one warp per
+// column with the column in registers (qr_apply_panel): a column is read and written once per
+// panel, and the cluster waits once per panel instead of once per column.  The rest of T (the
+// off-diagonal blocks of G and the merges) is built afterwards as in the other forms.
 constexpr int QNB = 16;
 
-__host__ __device__ inline size_t qr_blocked_bytes(int h) { return (size_t)h * QNB * sizeof(double) + 64; }
+// Shared memory of the blocked form: the panel (h x QNB) followed by three TNB x (TNB + 1)
+// staging blocks (the owner's block of G, the owner's T_p, this CTA's copy of T_p).
+constexpr int kQRTBlk = TNB * (TNB + 1);
+__host__ __device__ inline size_t qr_blocked_bytes(int h) {
+  return ((size_t)h * QNB + 3 * kQRTBlk) * sizeof(double) + 64;
+}
+
+// Q_p^T = I - Y_p T_p^T Y_p^T applied to one column a (rows j0 .. h-1) by one warp, the column
+// in NR registers per lane (nq <= NR of them in use): the lane partials of the nbp products
+// Y_p^T a are summed across the warp together (halving_sum16: 16 additions per lane instead of
+// 16 reductions of 5), W = T_p^T (Y_p^T a) is formed on lanes 2j, 2j + 1, and a -= Y_p W.
+template <int NR>
+__device__ __forceinline__ void qr_apply_panel(double* a, int h, int j0, int nq, int nbp, const double* Ys,
+                                               const double (*tq)[TNB + 1], int lane) {
+  double r[NR];
+#pragma unroll
+  for (int u = 0; u < NR; ++u) {
+    const int i = j0 + lane + 32 * u;
+    r[u] = (u < nq && i < h) ? __ldcg(&a[i]) : 0.0;
+  }
+  double acc[QNB];
+#pragma unroll
+  for (int k = 0; k < QNB; ++k) {
+    double t = 0.0;
+    if (k < nbp) {
+      const double* yk = Ys + (size_t)k * h;
+#pragma unroll
+      for (int u = 0; u < NR; ++u) {
+        const int i = j0 + lane + 32 * u;
+        if (u < nq && i < h) t = fma(yk[i], r[u], t);
+      }
+    }
+    acc[k] = t;
+  }
+  const double wv = halving_sum16(acc, lane);
+  const int jq = lane >> 1;
+  double wt = 0.0;
+#pragma unroll
+  for (int k = 0; k < QNB; ++k) wt = fma(tq[k][jq], __shfl_sync(0xffffffffu, wv, 2 * k), wt);
+#pragma unroll
+  for (int k = 0; k < QNB; ++k) {
+    const double wk = __shfl_sync(0xffffffffu, wt, 2 * k);
+    if (k < nbp) {
+      const double* yk = Ys + (size_t)k * h;
+#pragma unroll
+      for (int u = 0; u < NR; ++u) {
+        const int i = j0 + lane + 32 * u;
+        if (u < nq && i < h) r[u] = fma(-wk, yk[i], r[u]);
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < NR; ++u) {
+    const int i = j0 + lane + 32 * u;
+    if (u < nq && i < h) a[i] = r[u];
+  }
+}
 
 __device__ __forceinline__ void qr_blocked_impl(const QRDesc& d, int h, int w, double* flops, double* Ys) {
   cg::cluster_group cl = cg::this_cluster();
@@ -785,6 +860,11 @@ __device__ __forceinline__ void qr_blocked_impl(const QRDesc& d, int h, int w, d
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   __shared__ double red[QW + 1];
   __shared__ double ptau[QNB];
+  // after the panel in the dynamic shared memory (same offsets in every CTA of the cluster)
+  double (*gp)[TNB + 1] = reinterpret_cast<double (*)[TNB + 1]>(Ys + (size_t)h * QNB);   // owner's G block
+  double (*tp)[TNB + 1] = gp + TNB;                      // the owner's T_p (read by every CTA)
+  double (*tq)[TNB + 1] = tp + TNB;                      // this CTA's copy of T_p
+  static_assert(QNB == TNB, "panels and diagonal blocks of T coincide");
 
   if (crank == 0 && tid == 0 && flops && kmax > 0) {
     if (d.step >= 0) {
@@ -877,8 +957,47 @@ __device__ __forceinline__ void qr_blocked_impl(const QRDesc& d, int h, int w, d
         const int r = e % nbp, c = e / nbp;
         if (r <= c) Ys[j0 + r + (size_t)c * h] = (r == c) ? 1.0 : 0.0;
       }
+      __syncthreads();
+      // the panel's block of G (strictly upper; ten 4 x 4 tiles, one warp each), then T_p
+      for (int tile = warp; tile < 10; tile += QW) {
+        int J = 0;
+        while ((J + 1) * (J + 2) / 2 <= tile) ++J;
+        const int I = tile - J * (J + 1) / 2, i0 = 4 * I, c0 = 4 * J;
+        double acc[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+        for (int r = j0 + c0 + lane; r < h; r += 32) {
+          double yi[4], yj[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            yi[u] = i0 + u < nbp ? Ys[r + (size_t)(i0 + u) * h] : 0.0;
+            yj[u] = c0 + u < nbp ? Ys[r + (size_t)(c0 + u) * h] : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[4 * u + v] = fma(yi[u], yj[v], acc[4 * u + v]);
+        }
+        const double v = halving_sum16(acc, lane);
+        const int q = lane >> 1, i = i0 + q / 4, jj = c0 + q % 4;
+        if ((lane & 1) == 0) gp[i][jj] = (i < jj && jj < nbp) ? v : 0.0;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        double trow[TNB];
+        t_block_rows(gp, lane < nbp ? ptau[lane] : 0.0, lane, trow);
+        if (lane < TNB) {
+#pragma unroll
+          for (int c = 0; c < TNB; ++c) tp[lane][c] = trow[c];
+        }
+        if (d.T && lane < nbp) {
+#pragma unroll
+          for (int c = 0; c < TNB; ++c)
+            if (c < nbp && c >= lane) d.T[(j0 + lane) + (size_t)(j0 + c) * d.ldt] = trow[c];
+        }
+      }
     }
-    cl.sync();                                           // panel p and its tau published
+    cl.sync();                                           // panel p, its tau and T_p published
     if (crank != owner) {
       for (int e = tid; e < rows * nbp; e += QT) {
         const int i = j0 + e % rows, c = e / rows;
@@ -886,6 +1005,12 @@ __device__ __forceinline__ void qr_blocked_impl(const QRDesc& d, int h, int w, d
         Ys[i + (size_t)c * h] = i < j0 + c ? 0.0 : (i == j0 + c ? 1.0 : v);
       }
       if (tid < nbp) ptau[tid] = __ldcg(&d.tau[j0 + tid]);
+    }
+    {
+      // T_p from the owner's shared memory; the owner writes it again only for panel p + C,
+      // after the next cluster barrier, which every CTA passes after this copy
+      const double* src = cl.map_shared_rank(&tp[0][0], owner);
+      for (int e = tid; e < TNB * (TNB + 1); e += QT) (&tq[0][0])[e] = src[e];
     }
     __syncthreads();
     // apply the panel's reflectors in order to this CTA's columns beyond the panel
@@ -900,7 +1025,11 @@ __device__ __forceinline__ void qr_blocked_impl(const QRDesc& d, int h, int w, d
       const int q = qfirst + (idx / QNB) * C;             // blocks before the last are full
       const int c = q * QNB + idx % QNB;
       double* a = A + (size_t)c * lda;
-      if (nq <= kQRRegs) {
+      if (nq <= 12) {
+        qr_apply_panel<12>(a, h, j0, nq, nbp, Ys, tq, lane);
+      } else if (nq <= kQRRegs) {
+        // longer columns (h - j0 <= 512): the reflectors one after another, column in registers
+        // (the level-3 form would not fit the register budget)
         double r[kQRRegs];
 #pragma unroll
         for (int u = 0; u < kQRRegs; ++u) {
@@ -947,8 +1076,9 @@ __device__ __forceinline__ void qr_blocked_impl(const QRDesc& d, int h, int w, d
       }
     }
   }
-  // T from G = Y^T Y (starts with a cluster barrier: every column final everywhere)
-  qr_build_T(d, A, lda, h, kmax, C, crank, cl, false);
+  // the rest of T: off-diagonal blocks of G and the merges (starts with a cluster barrier:
+  // every column and every T_p final everywhere)
+  qr_build_T(d, A, lda, h, kmax, C, crank, cl, false, true);
 }
 
 // Bytes of shared memory of the distributed form for an h x w matrix on C CTAs.
@@ -2032,10 +2162,15 @@ constexpr int kJacobiSoloCols = 32;   // cores up to this many columns run on on
                                       // many while factorizations share the SMs)
 
 // Lane-group width from the actual column length of this cluster's core (ranks are known only
-// on the device; every CTA of the cluster reads the same descriptor, so the choice is uniform).
+// on the device; every CTA of the cluster reads the same descriptor, so the choice is uniform):
+// 4 lanes per pair up to 32 rows, else 8, with columns longer than 64 rows streamed from
+// shared memory.  Wider groups would hold longer columns in registers, but the rotation's
+// scalar FP64 work (scales, tangent, cosine: about 18 instructions per group) is shared by the
+// 32 / LG pairs of a warp, and with 32 lanes per pair it costs as much as the rows themselves.
 // kOwner: the instantiation launched on clusters of 8 or more CTAs for a factorization alone on
 // the GPU, the only launches where the owner-computes form is chosen (each instantiation gets
-// its own register allocation).
+// its own register allocation); that form keeps the wider groups, since alone on the GPU the
+// round's latency matters more than its FP64 instructions.
 template <bool kOwner>
 __global__ void __launch_bounds__(QT, 2) jacobi_dsmem_kernel(const JacobiDesc* __restrict__ descs,
                                                           int q1cap, int q2cap, int smem_bytes, int solo_cols) {
@@ -2060,7 +2195,9 @@ __global__ void __launch_bounds__(QT, 2) jacobi_dsmem_kernel(const JacobiDesc* _
     // owners: it pays off on large clusters, where a round is latency-bound, not on small ones,
     // where the SM's FP64 issue rate is the limit
     if (q1 <= 4 * kJacobiRegs) jacobi_owner_impl<4, false>(descs, di, flops, q1cap, q2cap);
-    else jacobi_owner_impl<8, false>(descs, di, flops, q1cap, q2cap);
+    else if (q1 <= 8 * kJacobiRegs) jacobi_owner_impl<8, false>(descs, di, flops, q1cap, q2cap);
+    else if (q1 <= 16 * kJacobiRegs) jacobi_owner_impl<16, false>(descs, di, flops, q1cap, q2cap);
+    else jacobi_owner_impl<32, false>(descs, di, flops, q1cap, q2cap);
   } else if (jacobi_dsmem_bytes(q1, q2, C) <= avail) {
     if (q1 <= 4 * kJacobiRegs) jacobi_dsmem_impl<4>(descs, di, flops, q1cap, q2cap);
     else jacobi_dsmem_impl<8>(descs, di, flops, q1cap, q2cap);
@@ -2086,7 +2223,11 @@ cudaError_t launch_jacobi(const JacobiDesc* h, int n, JacobiDesc* d, int cluster
   // Cluster size for this launch: enough CTAs that each has about two warps of pair groups per
   // round (more CTAs only add barrier cost: a round is one dependent chain per pair), at most
   // the context's size, and enough that the columns fit in shared memory.
-  const int ppw = q1cap <= 4 * kJacobiRegs ? 8 : 4;     // pairs per warp (lane groups of 4 or 8)
+  // pairs per warp: lane groups of 4 or 8 (up to 32 for long columns alone on the GPU, where the
+  // owner-computes form takes them)
+  const bool alone = smem_cap >= kJacobiSmemMax;
+  const int ppw = q1cap <= 4 * kJacobiRegs ? 8
+                  : (q1cap <= 8 * kJacobiRegs || !alone ? 4 : (q1cap <= 16 * kJacobiRegs ? 2 : 1));
   const int pairs = (q2cap + 1) / 2;
   cluster = max(1, min(cluster, (pairs + 2 * ppw - 1) / (2 * ppw)));
   // a core whose columns do not fit the context's cluster in distributed shared memory grows
