@@ -108,7 +108,7 @@ def test_compression_recovers_exact_ranks_and_thr_zero_is_exact():
 def test_example_6_2_reduced_size_matches_table5_in_magnitude():
     """Example 6.2 at m = 2000, n = 1000 (8 leaves instead of 16): rank-one random blocks,
     eps = 1e-10.  The paper reports, at 8000 x 4000, e_orth 2.8e-13, e_acc 1.4e-11, maximal ranks
-    Y 8, T 12, R 8, memory of Y and T 1.6x and of R 1.1x that of A."""
+    Y 8, T 12, Q 12, R 8, memory of Y and T 1.6x, of Q 2.2x and of R 1.1x that of A."""
     g = GOLD["table5_rectangular"]
     inp = W.random_rect_hodlr(2000, 1000, 125, g["k"], seed=0)
     A = W.rect_to_dense(inp)
@@ -121,3 +121,8 @@ def test_example_6_2_reduced_size_matches_table5_in_magnitude():
     mem_yt = (res.Y.storage() + res.T.storage()) / A_h.storage()
     mem_r = res.R.storage() / A_h.storage()
     assert abs(mem_yt - g["memory_vs_A"]["Y_and_T"]) <= 0.3 and abs(mem_r - g["memory_vs_A"]["R"]) <= 0.2
+    # Q = I - Y T Y^T itself, compressed in the square format of the row partition (Table 5's
+    # "Q" columns): larger ranks and memory than Y and T together, as the paper reports
+    Qh = R.compress(res.Q_dense(), inp.m_sizes, inp.m_sizes, g["eps"])
+    assert max(Qh.ranks()) <= g["max_rank"]["Q"]
+    assert abs(Qh.storage() / A_h.storage() - g["memory_vs_A"]["Q"]) <= 0.3
