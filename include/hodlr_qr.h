@@ -433,8 +433,11 @@ int hodlr_dense_qr_noalloc(hodlr_ctx* ctx, int h, int w, double* A_dev, int lda,
  *   rank_cap   : rank capacity of every factorization (as in hodlr_build).
  * Order: first come, first served, except that a solve whose factors are not ready (still being
  * factored, busy with another request, or about to be replaced) lets later requests pass.
- * Requests are progressed by every call on the server (submit, poll, stats); nothing blocks
- * except the upload of a factorization's matrix when it starts.  All device memory of the
+ * Requests are progressed by every call on the server (submit, poll, stats), none of which waits
+ * for the device: every slot has a host worker thread that issues its request (upload, build,
+ * factorization, solve, copy of the solution back), so the device work of requests in
+ * different slots overlaps even though issuing one factorization's launches can block its
+ * issuing thread.  All device memory of the
  * server comes from one pool of hbm_budget + hbm_budget / 8 bytes reserved at creation
  * (hodlr_ctx_set_memory_pool), so requests that come and go never wait for the device.  Calls
  * on one server must not overlap from several threads.
