@@ -437,10 +437,11 @@ int hodlr_dense_qr_noalloc(hodlr_ctx* ctx, int h, int w, double* A_dev, int lda,
  * for the device: every slot has a host worker thread that issues its request (upload, build,
  * factorization, solve, copy of the solution back), so the device work of requests in
  * different slots overlaps even though issuing one factorization's launches can block its
- * issuing thread.  All device memory of the
- * server comes from one pool of hbm_budget + hbm_budget / 8 bytes reserved at creation
- * (hodlr_ctx_set_memory_pool), so requests that come and go never wait for the device.  Calls
- * on one server must not overlap from several threads.
+ * issuing thread.  All device memory of the server comes from one pool of
+ * hbm_budget + hbm_budget / 8 bytes reserved at creation (hodlr_ctx_set_memory_pool), so
+ * requests that come and go never wait for the device.  Calls on one server from several
+ * threads are serialized by the server; hodlr_server_destroy must not overlap any other call,
+ * and waits for the requests on the device to finish.
  */
 typedef struct hodlr_server hodlr_server;
 int hodlr_server_create(int device, int slots, size_t hbm_budget, int rank_cap, hodlr_server** out);
