@@ -184,3 +184,20 @@ def errors(res: RectQRResult, A):
     e_orth = float(np.linalg.norm(Q.T @ Q - np.eye(Q.shape[0]), 2))
     e_acc = float(np.linalg.norm(A - Q @ R, 2))
     return e_orth, e_acc
+
+
+def lstsq(res: RectQRResult, B, m_sizes, n_sizes):
+    """Least-squares solution of min ||A X - B|| from the permuted QR (the use of a QR
+    decomposition the paper's introduction names for rectangular A): with A = Q R and the
+    triangle R~ = R[p[:n]], ||A X - B|| = ||R X - Q^T B||, minimized by R~ X = (Q^T B)[p[:n]];
+    the rows p[n:] of Q^T B are the residual.  Returns (X, residual norms per column)."""
+    import scipy.linalg as sla
+    B = np.asarray(B, dtype=np.float64)
+    if B.ndim == 1:
+        B = B[:, None]
+    Y, T, Rd = res.Y.to_dense(), res.T.to_dense(), res.R.to_dense()
+    QtB = B - Y @ (T.T @ (Y.T @ B))
+    p = row_permutation(m_sizes, n_sizes)
+    n = Rd.shape[1]
+    X = sla.solve_triangular(Rd[p[:n]], QtB[p[:n]], lower=False)
+    return X, np.linalg.norm(QtB[p[n:]], axis=0)

@@ -126,3 +126,26 @@ def test_example_6_2_reduced_size_matches_table5_in_magnitude():
     Qh = R.compress(res.Q_dense(), inp.m_sizes, inp.m_sizes, g["eps"])
     assert max(Qh.ranks()) <= g["max_rank"]["Q"]
     assert abs(Qh.storage() / A_h.storage() - g["memory_vs_A"]["Q"]) <= 0.3
+
+
+def test_least_squares_from_the_permuted_qr():
+    """min ||A X - B|| through the permuted QR: at tol = 0 it equals LAPACK's least-squares
+    solution (scipy lstsq) to rounding times the condition number, with the same residual norm;
+    at tol = 1e-10 the normal-equation residual A^T (A X - B) stays at the truncation level."""
+    inp, A = _inp(m=500, n=200, nmin=30, k=2, seed=11)
+    rng = np.random.default_rng(12)
+    B = rng.standard_normal((A.shape[0], 3))
+    import scipy.linalg as sla
+    Xr, res_r, _, _ = sla.lstsq(A, B)
+    kappa = np.linalg.cond(A)
+    exact = R.rect_qr(A, inp.m_sizes, inp.n_sizes, 0.0)
+    X0, r0 = R.lstsq(exact, B, inp.m_sizes, inp.n_sizes)
+    np.testing.assert_allclose(X0, Xr, atol=1e-13 * kappa * np.abs(Xr).max())
+    np.testing.assert_allclose(r0, np.linalg.norm(A @ Xr - B, axis=0), rtol=1e-10)
+    tol = 1e-10
+    approx = R.rect_qr(A, inp.m_sizes, inp.n_sizes, tol)
+    X1, r1 = R.lstsq(approx, B, inp.m_sizes, inp.n_sizes)
+    an = np.linalg.norm(A, 2)
+    gram = np.linalg.norm(A.T @ (A @ X1 - B), axis=0)
+    assert np.all(gram <= 100 * tol * an * an * np.linalg.norm(X1, axis=0) + 100 * tol * an * np.linalg.norm(B, axis=0))
+    np.testing.assert_allclose(r1, np.linalg.norm(A @ X1 - B, axis=0), rtol=1e-6)
