@@ -380,6 +380,11 @@ int hodlr_truncate(hodlr_ctx* ctx, int nL, int nR, int K, const double* L_dev,
  *   vector (*anorm_used, may be NULL, receives the value).  Outputs three new matrices owned by
  *   the caller (hodlr_rect_free).  HODLR_ERANK (outputs valid) when a compression hit rank_cap.
  *
+ * hodlr_rect_permutation — host only, no device: the row permutation of hodlr_permuted_qr,
+ *   p[i] = the row of A that is row i of P A (the first n_j rows of every row block j in block
+ *   order, then the remaining rows of every block), for the m = sum(m_sizes) entries of p.
+ *   HODLR_EINVAL unless nleaf is a power of two and 1 <= n_j <= m_j for every j.
+ *
  * hodlr_rect_to_dense — the dense m x n matrix of R into out_dev (ld >= m).  hodlr_rect_ranks —
  * the stored ranks of A12 (r12[v]) and A21 (r21[v]) for the nleaf - 1 internal nodes (heap
  * order), synchronous.  hodlr_rect_free — release a matrix (NULL is ignored).
@@ -393,6 +398,7 @@ int hodlr_rect_compress(hodlr_ctx* ctx, int m, int n, int nleaf, const int* m_si
 int hodlr_rect_qr(hodlr_ctx* ctx, int m, int n, int nleaf, const int* m_sizes, const int* n_sizes,
                   const double* A_dev, int lda, double tol, double anorm, int rank_cap, unsigned long long seed,
                   hodlr_rect** Y, hodlr_rect** T, hodlr_rect** R, double* anorm_used);
+int hodlr_rect_permutation(int nleaf, const int* m_sizes, const int* n_sizes, int* p);
 int hodlr_rect_to_dense(hodlr_ctx* ctx, const hodlr_rect* R, double* out_dev, int ld);
 int hodlr_rect_ranks(hodlr_ctx* ctx, const hodlr_rect* R, int* r12, int* r21);
 void hodlr_rect_free(hodlr_rect* R);

@@ -94,6 +94,7 @@ _SIGS = {
                                       C.c_ulonglong, C.POINTER(_VP)]),
     "hodlr_rect_qr": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, _PI, _PI, _VP, C.c_int, C.c_double, C.c_double,
                                 C.c_int, C.c_ulonglong, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), _PD]),
+    "hodlr_rect_permutation": (C.c_int, [C.c_int, _PI, _PI, _PI]),
     "hodlr_rect_to_dense": (C.c_int, [_VP, _VP, _VP, C.c_int]),
     "hodlr_rect_ranks": (C.c_int, [_VP, _VP, _PI, _PI]),
     "hodlr_rect_free": (None, [_VP]),
@@ -437,6 +438,15 @@ def truncate(ctx: Context, nL, nR, K, L_ptr, Rt_ptr, thr, kmax, Lout_ptr, Rout_p
 # ------------------------------------------------------------ rectangular HODLR (Sec. 6)
 def _ints(xs):
     return (C.c_int * len(xs))(*[int(x) for x in xs])
+
+
+def rect_permutation(m_sizes, n_sizes):
+    """Row permutation of the permuted QR (hodlr_rect_permutation, host only): p[i] is the row
+    of A that is row i of P A."""
+    m = int(sum(m_sizes))
+    p = (C.c_int * max(m, 1))()
+    check(lib().hodlr_rect_permutation(len(m_sizes), _ints(m_sizes), _ints(n_sizes), p), "hodlr_rect_permutation")
+    return np.array(p[:m])
 
 
 def permuted_qr(ctx: Context, m_sizes, n_sizes, A_ptr, lda, T_ptr, ldt):

@@ -3045,6 +3045,19 @@ int hodlr_rect_qr(hodlr_ctx* ctx, int m, int n, int nleaf, const int* m_sizes, c
   return rank_rc;
 }
 
+int hodlr_rect_permutation(int nleaf, const int* m_sizes, const int* n_sizes, int* p) {
+  if (!p || nleaf < 1 || !m_sizes || !n_sizes) return HODLR_EINVAL;
+  int m = 0, n = 0;
+  for (int j = 0; j < nleaf; ++j) {
+    m += m_sizes[j];
+    n += n_sizes[j];
+  }
+  if (!rect_args_ok(m, n, nleaf, m_sizes, n_sizes)) return HODLR_EINVAL;
+  for (const auto& g : perm_segments(nleaf, m_sizes, n_sizes))
+    for (int i = 0; i < g.len; ++i) p[g.dst + i] = g.src + i;
+  return HODLR_OK;
+}
+
 int hodlr_rect_to_dense(hodlr_ctx* ctx, const hodlr_rect* Rc, double* out_dev, int ld) {
   hodlr_rect* R = const_cast<hodlr_rect*>(Rc);
   if (!ctx || !R || !out_dev || ld < R->m) return HODLR_EINVAL;

@@ -111,3 +111,24 @@ def test_footprint_rejects_bad_partitions(libpath):
     assert B.lib().hodlr_footprint(201, 2, sizes, 32, 1, 0, 0, C.byref(out)) == B.HODLR_EINVAL   # sum != n
     assert B.lib().hodlr_footprint(200, 2, sizes, 0, 1, 0, 0, C.byref(out)) == B.HODLR_EINVAL    # rank_cap
     assert B.lib().hodlr_footprint(200, 2, sizes, 32, 1, 0, 2000, C.byref(out)) == B.HODLR_EINVAL
+
+
+@pytest.mark.parametrize("m_sizes,n_sizes", [([5, 4, 6, 3], [2, 4, 1, 3]), ([500] * 16, [250] * 16),
+                                             ([7], [7]), ([9, 12], [9, 3]), ([31, 40, 22, 50], [30, 1, 22, 17])])
+def test_rect_permutation_matches_oracle(libpath, m_sizes, n_sizes):
+    """The host-side row permutation of the permuted QR (Sec. 6) equals the oracle's."""
+    import oracle.rect as OR
+    from paper_1809_10585_gb300 import binding as B
+    assert B.rect_permutation(m_sizes, n_sizes).tolist() == OR.row_permutation(m_sizes, n_sizes).tolist()
+
+
+def test_rect_permutation_rejects_bad_partitions(libpath):
+    import ctypes as C
+    from paper_1809_10585_gb300 import binding as B
+    p = (C.c_int * 64)()
+    bad = [([4, 6], [5, 5]),            # m_1 < n_1
+           ([4, 4, 4], [2, 2, 2]),      # not a power of two of leaves
+           ([4, 4], [0, 2])]            # empty column block
+    for ms, ns in bad:
+        rc = B.lib().hodlr_rect_permutation(len(ms), (C.c_int * len(ms))(*ms), (C.c_int * len(ns))(*ns), p)
+        assert rc == B.HODLR_EINVAL
